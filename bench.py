@@ -1,0 +1,349 @@
+"""Benchmark of the QS-PIC hot path: plasma particle-slice updates per second.
+
+One step = one beam step of the method: a full plasma sweep (every xi slice: push, deposit,
+FFT field solves, predictor-corrector for B_perp) followed by the beam push with the fused
+deposit of the next sweep's beam sources.  Workload: the 256x256, 1024-slice, 4-ppc mixed
+precision electron-beam run (5.4e8 beam macroparticles), synthetic seeded inputs, state
+resident in HBM.  Also measured: the same workload on the FP64 path (speedup denominator),
+an end-to-end figure through host buffers, the roofline of the dominant kernel, and the FP64
+oracle on a bounded sample (CPU baseline).
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica (the method does not shard; weak
+scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2607_24214_b300 import config  # noqa: E402
+
+METRIC = "plasma particle-slice updates/s (push+deposit+field solve), mixed vs FP64"
+WORKLOAD = "c2_mixed_electron_beam_256x256_1024slices"
+CPU_SAMPLE_SLICES = 12
+
+
+def bytes_per_update(p):
+    """Algorithmic HBM bytes per plasma particle-slice update of one beam step (mixed path):
+    plasma state read+write once per slice (x, y, u_x, u_y, psi_prev: 5 x 4 B x 2), the beam
+    state read (32 B) and written (28 B) once, the beam-source slab written and read
+    (2 x 16 B per node), and the field slab written and read (2 x 24 B per node)."""
+    ppc = p.ppc_plasma_x * p.ppc_plasma_y
+    cells = p.nx * p.ny
+    plasma = 40.0 * ppc * cells * p.nxi
+    nb = sum(p.nx * p.ny * s.ppc_x * s.ppc_y * s.ppc_xi * p.nxi for s in p.species)
+    beam = 60.0 * nb
+    slabs = (32.0 + 48.0) * cells * (p.nxi + 1)
+    return (plasma + beam + slabs) / (ppc * cells * p.nxi)
+
+
+def sweep_bytes(p):
+    """Algorithmic HBM bytes of one sweep launch: plasma state r+w per slice, beam sources
+    read (16 B per node), field slab written (24 B per node)."""
+    ppc = p.ppc_plasma_x * p.ppc_plasma_y
+    cells = p.nx * p.ny
+    return 40.0 * ppc * cells * p.nxi + (16.0 + 24.0) * cells * (p.nxi + 1)
+
+
+def push_bytes(p):
+    """Algorithmic HBM bytes of the beam push of one step: beam state read 32 B and written
+    28 B per particle, field slab read (24 B per node), sources written (16 B per node)."""
+    nb = sum(p.nx * p.ny * s.ppc_x * s.ppc_y * s.ppc_xi * p.nxi for s in p.species)
+    return 60.0 * nb + (24.0 + 16.0) * p.nx * p.ny * (p.nxi + 1)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.rows = []
+        self.proc = None
+        self.idx = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace('.', '').isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace('.', '').isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = set()
+        for r in self.rows:
+            for i, n in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def updates_per_step(p):
+    return p.plasma_per_slice() * p.nxi
+
+
+def time_steps(q, p, steps, warmup, torch, stream, extra=None):
+    """Warm up, then time `steps` beam steps with CUDA events on the library's stream; also
+    the sweep and push launches separately.  Returns (total ms, sweep ms list, push ms list,
+    launches)."""
+    for _ in range(warmup):
+        q.sweep()
+        q.beam_step()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    l0 = q.launch_count()
+    t0.record(stream)
+    for k in range(steps):
+        ev[k][0].record(stream)
+        q.sweep()
+        ev[k][1].record(stream)
+        q.beam_step()
+        ev[k][2].record(stream)
+        if extra:
+            extra()
+    t1.record(stream)
+    t1.synchronize()
+    torch.cuda.synchronize()
+    launches = q.launch_count() - l0
+    sw = [ev[k][0].elapsed_time(ev[k][1]) for k in range(steps)]
+    pu = [ev[k][1].elapsed_time(ev[k][2]) for k in range(steps)]
+    return t0.elapsed_time(t1), sw, pu, launches
+
+
+def cpu_baseline(p, slices=CPU_SAMPLE_SLICES):
+    """The FP64 oracle, as it stands, on the first `slices` slices of one sweep of the same
+    workload (the particles of the first xi cells only: the slice loop is sequential in xi)."""
+    from oracle import qspic
+    from paper_2607_24214_b300 import inputs
+    per_layer = p.nx * p.ny * p.species[0].ppc_x * p.species[0].ppc_y * p.species[0].ppc_xi
+    sub = inputs.beam_arrays(p, 0, 0, (slices + 2) * per_layer)
+    t = time.perf_counter()
+    src = qspic.beam_sources(p, [sub], n_nodes=slices + 2)
+    qspic.plasma_sweep(p, src, n_slices=slices)
+    dt = time.perf_counter() - t
+    return p.plasma_per_slice() * slices / dt, dt
+
+
+def run_reference(args, p):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup_ref):
+        cpu_baseline(p, 2)
+    t0 = time.perf_counter()
+    for _ in range(args.steps_ref):
+        v, _ = cpu_baseline(p)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    val = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "updates/s",
+            "n_gpus": args.gpus, "steps": args.steps_ref, "warmup": args.warmup_ref,
+            "ms_per_step": 1e3 * wall / max(args.steps_ref, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"first {CPU_SAMPLE_SLICES} slices"},
+            "cpu_baseline": {"value": val, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {CPU_SAMPLE_SLICES} of {p.nxi + 1} slices of "
+                                       f"one sweep, {p.nx}x{p.ny}, numpy FP64"},
+            "e2e": {"value": val, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--steps-ref", type=int, default=2)
+    ap.add_argument("--warmup-ref", type=int, default=0)
+    args = ap.parse_args()
+    p = config.c2_mixed_electron_beam()
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    if args.impl == "reference":
+        run_reference(args, p)
+        return
+    import torch
+
+    from paper_2607_24214_b300.qsa import QSA
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    q = QSA(p)
+    barrier(world)
+    with Clocks(local) as clk:
+        ms, sw, pu, launches = time_steps(q, p, args.steps, args.warmup, torch, stream)
+    barrier(world)
+    ms = max_over_ranks(ms, world)
+    d = q.diagnostics()
+    ups = updates_per_step(p)
+    value = ups * args.steps * world / (ms * 1e-3)
+    sw_ms, pu_ms = float(np.mean(sw)), float(np.mean(pu))
+    # dominant kernel: the larger of the sweep launch and the beam push
+    if sw_ms >= pu_ms:
+        dom, dom_ms, dom_bytes = "sweep_kernel", sw_ms, sweep_bytes(p)
+    else:
+        dom, dom_ms, dom_bytes = "beam_push_kernel", pu_ms, push_bytes(p)
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
+            "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+            "peak_source": peak_src,
+            "step_frac": bytes_per_update(p) * value / world / 1e9 / hbm_peak,
+            "sweep_ms": sw_ms, "push_ms": pu_ms}
+    q.close()
+    del q
+    torch.cuda.empty_cache()
+
+    line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": p.nx, "ny": p.ny, "nxi": p.nxi,
+                       "ppc_plasma": 4, "ppc_beam": 8, "beam_particles": 8 * p.nx * p.ny * p.nxi,
+                       "n_pc_iter": p.n_pc_iter, "precision": "mixed",
+                       "l2": "inputs larger than L2 (17 GB beam state)",
+                       "parallelism": f"replicas{world}"},
+            "gpu_launches": launches, "roofline": roof,
+            "clocks": clk.summary(), "status": d["status"]}
+
+    if not args.no_fp64:
+        p64 = p.with_(precision="fp64")
+        q = QSA(p64)
+        ms64, sw64, pu64, _ = time_steps(q, p64, args.fp64_steps, 1, torch, stream)
+        q.close()
+        del q
+        torch.cuda.empty_cache()
+        v64 = ups * args.fp64_steps / (ms64 * 1e-3)
+        line["fp64"] = {"value": v64, "unit": "updates/s", "steps": args.fp64_steps,
+                        "ms_per_step": ms64 / args.fp64_steps, "sweep_ms": float(np.mean(sw64)),
+                        "push_ms": float(np.mean(pu64)), "speedup_mixed_over_fp64": value / v64}
+
+    if not args.no_e2e:
+        line["e2e"] = e2e(p, args.e2e_steps, torch, stream)
+
+    if rank == 0 and not args.no_cpu:
+        v, dt = cpu_baseline(p)
+        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {CPU_SAMPLE_SLICES} of {p.nxi + 1} slices of "
+                                          f"one sweep of the same workload ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e(p, steps, torch, stream):
+    """Same metric through the public API with the beam state in pinned host memory: every
+    step uploads the beam (qsa_set_beam), sweeps, pushes and reads the per-slice diagnostics
+    back (qsa_diagnostics)."""
+    from paper_2607_24214_b300.qsa import QSA
+    q = QSA(p)
+    n = p.nx * p.ny * p.nxi * 8
+    keys = ("x", "y", "xi", "ux", "uy", "uz", "w")
+    host = {k: torch.empty(n, dtype=torch.float64, pin_memory=True).numpy() for k in keys}
+    import ctypes as ct
+    from paper_2607_24214_b300.qsa import _ptr
+    nout = ct.c_int64()
+    q._check(q.lib.qsa_get_beam(q.h, 0, n, *[_ptr(host[k]) for k in keys], ct.byref(nout)))
+    # one untimed pass
+    q.set_beam(0, host)
+    q.sweep()
+    q.beam_step()
+    q.diagnostics()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(steps):
+        q.set_beam(0, host)
+        q.sweep()
+        q.beam_step()
+        q.diagnostics()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    q.close()
+    del q
+    torch.cuda.empty_cache()
+    diag_bytes = (p.nxi + 1) * 15 * 8
+    return {"value": updates_per_step(p) * steps / dt, "unit": "updates/s",
+            "h2d_bytes_per_step": 7 * 8 * n, "d2h_bytes_per_step": diag_bytes,
+            "steps": steps}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * qsa.h -- C ABI of the B300 quasistatic PIC (QS-PIC) hot path.
+ *
+ * The method: arxiv 2607.24214, "Modeling ultrarelativistic streaming plasma instabilities
+ * under the quasistatic approximation".  Its section "Quasistatic model" fixes the physical
+ * setting (cold plasma electrons, immobile ions, beam species of charge Z_s, mass M_s, density
+ * ratio alpha_s = n_bs/n_p and Lorentz factor gamma_b; comoving variables (xi, tau) =
+ * (ct - x, t)); its QuaSSis paragraph fixes the code family (QS-PIC, transversely periodic
+ * boundaries, random macroparticle weights).  The paper prints no discrete algorithm; the
+ * discrete scheme implemented here (and, independently, by the FP64 oracle under oracle/) is:
+ *   - per beam step, a plasma sweep over xi slices j = 0..nxi: the plasma electrons start at
+ *     rest on a quiet lattice at xi = 0 and are pushed slice by slice; at each slice the
+ *     transverse fields psi, E_z, B_z, B_x, B_y are solved spectrally on the periodic grid, B_perp
+ *     by a predictor-corrector of n_pc_iter solves; the k = 0 mode is integrated in FP64;
+ *   - then a beam push by dt (relativistic Boris) through the stored slice fields.
+ * Normalised units throughout: time 1/omega_p, length c/omega_p, momentum m_e c, density n_p,
+ * fields m_e c omega_p/e.  z is the propagation axis; the paper's x is z here, its y is (x, y).
+ *
+ * Conventions of every entry point
+ *   - All calls return a qsa_status (0 = QSA_OK, < 0 error, > 0 warning) unless stated.
+ *   - Host arrays passed in are copied before the call returns; output buffers are the
+ *     caller's.  The library owns all device memory; it allocates it through the caller's
+ *     allocator callbacks when given (else cudaMallocAsync on the handle's stream).
+ *   - Work is enqueued on the handle's stream (the cudaStream_t passed to qsa_init, may be 0).
+ *     Calls that return host data synchronise that stream.
+ *   - Device-side failures (a grid barrier that timed out, non-finite values) are latched in a
+ *     device status word and returned by the next synchronising call.
+ *   - One handle per stream; a handle is not thread-safe.
+ *   - On error, qsa_last_error(h) gives a one-line description.
+ */
+#ifndef QSA_H
+#define QSA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QSA_MAX_SPECIES 4
+#define QSA_MAX_MODES 16
+#define QSA_MAX_N 512 /* largest transverse grid side: sizes are 1 or 2^a 3^b <= 512 */
+
+typedef enum {
+  QSA_OK = 0,
+  QSA_ERR_ARG = -1,       /* invalid argument or parameter */
+  QSA_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+  QSA_ERR_OOM = -3,       /* an allocation failed */
+  QSA_ERR_TIMEOUT = -4,   /* a device-side wait exceeded spin_limit iterations */
+  QSA_ERR_NONFINITE = -5, /* non-finite field or particle value detected */
+  QSA_ERR_STATE = -6,     /* call out of order (e.g. beam step before any sweep) */
+  QSA_WARN_PSI_FLOOR = 1  /* 1 + psi fell below psi_floor for some plasma particle */
+} qsa_status;
+
+typedef enum { QSA_FP64 = 0, QSA_MIXED = 1 } qsa_precision;
+
+/* One beam species (section "Quasistatic model": Z_s, M_s, alpha_s, gamma_b). */
+typedef struct {
+  double Z, M, alpha, gamma_b;
+  double gamma_spread_rel; /* std of gamma/gamma_b (Gaussian) */
+  double uperp_spread;     /* std of u_x, u_y (Gaussian, m_e c) */
+  double noise_rel;        /* std of the relative weight perturbation ("random weights") */
+  int32_t ppc_x, ppc_y, ppc_xi;
+  int32_t seeded;          /* 1: multiply this species' weights by the mode list */
+  double xi_front, xi_back;/* beam occupies [xi_front, xi_back); xi_back < 0 means Lxi */
+} qsa_species;
+
+/* Seeded transverse density mode: weight factor 1 + amplitude cos(k.x + phase). */
+typedef struct {
+  int32_t mx, my;          /* k = (2 pi mx / Lx, 2 pi my / Ly) */
+  double amplitude, phase;
+} qsa_mode;
+
+typedef struct {
+  int32_t nx, ny, nxi;     /* transverse cells (1 or 2^a 3^b <= 512), xi slices */
+  int32_t ppc_plasma_x, ppc_plasma_y;
+  int32_t n_species, n_modes;
+  int32_t precision;       /* qsa_precision */
+  int32_t n_pc_iter;       /* predictor-corrector field solves per slice (>= 1) */
+  int32_t _reserved;
+  double Lx, Ly, Lxi;      /* periodic box (Lx, Ly) and window length, c/omega_p */
+  double dt;               /* beam time step, 1/omega_p */
+  double psi_floor;        /* lower bound applied to 1 + psi of plasma particles */
+  uint64_t seed;           /* Philox key of the beam initial conditions */
+  int64_t spin_limit;      /* iteration limit of every device-side wait */
+  qsa_species species[QSA_MAX_SPECIES];
+  qsa_mode modes[QSA_MAX_MODES];
+} qsa_params;
+
+/* Allocator callbacks: alloc returns a device pointer (NULL on failure) of at least `bytes`
+ * bytes, aligned to 256 B, usable on `stream`; free releases it. */
+typedef void* (*qsa_alloc_fn)(size_t bytes, void* ctx, void* stream);
+typedef void (*qsa_free_fn)(void* ptr, size_t bytes, void* ctx, void* stream);
+
+typedef struct qsa_handle qsa_handle;
+
+/* Per-slice diagnostics of the last sweep; every non-NULL pointer is a caller array of
+ * nxi + 1 entries (energy: 6 * (nxi + 1), slice-major).  Any pointer may be NULL. */
+typedef struct {
+  double* energy;       /* 1/2 sum F^2 dx dy dxi of E_x, E_y, E_z, B_x, B_y, B_z */
+  double* psi0;         /* k = 0 mode of psi */
+  double* ez0;          /* k = 0 mode of E_z */
+  double* jz_mean;      /* <J_z> total (plasma + beam) */
+  double* kappa2;       /* Helmholtz shift of the B_perp solves, <w/(1+psi)>/(Lx Ly) */
+  double* opp_min;      /* min over plasma particles of 1 + psi (before the floor) */
+  double* n_floor;      /* plasma particles with 1 + psi < psi_floor */
+  double* invariant;    /* max |gamma - u_z - (1+psi)|/(1+psi) */
+  double* charge;       /* |sum_cells (rho - J_z)_plasma dx dy + Lx Ly| */
+  double* pc_residual;  /* ||B_perp(n) - B_perp(n-1)|| / ||B_perp(n)|| of the last solve */
+  int64_t beam_lost;    /* out: beam particles that left the window (all species) */
+  int64_t sweeps;       /* out: sweeps done by this handle */
+} qsa_diag;
+
+/* Create a handle: validates params, allocates device state, builds every beam species on
+ * the device from `seed` (quiet lattice, Philox-4x32-10 random weights and momenta; the same
+ * construction as paper_2607_24214_b300/inputs.py).  `stream` is a cudaStream_t or NULL.
+ * alloc/free may be NULL (then cudaMallocAsync / cudaFreeAsync).  Errors: QSA_ERR_ARG for an
+ * invalid parameter, QSA_ERR_OOM, QSA_ERR_CUDA; *out is NULL on error. */
+int qsa_init(const qsa_params* params, void* stream, qsa_alloc_fn alloc, qsa_free_fn free_fn,
+             void* alloc_ctx, qsa_handle** out);
+
+/* Replace species `s` with host fp64 arrays of n particles in the canonical id order of the
+ * lattice (id = ((k_xi*ny + iy)*nx + ix)*ppc + (s_xi*ppc_y + s_y)*ppc_x + s_x); n must equal
+ * the species' lattice count.  x, y in [0, L); xi in [0, Lxi); w = 0 marks a lost particle.
+ * Copies and converts to the device layout; marks the beam sources stale. */
+int qsa_set_beam(qsa_handle* h, int s, int64_t n, const double* x, const double* y,
+                 const double* xi, const double* ux, const double* uy, const double* uz,
+                 const double* w);
+
+/* Copy species `s` back to host fp64 arrays (canonical id order, positions wrapped into
+ * [0, L)); cap = capacity of each array; *n_out = particles written.  Synchronises. */
+int qsa_get_beam(qsa_handle* h, int s, int64_t cap, double* x, double* y, double* xi,
+                 double* ux, double* uy, double* uz, double* w, int64_t* n_out);
+
+/* One plasma sweep at the current beam state: deposits the beam sources if stale, then runs
+ * the slice loop j = 0..nxi in one persistent launch and fills the field slab and the
+ * per-slice diagnostics.  Asynchronous. */
+int qsa_plasma_sweep(qsa_handle* h);
+
+/* Push every live beam particle by dt through the current field slab (trilinear gather,
+ * relativistic Boris), drop particles with xi >= Lxi, and deposit the beam sources of the
+ * next sweep.  QSA_ERR_STATE before the first sweep.  Asynchronous. */
+int qsa_beam_step(qsa_handle* h);
+
+/* Copy the per-slice diagnostics of the last sweep into `out`; synchronises and returns the
+ * latched device status (QSA_ERR_TIMEOUT, QSA_WARN_PSI_FLOOR, ...). */
+int qsa_diagnostics(qsa_handle* h, qsa_diag* out);
+
+/* Copy field `field` (0..5 = E_x - B_y, E_y + B_x, E_z, B_x, B_y, B_z) of slices j0..j1-1
+ * of the slab into host_out[(j - j0) * ny * nx + iy * nx + ix] (fp64).  Synchronises. */
+int qsa_copy_field(qsa_handle* h, int field, int j0, int j1, double* host_out);
+
+/* Copy beam source `q` (0..3 = S_b = Z n (1 - v_z), J_zb, J_xb, J_yb) of nodes j0..j1-1 into
+ * host_out like qsa_copy_field.  Deposits the sources first if they are stale. */
+int qsa_copy_source(qsa_handle* h, int q, int j0, int j1, double* host_out);
+
+/* Standalone transverse solve on the handle's grid, through the same device phases (row
+ * FFT, column FFT + k-space solve, inverse FFTs) as the sweep.  Inputs are host fp64 [ny][nx]
+ * arrays; the k = 0 mode is dropped:
+ *   psi = S/k^2, d_x psi, d_y psi;  E_z = -(i k.J)/k^2;  B_z = (i k_x J_y - i k_y J_x)/k^2;
+ *   (k^2 + kappa2) B_x = i k_y J_z + D_y,  (k^2 + kappa2) B_y = -i k_x J_z - D_x.
+ * out: 7 host arrays back to back, [7][ny][nx]: psi, d_x psi, d_y psi, E_z, B_z, B_x, B_y.
+ * Uses the handle's sweep buffers (do not overlap with a sweep); synchronises. */
+int qsa_field_solve(qsa_handle* h, const double* S, const double* Jx, const double* Jy,
+                    const double* Jz, const double* Dx, const double* Dy, double kappa2,
+                    double* out);
+
+/* Kernel launches made by this handle since qsa_init (for launch accounting). */
+int64_t qsa_launch_count(const qsa_handle* h);
+
+/* Device bytes held by the handle. */
+int64_t qsa_device_bytes(const qsa_handle* h);
+
+/* One-line text of the last error of h (or of the last failed qsa_init when h is NULL). */
+const char* qsa_last_error(const qsa_handle* h);
+
+/* Release the handle and all its device memory (waits for its stream). */
+void qsa_destroy(qsa_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSA_H */

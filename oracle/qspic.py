@@ -192,12 +192,13 @@ def push_xi(ux, uy, opp, gx, gy, Bx, By, Bz, dxi):
 # ----------------------------------------------------------------------------------------
 # beam sources and plasma sweep
 # ----------------------------------------------------------------------------------------
-def beam_sources(p, beams):
+def beam_sources(p, beams, n_nodes=None):
     """Slab [4, nxi+1, ny, nx] of beam S_b = Z n (1 - v_z), J_z, J_x, J_y at xi nodes k dxi:
     CIC in x, y, linear in xi, density = sum Z w W / (dx dy dxi).  Live particles have
-    0 <= xi < Lxi, so both xi nodes lie in 0..nxi."""
+    0 <= xi < Lxi, so both xi nodes lie in 0..nxi.  With n_nodes, only nodes 0..n_nodes-1 are
+    kept (for runs on the first slices of a large window)."""
     G = Grid(p)
-    nk = p.nxi + 1
+    nk = p.nxi + 1 if n_nodes is None else n_nodes
     dxi = p.Lxi / p.nxi
     src = np.zeros((4, nk * p.ny * p.nx))
     for sp, b in zip(p.species, beams):
@@ -214,22 +215,26 @@ def beam_sources(p, beams):
         k0 = np.floor(g).astype(np.int64)
         f = g - k0
         for k, wk in ((k0, 1.0 - f), (k0 + 1, f)):
+            keep = k < nk
             for iy, wy in ((iy0, wy0), (iy1, wy1)):
                 for ix, wx in ((ix0, wx0), (ix1, wx1)):
-                    idx = (k * p.ny + iy) * p.nx + ix
-                    wt = wk * wy * wx
+                    idx = ((k * p.ny + iy) * p.nx + ix)[keep]
+                    wt = (wk * wy * wx)[keep]
                     for slot in range(4):
-                        src[slot] += np.bincount(idx, weights=vals[slot] * wt,
+                        src[slot] += np.bincount(idx, weights=vals[slot][keep] * wt,
                                                  minlength=src.shape[1])
     return src.reshape(4, nk, p.ny, p.nx)
 
 
-def plasma_sweep(p, src, return_particles=False, return_psi=False):
+def plasma_sweep(p, src, return_particles=False, return_psi=False, n_slices=None):
     """One sweep of the plasma through slices j = 0..nxi.  Returns the field slab
-    [nxi+1, 6, ny, nx] (Wx, Wy, Ez, Bx, By, Bz) and per-slice diagnostics."""
+    [nxi+1, 6, ny, nx] (Wx, Wy, Ez, Bx, By, Bz) and per-slice diagnostics.  With n_slices the
+    sweep stops after slices 0..n_slices-1 (the slice loop is sequential in xi, so these are
+    exactly the first slices of the full sweep); src then needs nodes 0..n_slices."""
     G = Grid(p)
     dxi = p.Lxi / p.nxi
-    nk = p.nxi + 1
+    nk = p.nxi + 1 if n_slices is None else n_slices
+    nsrc = src.shape[1]
     floor = p.psi_floor
     cell = G.dx * G.dy
     # quiet lattice at xi = 0
@@ -247,7 +252,7 @@ def plasma_sweep(p, src, return_particles=False, return_psi=False):
     psi_prev = np.zeros(npart)
 
     def src_at(slot, k):
-        if 0 <= k < nk:
+        if 0 <= k < nsrc:
             return src[slot, k]
         return np.zeros((p.ny, p.nx))
 
@@ -326,7 +331,7 @@ def plasma_sweep(p, src, return_particles=False, return_psi=False):
         psi_prev = psi_p
         psi0 = psi0 + dxi * ez0_next
         ez0_half = ez0_next
-        if j + 1 < nk:
+        if j + 1 < min(nk, p.nxi + 1):
             Se = deposit(G, x, y, -w)
             psi, gx_grid, gy_grid = solve_psi(G, Se + src_at(0, j + 1))
     if return_psi:

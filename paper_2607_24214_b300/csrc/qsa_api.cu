@@ -1,0 +1,689 @@
+// C ABI of the QS-PIC hot path (declarations and contracts in include/qsa.h).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/qsa.h"
+#include "qsa_beam.cuh"
+#include "qsa_common.cuh"
+#include "qsa_fft.cuh"
+#include "qsa_sweep.cuh"
+
+using namespace qsa;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+constexpr int kThreads = 256;
+
+bool size_ok(int n) {
+  if (n < 1 || n > QSA_MAX_N) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+FftPlan make_plan(int n) {
+  FftPlan p{};
+  p.n = n;
+  int m = n;
+  while (m % 4 == 0) { p.radix[p.nstages++] = 4; m /= 4; }
+  while (m % 2 == 0) { p.radix[p.nstages++] = 2; m /= 2; }
+  while (m % 3 == 0) { p.radix[p.nstages++] = 3; m /= 3; }
+  return p;
+}
+
+struct Base {
+  virtual ~Base() {}
+};
+
+}  // namespace
+
+struct qsa_handle {
+  qsa_params prm;
+  cudaStream_t stream = nullptr;
+  qsa_alloc_fn alloc = nullptr;
+  qsa_free_fn free_fn = nullptr;
+  void* ctx = nullptr;
+  int num_sms = 0;
+  DevParams dp{};
+  std::vector<std::pair<void*, size_t>> allocs;
+  int64_t bytes = 0;
+  int64_t launches = 0;
+  int64_t sweeps = 0;
+  bool src_valid = false;
+  std::string err;
+  // typed state lives behind these pointers (R = double for FP64, float for mixed)
+  bool fp64 = true;
+  void* st = nullptr;
+};
+
+namespace {
+
+int fail(qsa_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_init_error = msg;
+  return code;
+}
+
+int cuda_fail(qsa_handle* h, cudaError_t e, const char* what) {
+  return fail(h, QSA_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void* dalloc(qsa_handle* h, size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (h->alloc) {
+    p = h->alloc(bytes, h->ctx, (void*)h->stream);
+  } else if (cudaMallocAsync(&p, bytes, h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) {
+    h->allocs.push_back({p, bytes});
+    h->bytes += (int64_t)bytes;
+  }
+  return p;
+}
+
+void dfree_all(qsa_handle* h) {
+  for (auto& a : h->allocs) {
+    if (h->free_fn) h->free_fn(a.first, a.second, h->ctx, (void*)h->stream);
+    else cudaFreeAsync(a.first, h->stream);
+  }
+  h->allocs.clear();
+}
+
+template <typename R>
+struct State {
+  using BR = R;
+  SweepArgs<R> sa{};
+  std::vector<BeamArrays<BR>> beams;
+  std::vector<SpeciesDev> species;
+  ModesDev modes{};
+  R* src = nullptr;
+  R* slab = nullptr;
+  double* diag = nullptr;
+  unsigned long long* lost = nullptr;
+  unsigned* bar = nullptr;  // [0] count, [1] generation
+  int* status = nullptr;
+  C<R>* tw = nullptr;
+  size_t smem = 0;
+  int grid = 0;
+};
+
+template <typename R>
+State<R>* S(qsa_handle* h) { return reinterpret_cast<State<R>*>(h->st); }
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);    \
+  } while (0)
+
+template <typename R>
+size_t sweep_smem(const DevParams& dp) {
+  size_t tile = (size_t)kTileRows * dp.nx * kNF * sizeof(R);
+  size_t row = (size_t)2 * 3 * dp.nx * sizeof(C<R>);
+  size_t col = (size_t)2 * kNF * dp.ny * sizeof(C<R>);
+  size_t m = tile > row ? tile : row;
+  return m > col ? m : col;
+}
+
+template <typename R>
+int setup(qsa_handle* h) {
+  State<R>* s = new State<R>();
+  h->st = s;
+  const DevParams& dp = h->dp;
+  const size_t g = (size_t)dp.nx * dp.ny;
+  const size_t spec = (size_t)dp.nxh * dp.ny;
+  SweepArgs<R>& a = s->sa;
+  a.p = dp;
+  auto A = [&](size_t bytes) { return dalloc(h, bytes); };
+  const size_t np = (size_t)dp.np;
+  R** pl[5] = {&a.pox, &a.poy, &a.pux, &a.puy, &a.ppsi};
+  for (auto p : pl) if (!(*p = (R*)A(np * sizeof(R)))) return fail(h, QSA_ERR_OOM, "plasma");
+  R** gr[7] = {&a.psi, &a.gpx, &a.gpy, &a.bx, &a.by, &a.bz, &a.ez};
+  for (auto p : gr) if (!(*p = (R*)A(g * sizeof(R)))) return fail(h, QSA_ERR_OOM, "grids");
+  if (!(a.part = (R*)A((size_t)dp.ny * kTileRows * dp.nx * kNF * sizeof(R))) ||
+      !(a.ovf = (R*)A(g * kNF * sizeof(R))) ||
+      !(a.rspec = (C<R>*)A(kNF * spec * sizeof(C<R>))) ||
+      !(a.cspec = (C<R>*)A(4 * spec * sizeof(C<R>))) ||
+      !(a.jprev = (C<R>*)A(2 * spec * sizeof(C<R>))) ||
+      !(a.bold = (C<R>*)A(2 * spec * sizeof(C<R>))) ||
+      !(s->tw = (C<R>*)A((size_t)(dp.nx + dp.ny) * sizeof(C<R>))) ||
+      !(s->src = (R*)A((size_t)dp.nk * g * 4 * sizeof(R))) ||
+      !(s->slab = (R*)A((size_t)dp.nk * g * 8 * sizeof(R))) ||
+      !(s->diag = (double*)A((size_t)D_COUNT * dp.nk * sizeof(double))) ||
+      !(s->lost = (unsigned long long*)A(sizeof(unsigned long long))) ||
+      !(s->bar = (unsigned*)A(2 * sizeof(unsigned))) ||
+      !(s->status = (int*)A(sizeof(int))))
+    return fail(h, QSA_ERR_OOM, "sweep buffers");
+  // twiddles exp(-2 pi i m/n), built in FP64 on the host
+  std::vector<C<R>> tw(dp.nx + dp.ny);
+  for (int m = 0; m < dp.nx; ++m) {
+    const double t = -2.0 * M_PI * m / dp.nx;
+    tw[m] = C<R>{R(std::cos(t)), R(std::sin(t))};
+  }
+  for (int m = 0; m < dp.ny; ++m) {
+    const double t = -2.0 * M_PI * m / dp.ny;
+    tw[dp.nx + m] = C<R>{R(std::cos(t)), R(std::sin(t))};
+  }
+  CK(cudaMemcpyAsync(s->tw, tw.data(), tw.size() * sizeof(C<R>), cudaMemcpyHostToDevice,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  a.twx = s->tw;
+  a.twy = s->tw + dp.nx;
+  a.src = s->src;
+  a.slab = s->slab;
+  a.diag = s->diag;
+  a.bar = Barrier{s->bar, s->bar + 1, s->status, (long long)h->prm.spin_limit};
+  CK(cudaMemsetAsync(s->bar, 0, 2 * sizeof(unsigned), h->stream));
+  CK(cudaMemsetAsync(s->status, 0, sizeof(int), h->stream));
+  CK(cudaMemsetAsync(s->lost, 0, sizeof(unsigned long long), h->stream));
+  CK(cudaMemsetAsync(s->slab, 0, (size_t)dp.nk * g * 8 * sizeof(R), h->stream));
+  CK(cudaMemsetAsync(s->diag, 0, (size_t)D_COUNT * dp.nk * sizeof(double), h->stream));
+  // launch shape of the persistent kernels
+  s->smem = sweep_smem<R>(dp);
+  CK(cudaFuncSetAttribute(sweep_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)s->smem));
+  CK(cudaFuncSetAttribute(solve_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)s->smem));
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<R>, kThreads, s->smem));
+  int per_sm2 = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, solve_kernel<R>, kThreads, s->smem));
+  per_sm = per_sm < per_sm2 ? per_sm : per_sm2;
+  if (per_sm < 1) return fail(h, QSA_ERR_ARG, "sweep kernel does not fit on an SM");
+  const int work = dp.ny > dp.nxh ? dp.ny : dp.nxh;
+  s->grid = per_sm * h->num_sms;
+  if (s->grid > work) s->grid = work;
+  // beam species
+  const qsa_params& P = h->prm;
+  s->modes.n = P.n_modes;
+  for (int m = 0; m < P.n_modes; ++m) {
+    s->modes.mx[m] = P.modes[m].mx;
+    s->modes.my[m] = P.modes[m].my;
+    s->modes.amp[m] = P.modes[m].amplitude;
+    s->modes.phase[m] = P.modes[m].phase;
+  }
+  for (int si = 0; si < P.n_species; ++si) {
+    const qsa_species& q = P.species[si];
+    SpeciesDev sp{};
+    sp.Z = q.Z; sp.M = q.M; sp.alpha = q.alpha; sp.gamma_b = q.gamma_b;
+    sp.gamma_spread_rel = q.gamma_spread_rel; sp.uperp_spread = q.uperp_spread;
+    sp.noise_rel = q.noise_rel;
+    sp.ppx = q.ppc_x; sp.ppy = q.ppc_y; sp.ppxi = q.ppc_xi;
+    sp.ppc = q.ppc_x * q.ppc_y * q.ppc_xi;
+    const double back = q.xi_back < 0 ? P.Lxi : q.xi_back;
+    sp.k0 = (int)std::lround(q.xi_front / dp.dxi);
+    sp.nkb = (int)std::lround(back / dp.dxi) - sp.k0;
+    sp.seeded = q.seeded;
+    sp.index = si;
+    BeamArrays<R> b{};
+    b.n = (long long)dp.nx * dp.ny * sp.nkb * sp.ppc;
+    const size_t n = (size_t)b.n;
+    if (!(b.ox = (R*)A(n * sizeof(R))) || !(b.oy = (R*)A(n * sizeof(R))) ||
+        !(b.oxi = (R*)A(n * sizeof(R))) || !(b.ux = (R*)A(n * sizeof(R))) ||
+        !(b.uy = (R*)A(n * sizeof(R))) || !(b.w = (R*)A(n * sizeof(R))) ||
+        !(b.uz = (double*)A(n * sizeof(double))))
+      return fail(h, QSA_ERR_OOM, "beam arrays");
+    s->species.push_back(sp);
+    s->beams.push_back(b);
+    if (b.n > 0) {
+      const unsigned blocks = (unsigned)((b.n + kThreads - 1) / kThreads);
+      beam_init_kernel<R><<<blocks, kThreads, 0, h->stream>>>(b, dp, sp, s->modes, P.seed);
+      ++h->launches;
+      CK(cudaGetLastError());
+    }
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return QSA_OK;
+}
+
+template <typename R>
+int deposit_sources(qsa_handle* h) {
+  State<R>* s = S<R>(h);
+  const DevParams& dp = h->dp;
+  CK(cudaMemsetAsync(s->src, 0, (size_t)dp.nk * dp.nx * dp.ny * 4 * sizeof(R), h->stream));
+  for (size_t si = 0; si < s->beams.size(); ++si) {
+    const auto& b = s->beams[si];
+    if (b.n == 0) continue;
+    const unsigned blocks = (unsigned)((b.n + kThreads - 1) / kThreads);
+    beam_deposit_kernel<R><<<blocks, kThreads, 0, h->stream>>>(b, dp, s->species[si], s->src);
+    ++h->launches;
+    CK(cudaGetLastError());
+  }
+  h->src_valid = true;
+  return QSA_OK;
+}
+
+__global__ void diag_init_kernel(double* diag, int nk) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= D_COUNT * nk) return;
+  diag[i] = 0.0;
+  if (i / nk == D_OPPMIN) {
+    unsigned long long k = dkey(1e300);
+    diag[i] = __longlong_as_double((long long)k);
+  }
+}
+
+template <typename R>
+int sweep(qsa_handle* h) {
+  State<R>* s = S<R>(h);
+  const DevParams& dp = h->dp;
+  if (!h->src_valid) {
+    int rc = deposit_sources<R>(h);
+    if (rc) return rc;
+  }
+  const size_t g = (size_t)dp.nx * dp.ny;
+  const size_t spec = (size_t)dp.nxh * dp.ny;
+  SweepArgs<R>& a = s->sa;
+  CK(cudaMemsetAsync(a.ovf, 0, g * kNF * sizeof(R), h->stream));
+  CK(cudaMemsetAsync(a.bold, 0, 2 * spec * sizeof(C<R>), h->stream));
+  CK(cudaMemsetAsync(a.bx, 0, g * sizeof(R), h->stream));
+  CK(cudaMemsetAsync(a.by, 0, g * sizeof(R), h->stream));
+  CK(cudaMemsetAsync(a.bz, 0, g * sizeof(R), h->stream));
+  CK(cudaMemsetAsync(s->bar, 0, sizeof(unsigned), h->stream));
+  const int nd = D_COUNT * dp.nk;
+  diag_init_kernel<<<(nd + 255) / 256, 256, 0, h->stream>>>(s->diag, dp.nk);
+  ++h->launches;
+  a.src = s->src;
+  void* args[] = {&a};
+  CK(cudaLaunchCooperativeKernel((void*)sweep_kernel<R>, dim3(s->grid), dim3(kThreads), args,
+                                 s->smem, h->stream));
+  ++h->launches;
+  ++h->sweeps;
+  return QSA_OK;
+}
+
+template <typename R>
+int beam_step(qsa_handle* h) {
+  State<R>* s = S<R>(h);
+  const DevParams& dp = h->dp;
+  CK(cudaMemsetAsync(s->src, 0, (size_t)dp.nk * dp.nx * dp.ny * 4 * sizeof(R), h->stream));
+  for (size_t si = 0; si < s->beams.size(); ++si) {
+    const auto& b = s->beams[si];
+    if (b.n == 0) continue;
+    const unsigned blocks = (unsigned)((b.n + kThreads - 1) / kThreads);
+    beam_push_kernel<R><<<blocks, kThreads, 0, h->stream>>>(b, dp, s->species[si], s->slab,
+                                                            s->src, s->lost);
+    ++h->launches;
+    CK(cudaGetLastError());
+  }
+  h->src_valid = true;
+  return QSA_OK;
+}
+
+int status_code(int st) {
+  if (st & ST_TIMEOUT) return QSA_ERR_TIMEOUT;
+  if (st & ST_NONFINITE) return QSA_ERR_NONFINITE;
+  if (st & ST_FLOOR) return QSA_WARN_PSI_FLOOR;
+  return QSA_OK;
+}
+
+double key_to_double(double stored) {
+  unsigned long long k;
+  std::memcpy(&k, &stored, 8);
+  unsigned long long b = (k & 0x8000000000000000ull) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+  double v;
+  std::memcpy(&v, &b, 8);
+  return v;
+}
+
+template <typename R>
+int diagnostics(qsa_handle* h, qsa_diag* out) {
+  State<R>* s = S<R>(h);
+  const int nk = h->dp.nk;
+  std::vector<double> d((size_t)D_COUNT * nk);
+  int st = 0;
+  unsigned long long lost = 0;
+  CK(cudaMemcpyAsync(d.data(), s->diag, d.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&lost, s->lost, sizeof(lost), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  auto row = [&](int r) { return d.data() + (size_t)r * nk; };
+  const double npc = (double)h->dp.ppc * h->dp.nx * h->dp.ny;
+  const double area = h->prm.Lx * h->prm.Ly;
+  for (int j = 0; j < nk; ++j) {
+    if (out->energy)
+      for (int f = 0; f < 6; ++f) out->energy[(size_t)j * 6 + f] = row(D_E0 + f)[j];
+    if (out->psi0) out->psi0[j] = row(D_PSI0)[j];
+    if (out->ez0) out->ez0[j] = row(D_EZ0)[j];
+    if (out->jz_mean) out->jz_mean[j] = row(D_JZ)[j];
+    if (out->kappa2) out->kappa2[j] = row(D_KAPPA)[j] / npc;
+    if (out->opp_min) out->opp_min[j] = key_to_double(row(D_OPPMIN)[j]);
+    if (out->n_floor) out->n_floor[j] = row(D_NFLOOR)[j];
+    if (out->invariant) out->invariant[j] = row(D_INV)[j];
+    if (out->charge) out->charge[j] = std::fabs(row(D_CHARGE)[j] + area);
+    if (out->pc_residual) {
+      const double den = row(D_PCDEN)[j];
+      out->pc_residual[j] = den > 0 ? std::sqrt(row(D_PCNUM)[j] / den) : 0.0;
+    }
+  }
+  out->beam_lost = (int64_t)lost;
+  out->sweeps = h->sweeps;
+  const int rc = status_code(st);
+  if (rc < 0) fail(h, rc, rc == QSA_ERR_TIMEOUT ? "device wait exceeded spin_limit"
+                                                 : "non-finite field value");
+  return rc;
+}
+
+template <typename R>
+int copy_field(qsa_handle* h, int field, int j0, int j1, double* out, bool source) {
+  State<R>* s = S<R>(h);
+  const DevParams& dp = h->dp;
+  const int stride = source ? 4 : 8;
+  const size_t g = (size_t)dp.nx * dp.ny;
+  std::vector<R> tmp((size_t)(j1 - j0) * g * stride);
+  const R* base = (source ? s->src : s->slab) + (size_t)j0 * g * stride;
+  CK(cudaMemcpyAsync(tmp.data(), base, tmp.size() * sizeof(R), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (size_t i = 0; i < (size_t)(j1 - j0) * g; ++i) out[i] = (double)tmp[i * stride + field];
+  return QSA_OK;
+}
+
+template <typename R>
+int beam_io(qsa_handle* h, int si, bool to_host, int64_t n, const double* const* in,
+            double* const* out) {
+  State<R>* s = S<R>(h);
+  const auto& b = s->beams[si];
+  const size_t bytes = (size_t)b.n * sizeof(double);
+  std::vector<void*> tmp;
+  for (int k = 0; k < 7; ++k) {
+    void* p = dalloc(h, bytes);
+    if (!p) return fail(h, QSA_ERR_OOM, "beam staging");
+    tmp.push_back(p);
+  }
+  const unsigned blocks = (unsigned)((b.n + kThreads - 1) / kThreads);
+  int rc = QSA_OK;
+  if (!to_host) {
+    for (int k = 0; k < 7; ++k)
+      CK(cudaMemcpyAsync(tmp[k], in[k], bytes, cudaMemcpyHostToDevice, h->stream));
+    beam_from_host_kernel<R><<<blocks, kThreads, 0, h->stream>>>(
+        b, h->dp, s->species[si], (double*)tmp[0], (double*)tmp[1], (double*)tmp[2],
+        (double*)tmp[3], (double*)tmp[4], (double*)tmp[5], (double*)tmp[6]);
+    ++h->launches;
+    CK(cudaGetLastError());
+    h->src_valid = false;
+  } else {
+    beam_to_host_kernel<R><<<blocks, kThreads, 0, h->stream>>>(
+        b, h->dp, s->species[si], (double*)tmp[0], (double*)tmp[1], (double*)tmp[2],
+        (double*)tmp[3], (double*)tmp[4], (double*)tmp[5], (double*)tmp[6]);
+    ++h->launches;
+    CK(cudaGetLastError());
+    for (int k = 0; k < 7; ++k)
+      CK(cudaMemcpyAsync(out[k], tmp[k], bytes, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  // release the staging buffers (the last seven allocations)
+  for (int k = 0; k < 7; ++k) {
+    auto a = h->allocs.back();
+    h->allocs.pop_back();
+    h->bytes -= (int64_t)a.second;
+    if (h->free_fn) h->free_fn(a.first, a.second, h->ctx, (void*)h->stream);
+    else cudaFreeAsync(a.first, h->stream);
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
+template <typename R>
+int field_solve(qsa_handle* h, const double* const* in, double kappa2, double* out) {
+  State<R>* s = S<R>(h);
+  const DevParams& dp = h->dp;
+  const size_t g = (size_t)dp.nx * dp.ny;
+  SweepArgs<R> a = s->sa;
+  a.src = nullptr;
+  std::vector<R> ov(g * kNF);
+  std::vector<double> dg((size_t)D_COUNT * dp.nk, 0.0);
+  dg[(size_t)D_KAPPA * dp.nk] = kappa2 * dp.ppc * (double)dp.nx * dp.ny;
+  CK(cudaMemcpyAsync(s->diag, dg.data(), dg.size() * sizeof(double), cudaMemcpyHostToDevice,
+                     h->stream));
+  CK(cudaMemsetAsync(a.part, 0, (size_t)dp.ny * kTileRows * dp.nx * kNF * sizeof(R), h->stream));
+  CK(cudaMemsetAsync(a.jprev, 0, 2 * (size_t)dp.nxh * dp.ny * sizeof(C<R>), h->stream));
+  CK(cudaMemsetAsync(a.bold, 0, 2 * (size_t)dp.nxh * dp.ny * sizeof(C<R>), h->stream));
+  // B solve: trial fields Jx, Jy, Jz, Jx^{+1/2} = D_x dxi, Jy^{+1/2} = D_y dxi (J^{-1/2} = 0)
+  for (size_t i = 0; i < g; ++i) {
+    ov[i * kNF + 0] = R(in[1][i]);
+    ov[i * kNF + 1] = R(in[2][i]);
+    ov[i * kNF + 2] = R(in[3][i]);
+    ov[i * kNF + 3] = R(in[4][i] * dp.dxi);
+    ov[i * kNF + 4] = R(in[5][i] * dp.dxi);
+  }
+  CK(cudaMemcpyAsync(a.ovf, ov.data(), ov.size() * sizeof(R), cudaMemcpyHostToDevice,
+                     h->stream));
+  CK(cudaMemsetAsync(s->bar, 0, sizeof(unsigned), h->stream));
+  int which = 0;
+  void* args[] = {&a, &which};
+  CK(cudaLaunchCooperativeKernel((void*)solve_kernel<R>, dim3(s->grid), dim3(kThreads), args,
+                                 s->smem, h->stream));
+  ++h->launches;
+  std::vector<R> tmp(g);
+  auto get = [&](const R* d, double* o) -> int {
+    CK(cudaMemcpyAsync(tmp.data(), d, g * sizeof(R), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < g; ++i) o[i] = (double)tmp[i];
+    return QSA_OK;
+  };
+  int rc;
+  if ((rc = get(a.ez, out + 3 * g)) || (rc = get(a.bz, out + 4 * g)) ||
+      (rc = get(a.bx, out + 5 * g)) || (rc = get(a.by, out + 6 * g)))
+    return rc;
+  // psi solve: S in field 0 of three
+  std::fill(ov.begin(), ov.end(), R(0));
+  for (size_t i = 0; i < g; ++i) ov[i * 3] = R(in[0][i]);
+  CK(cudaMemcpyAsync(a.ovf, ov.data(), g * 3 * sizeof(R), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemsetAsync(a.part, 0, (size_t)dp.ny * kTileRows * dp.nx * kNF * sizeof(R), h->stream));
+  CK(cudaMemsetAsync(s->bar, 0, sizeof(unsigned), h->stream));
+  which = 1;
+  CK(cudaLaunchCooperativeKernel((void*)solve_kernel<R>, dim3(s->grid), dim3(kThreads), args,
+                                 s->smem, h->stream));
+  ++h->launches;
+  if ((rc = get(a.psi, out)) || (rc = get(a.gpx, out + g)) || (rc = get(a.gpy, out + 2 * g)))
+    return rc;
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  rc = status_code(st);
+  return rc < 0 ? fail(h, rc, "device wait exceeded spin_limit") : QSA_OK;
+}
+
+int validate(const qsa_params* p, std::string& why) {
+  auto bad = [&](const std::string& m) { why = m; return QSA_ERR_ARG; };
+  if (!p) return bad("params is NULL");
+  if (!size_ok(p->nx) || !size_ok(p->ny)) return bad("nx, ny must be 1 or 2^a 3^b <= 512");
+  if (p->nxi < 1) return bad("nxi must be >= 1");
+  if (!(p->Lx > 0 && p->Ly > 0 && p->Lxi > 0 && p->dt > 0)) return bad("box and dt must be > 0");
+  if (p->ppc_plasma_x < 1 || p->ppc_plasma_y < 1 || p->ppc_plasma_x * p->ppc_plasma_y > 64)
+    return bad("plasma ppc must be in 1..64");
+  if (p->n_species < 0 || p->n_species > QSA_MAX_SPECIES) return bad("n_species out of range");
+  if (p->n_modes < 0 || p->n_modes > QSA_MAX_MODES) return bad("n_modes out of range");
+  if (p->precision != QSA_FP64 && p->precision != QSA_MIXED) return bad("unknown precision");
+  if (p->n_pc_iter < 1 || p->n_pc_iter > 64) return bad("n_pc_iter must be in 1..64");
+  if (!(p->psi_floor > 0 && p->psi_floor < 1)) return bad("psi_floor must be in (0, 1)");
+  if (p->spin_limit < 0) return bad("spin_limit must be >= 0");
+  const double dxi = p->Lxi / p->nxi;
+  for (int s = 0; s < p->n_species; ++s) {
+    const qsa_species& q = p->species[s];
+    if (!(q.M > 0) || !(q.gamma_b >= 1) || q.alpha < 0) return bad("species Z/M/gamma/alpha");
+    if (q.ppc_x < 1 || q.ppc_y < 1 || q.ppc_xi < 1) return bad("species ppc must be >= 1");
+    const double back = q.xi_back < 0 ? p->Lxi : q.xi_back;
+    if (q.xi_front < 0 || back > p->Lxi * (1 + 1e-12) || back <= q.xi_front)
+      return bad("species xi extent must satisfy 0 <= front < back <= Lxi");
+    if (std::fabs(q.xi_front / dxi - std::lround(q.xi_front / dxi)) > 1e-9 ||
+        std::fabs(back / dxi - std::lround(back / dxi)) > 1e-9)
+      return bad("species xi extent must be whole slices");
+    if (!(q.gamma_spread_rel >= 0 && q.gamma_spread_rel < 0.2)) return bad("gamma spread");
+  }
+  return QSA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qsa_init(const qsa_params* params, void* stream, qsa_alloc_fn alloc, qsa_free_fn free_fn,
+             void* alloc_ctx, qsa_handle** out) {
+  if (!out) return fail(nullptr, QSA_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  if (validate(params, why) != QSA_OK) return fail(nullptr, QSA_ERR_ARG, why);
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(nullptr, QSA_ERR_ARG, "alloc and free must both be given or both be NULL");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, QSA_ERR_CUDA, cudaGetErrorString(e));
+  qsa_handle* h = new qsa_handle();
+  h->prm = *params;
+  h->stream = (cudaStream_t)stream;
+  h->alloc = alloc;
+  h->free_fn = free_fn;
+  h->ctx = alloc_ctx;
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  DevParams& dp = h->dp;
+  dp.nx = params->nx;
+  dp.ny = params->ny;
+  dp.nxi = params->nxi;
+  dp.nk = params->nxi + 1;
+  dp.nxh = params->nx / 2 + 1;
+  dp.ppx = params->ppc_plasma_x;
+  dp.ppy = params->ppc_plasma_y;
+  dp.ppc = dp.ppx * dp.ppy;
+  dp.np = dp.ppc * dp.nx * dp.ny;
+  dp.n_pc = params->n_pc_iter;
+  dp.nsmem_rows = kTileRows;
+  dp.Lx = params->Lx;
+  dp.Ly = params->Ly;
+  dp.Lxi = params->Lxi;
+  dp.dx = params->Lx / params->nx;
+  dp.dy = params->Ly / params->ny;
+  dp.dxi = params->Lxi / params->nxi;
+  dp.dt = params->dt;
+  dp.psi_floor = params->psi_floor;
+  dp.spin_limit = params->spin_limit;
+  dp.px = make_plan(dp.nx);
+  dp.py = make_plan(dp.ny);
+  h->fp64 = params->precision == QSA_FP64;
+  const size_t smem = h->fp64 ? sweep_smem<double>(dp) : sweep_smem<float>(dp);
+  int max_smem = 0;
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int rc;
+  if ((int)smem > max_smem) {
+    rc = fail(h, QSA_ERR_ARG, "grid too large for shared memory");
+  } else {
+    rc = h->fp64 ? setup<double>(h) : setup<float>(h);
+  }
+  if (rc != QSA_OK) {
+    g_init_error = h->err;
+    qsa_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return QSA_OK;
+}
+
+int qsa_set_beam(qsa_handle* h, int s, int64_t n, const double* x, const double* y,
+                 const double* xi, const double* ux, const double* uy, const double* uz,
+                 const double* w) {
+  if (!h) return QSA_ERR_ARG;
+  if (s < 0 || s >= h->prm.n_species) return fail(h, QSA_ERR_ARG, "species index");
+  const int64_t want = h->fp64 ? S<double>(h)->beams[s].n : S<float>(h)->beams[s].n;
+  if (n != want) return fail(h, QSA_ERR_ARG, "n must equal the species' lattice count");
+  if (!x || !y || !xi || !ux || !uy || !uz || !w) return fail(h, QSA_ERR_ARG, "NULL array");
+  for (int64_t i = 0; i < n; ++i)
+    if (!(xi[i] >= 0.0 && xi[i] < h->prm.Lxi) && w[i] != 0.0)
+      return fail(h, QSA_ERR_ARG, "xi of a live particle outside [0, Lxi)");
+  const double* in[7] = {x, y, xi, ux, uy, uz, w};
+  return h->fp64 ? beam_io<double>(h, s, false, n, in, nullptr)
+                 : beam_io<float>(h, s, false, n, in, nullptr);
+}
+
+int qsa_get_beam(qsa_handle* h, int s, int64_t cap, double* x, double* y, double* xi,
+                 double* ux, double* uy, double* uz, double* w, int64_t* n_out) {
+  if (!h) return QSA_ERR_ARG;
+  if (s < 0 || s >= h->prm.n_species) return fail(h, QSA_ERR_ARG, "species index");
+  const int64_t n = h->fp64 ? S<double>(h)->beams[s].n : S<float>(h)->beams[s].n;
+  if (cap < n) return fail(h, QSA_ERR_ARG, "capacity smaller than the species count");
+  if (!x || !y || !xi || !ux || !uy || !uz || !w) return fail(h, QSA_ERR_ARG, "NULL array");
+  double* out[7] = {x, y, xi, ux, uy, uz, w};
+  const int rc = h->fp64 ? beam_io<double>(h, s, true, n, nullptr, out)
+                         : beam_io<float>(h, s, true, n, nullptr, out);
+  if (n_out) *n_out = rc == QSA_OK ? n : 0;
+  return rc;
+}
+
+int qsa_plasma_sweep(qsa_handle* h) {
+  if (!h) return QSA_ERR_ARG;
+  return h->fp64 ? sweep<double>(h) : sweep<float>(h);
+}
+
+int qsa_beam_step(qsa_handle* h) {
+  if (!h) return QSA_ERR_ARG;
+  if (h->sweeps == 0) return fail(h, QSA_ERR_STATE, "beam step before any sweep");
+  return h->fp64 ? beam_step<double>(h) : beam_step<float>(h);
+}
+
+int qsa_diagnostics(qsa_handle* h, qsa_diag* out) {
+  if (!h || !out) return QSA_ERR_ARG;
+  return h->fp64 ? diagnostics<double>(h, out) : diagnostics<float>(h, out);
+}
+
+int qsa_copy_field(qsa_handle* h, int field, int j0, int j1, double* host_out) {
+  if (!h || !host_out) return QSA_ERR_ARG;
+  if (field < 0 || field > 5 || j0 < 0 || j1 > h->dp.nk || j0 >= j1)
+    return fail(h, QSA_ERR_ARG, "field or slice range");
+  return h->fp64 ? copy_field<double>(h, field, j0, j1, host_out, false)
+                 : copy_field<float>(h, field, j0, j1, host_out, false);
+}
+
+int qsa_copy_source(qsa_handle* h, int q, int j0, int j1, double* host_out) {
+  if (!h || !host_out) return QSA_ERR_ARG;
+  if (q < 0 || q > 3 || j0 < 0 || j1 > h->dp.nk || j0 >= j1)
+    return fail(h, QSA_ERR_ARG, "source or node range");
+  if (!h->src_valid) {
+    const int rc = h->fp64 ? deposit_sources<double>(h) : deposit_sources<float>(h);
+    if (rc) return rc;
+  }
+  return h->fp64 ? copy_field<double>(h, q, j0, j1, host_out, true)
+                 : copy_field<float>(h, q, j0, j1, host_out, true);
+}
+
+int qsa_field_solve(qsa_handle* h, const double* S_, const double* Jx, const double* Jy,
+                    const double* Jz, const double* Dx, const double* Dy, double kappa2,
+                    double* out) {
+  if (!h || !S_ || !Jx || !Jy || !Jz || !Dx || !Dy || !out) return QSA_ERR_ARG;
+  if (!(kappa2 >= 0)) return fail(h, QSA_ERR_ARG, "kappa2 must be >= 0");
+  const double* in[6] = {S_, Jx, Jy, Jz, Dx, Dy};
+  return h->fp64 ? field_solve<double>(h, in, kappa2, out) : field_solve<float>(h, in, kappa2, out);
+}
+
+int64_t qsa_launch_count(const qsa_handle* h) { return h ? h->launches : 0; }
+
+int64_t qsa_device_bytes(const qsa_handle* h) { return h ? h->bytes : 0; }
+
+const char* qsa_last_error(const qsa_handle* h) {
+  return h ? h->err.c_str() : g_init_error.c_str();
+}
+
+void qsa_destroy(qsa_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  dfree_all(h);
+  cudaStreamSynchronize(h->stream);
+  if (h->st) {
+    if (h->fp64) delete S<double>(h);
+    else delete S<float>(h);
+  }
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,370 @@
+// Beam macroparticles: device initialisation, relativistic Boris push in tau through the
+// field slab (trilinear: CIC in x, y, linear in xi), loss at the back of the window, and the
+// deposit of the beam sources S_b = Z n (1 - v_z), J_z, J_x, J_y of the next sweep.
+//
+// Storage per species, index s = ((k_xi * ny + iy) * ppc + sub) * nx + ix (a warp holds 32
+// neighbouring cells of one sub-lattice position).  Positions are offsets, in cells, from
+// the particle's lattice home; this keeps the slow transverse and longitudinal drifts of an
+// ultrarelativistic beam (1e-6 cells per step) exact in FP32.  u_z is FP64 in both paths.
+#pragma once
+#include "qsa_common.cuh"
+
+namespace qsa {
+
+template <typename BR>
+struct BeamArrays {
+  BR *ox, *oy, *oxi, *ux, *uy, *w;
+  double* uz;
+  long long n;
+};
+
+struct SpeciesDev {
+  double Z, M, alpha, gamma_b, gamma_spread_rel, uperp_spread, noise_rel;
+  int ppx, ppy, ppxi, ppc;
+  int k0, nkb;  // first xi cell and number of xi cells
+  int seeded, index;
+};
+
+struct ModesDev {
+  int n;
+  int mx[16], my[16];
+  double amp[16], phase[16];
+};
+
+// Home of storage index s: cell (ix, iy, kxi) and sub-lattice (sx, sy, sxi).
+struct Home {
+  int ix, iy, kxi, sx, sy, sxi;
+  long long id;  // canonical id ((kxi*ny + iy)*nx + ix)*ppc + sub
+};
+__device__ __forceinline__ Home home_of(long long s, int nx, int ny, const SpeciesDev& sp) {
+  Home h;
+  h.ix = (int)(s % nx);
+  long long r = s / nx;
+  const int sub = (int)(r % sp.ppc);
+  r /= sp.ppc;
+  h.iy = (int)(r % ny);
+  h.kxi = (int)(r / ny);
+  h.sx = sub % sp.ppx;
+  h.sy = (sub / sp.ppx) % sp.ppy;
+  h.sxi = sub / (sp.ppx * sp.ppy);
+  h.id = (((long long)h.kxi * ny + h.iy) * nx + h.ix) * sp.ppc + sub;
+  return h;
+}
+
+// ------------------------------------------------------------------ initialisation
+template <typename BR>
+__global__ void beam_init_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp, ModesDev md,
+                                 unsigned long long seed) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= b.n) return;
+  const Home h = home_of(s, p.nx, p.ny, sp);
+  const U4 r = philox4x32_10(U4{(uint32_t)(h.id & 0xFFFFFFFFull), (uint32_t)(h.id >> 32),
+                                (uint32_t)sp.index, 0u},
+                             (uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32));
+  const double a0 = sqrt(-2.0 * log(u01(r.a))), a1 = sqrt(-2.0 * log(u01(r.c)));
+  double s1, c1, s3, c3;
+  sincospi(2.0 * u01(r.b), &s1, &c1);
+  sincospi(2.0 * u01(r.d), &s3, &c3);
+  const double n0 = a0 * c1, n1 = a0 * s1, n2 = a1 * c3, n3 = a1 * s3;
+  double w = sp.alpha * p.dx * p.dy * p.dxi / sp.ppc * (1.0 + sp.noise_rel * n0);
+  if (sp.seeded && md.n > 0) {
+    const double x = (h.ix + (h.sx + 0.5) / sp.ppx) * p.dx;
+    const double y = (h.iy + (h.sy + 0.5) / sp.ppy) * p.dy;
+    double m = 1.0;
+    for (int k = 0; k < md.n; ++k) {
+      const double kx = 6.283185307179586476925 * md.mx[k] / p.Lx;
+      const double ky = 6.283185307179586476925 * md.my[k] / p.Ly;
+      m += md.amp[k] * cos(kx * x + ky * y + md.phase[k]);
+    }
+    w *= m;
+  }
+  const double ux = sp.uperp_spread * n1, uy = sp.uperp_spread * n2;
+  const double gam = sp.gamma_b * (1.0 + sp.gamma_spread_rel * n3);
+  b.ox[s] = BR(0);
+  b.oy[s] = BR(0);
+  b.oxi[s] = BR(0);
+  b.ux[s] = BR(ux);
+  b.uy[s] = BR(uy);
+  b.uz[s] = sqrt(gam * gam - 1.0 - ux * ux - uy * uy);
+  b.w[s] = BR(w);
+}
+
+// ------------------------------------------------------------------ deposit
+// Linear-in-xi x CIC deposit of the four source densities of one particle into the source
+// slab [nk][ny][nx][4] (global atomics).
+template <typename BR>
+struct BeamCic {
+  int x0, x1, y0, y1, k0;
+  BR fx, fy, fk;
+};
+
+template <typename BR>
+__device__ __forceinline__ BeamCic<BR> beam_cic(const Home& h, const SpeciesDev& sp, BR ox,
+                                                BR oy, BR oxi, const DevParams& p) {
+  BeamCic<BR> c;
+  const BR lx = (BR(h.sx) + BR(0.5)) / BR(sp.ppx) + ox;
+  const BR ly = (BR(h.sy) + BR(0.5)) / BR(sp.ppy) + oy;
+  const BR lk = (BR(h.sxi) + BR(0.5)) / BR(sp.ppxi) + oxi;
+  const BR fx = floor(lx), fy = floor(ly), fk = floor(lk);
+  c.fx = lx - fx;
+  c.fy = ly - fy;
+  c.fk = lk - fk;
+  const int gx = h.ix + (int)fx, gy = h.iy + (int)fy;
+  c.x0 = wrap(gx, p.nx);
+  c.x1 = wrap(gx + 1, p.nx);
+  c.y0 = wrap(gy, p.ny);
+  c.y1 = wrap(gy + 1, p.ny);
+  c.k0 = sp.k0 + h.kxi + (int)fk;
+  return c;
+}
+
+__device__ __forceinline__ void red4(float* a, float s, float z, float x, float y) {
+  atomicAdd(reinterpret_cast<float4*>(a), make_float4(s, z, x, y));
+}
+__device__ __forceinline__ void red4(double* a, double s, double z, double x, double y) {
+  atomicAdd(a, s);
+  atomicAdd(a + 1, z);
+  atomicAdd(a + 2, x);
+  atomicAdd(a + 3, y);
+}
+
+template <typename BR>
+__device__ __forceinline__ void beam_deposit(BR* src, const BeamCic<BR>& c, const DevParams& p,
+                                             BR s, BR jz, BR jx, BR jy) {
+  const BR gx = BR(1) - c.fx, gy = BR(1) - c.fy, gk = BR(1) - c.fk;
+#pragma unroll
+  for (int dk = 0; dk < 2; ++dk) {
+    const int k = c.k0 + dk;
+    if (k < 0 || k >= p.nk) continue;
+    const BR wk = dk ? c.fk : gk;
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const int y = dy ? c.y1 : c.y0;
+      const BR wy = wk * (dy ? c.fy : gy);
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const int x = dx ? c.x1 : c.x0;
+        const BR wt = wy * (dx ? c.fx : gx);
+        red4(src + (((size_t)k * p.ny + y) * p.nx + x) * 4, wt * s, wt * jz, wt * jx, wt * jy);
+      }
+    }
+  }
+}
+
+// Source densities of one particle: q = Z w/(dx dy dxi); S_b = q (1 - v_z), J = q u/gamma.
+__device__ __forceinline__ void beam_sources(double ux, double uy, double uz, double q,
+                                             double& s, double& jz, double& jx, double& jy) {
+  const double up2 = ux * ux + uy * uy;
+  const double g = sqrt(1.0 + up2 + uz * uz);
+  s = q * (1.0 + up2) / (g * (g + uz));
+  jz = q * uz / g;
+  jx = q * ux / g;
+  jy = q * uy / g;
+}
+__device__ __forceinline__ void beam_sources(float ux, float uy, double uz, float q, float& s,
+                                             float& jz, float& jx, float& jy) {
+  const float up2 = ux * ux + uy * uy;
+  const float uzf = (float)uz;
+  const float d = (1.0f + up2) / (sqrtf(1.0f + up2 + uzf * uzf) + uzf);  // gamma - u_z
+  const float g = uzf + d;
+  const float omv = d / g;                                               // 1 - v_z
+  s = q * omv;
+  jz = q * (1.0f - omv);
+  jx = q * ux / g;
+  jy = q * uy / g;
+}
+
+template <typename BR>
+__global__ void beam_deposit_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp, BR* src) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= b.n) return;
+  const BR w = b.w[s];
+  if (w == BR(0)) return;
+  const Home h = home_of(s, p.nx, p.ny, sp);
+  const BeamCic<BR> c = beam_cic<BR>(h, sp, b.ox[s], b.oy[s], b.oxi[s], p);
+  BR S, JZ, JX, JY;
+  const BR q = BR(sp.Z) * w * BR(1.0 / (p.dx * p.dy * p.dxi));
+  beam_sources(b.ux[s], b.uy[s], b.uz[s], q, S, JZ, JX, JY);
+  beam_deposit(src, c, p, S, JZ, JX, JY);
+}
+
+// ------------------------------------------------------------------ push
+template <typename BR>
+__device__ __forceinline__ void gather_slab(const BR* __restrict__ slab, const BeamCic<BR>& c,
+                                            const DevParams& p, BR F[6]) {
+#pragma unroll
+  for (int f = 0; f < 6; ++f) F[f] = BR(0);
+  const BR gx = BR(1) - c.fx, gy = BR(1) - c.fy, gk = BR(1) - c.fk;
+#pragma unroll
+  for (int dk = 0; dk < 2; ++dk) {
+    const int k = c.k0 + dk;
+    if (k < 0 || k >= p.nk) continue;
+    const BR wk = dk ? c.fk : gk;
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const int y = dy ? c.y1 : c.y0;
+      const BR wy = wk * (dy ? c.fy : gy);
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const int x = dx ? c.x1 : c.x0;
+        const BR wt = wy * (dx ? c.fx : gx);
+        const BR* e = slab + (((size_t)k * p.ny + y) * p.nx + x) * 8;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) F[f] += wt * e[f];
+      }
+    }
+  }
+}
+
+// Relativistic Boris (FP64): half kick h E, rotation t = h B/gamma^-, half kick.
+__device__ __forceinline__ void boris(double& ux, double& uy, double& uz, const double F[6],
+                                      double h) {
+  const double Ex = F[0] + F[4], Ey = F[1] - F[3], Ez = F[2];
+  const double Bx = F[3], By = F[4], Bz = F[5];
+  const double mx = ux + h * Ex, my = uy + h * Ey, mz = uz + h * Ez;
+  const double gm = sqrt(1.0 + mx * mx + my * my + mz * mz);
+  const double tx = h * Bx / gm, ty = h * By / gm, tz = h * Bz / gm;
+  const double px = mx + (my * tz - mz * ty), py = my + (mz * tx - mx * tz),
+               pz = mz + (mx * ty - my * tx);
+  const double s = 2.0 / (1.0 + tx * tx + ty * ty + tz * tz);
+  const double sx = s * tx, sy = s * ty, sz = s * tz;
+  ux = mx + (py * sz - pz * sy) + h * Ex;
+  uy = my + (pz * sx - px * sz) + h * Ey;
+  uz = mz + (px * sy - py * sx) + h * Ez;
+}
+
+// The same Boris step with FP32 transverse arithmetic and FP64 u_z accumulation, written so
+// that no step subtracts nearly equal terms: with W = E_perp - z x B (the slab's first two
+// fields), E_x - v_z B_y = W_x + (1 - v_z) B_y, and 1 - v_z is formed from gamma - u_z =
+// (1 + u_perp^2)/(gamma + u_z).
+__device__ __forceinline__ void boris(float& ux, float& uy, double& uz, const float F[6],
+                                      float h) {
+  const float Wx = F[0], Wy = F[1], Ez = F[2], Bx = F[3], By = F[4], Bz = F[5];
+  const float mx = ux + h * (Wx + By), my = uy + h * (Wy - Bx);
+  const double mz = uz + (double)(h * Ez);
+  const float mzf = (float)mz;
+  const float mp2 = mx * mx + my * my;
+  const float gm = sqrtf(1.0f + mp2 + mzf * mzf);
+  const float dm = (1.0f + mp2) / (gm + mzf);  // gamma^- - m_z
+  const float ig = 1.0f / gm;
+  const float tx = h * Bx * ig, ty = h * By * ig, tz = h * Bz * ig;
+  const float t2 = tx * tx + ty * ty + tz * tz;
+  const float sfac = 2.0f / (1.0f + t2);
+  const float sx = sfac * tx, sy = sfac * ty, sz = sfac * tz;
+  // u' = m + m x t, transverse parts without the m_z t cancellation
+  const float pxp = ux + h * Wx + h * By * dm * ig + my * tz;
+  const float pyp = uy + h * Wy - h * Bx * dm * ig - mx * tz;
+  // eps = 1 - u'_z / (gamma^- (1 + t^2)), u'_z = m_z + m_x t_y - m_y t_x
+  const float eps = (dm + gm * t2 - (mx * ty - my * tx)) * ig / (1.0f + t2);
+  ux = ux + 2.0f * h * Wx + 2.0f * h * By * eps + pyp * sz;
+  uy = uy + 2.0f * h * Wy - 2.0f * h * Bx * eps - pxp * sz;
+  uz = mz + (double)(h * Ez + pxp * sy - pyp * sx);
+}
+
+template <typename BR>
+__global__ void beam_push_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp, const BR* slab,
+                                 BR* src, unsigned long long* lost) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int my_lost = 0;
+  if (s < b.n) {
+    const BR w = b.w[s];
+    if (w != BR(0)) {
+      const Home h = home_of(s, p.nx, p.ny, sp);
+      BR ox = b.ox[s], oy = b.oy[s], oxi = b.oxi[s];
+      const BeamCic<BR> c = beam_cic<BR>(h, sp, ox, oy, oxi, p);
+      BR F[6];
+      gather_slab(slab, c, p, F);
+      BR ux = b.ux[s], uy = b.uy[s];
+      double uz = b.uz[s];
+      boris(ux, uy, uz, F, BR(0.5 * sp.Z * p.dt / sp.M));
+      // positions: dx/dt = u/gamma, dxi/dt = 1 - v_z = (1 + u_perp^2)/(gamma (gamma + u_z))
+      BR g, omv;
+      {
+        const BR up2 = ux * ux + uy * uy;
+        if (sizeof(BR) == 8) {
+          const double gg = sqrt(1.0 + (double)up2 + uz * uz);
+          g = BR(gg);
+          omv = BR((1.0 + (double)up2) / (gg * (gg + uz)));
+        } else {
+          const float uzf = (float)uz;
+          const float d = (1.0f + (float)up2) / (sqrtf(1.0f + (float)up2 + uzf * uzf) + uzf);
+          g = BR(uzf + d);
+          omv = BR(d / (uzf + d));
+        }
+      }
+      ox += BR(p.dt / p.dx) * ux / g;
+      oy += BR(p.dt / p.dy) * uy / g;
+      oxi += BR(p.dt / p.dxi) * omv;
+      b.ox[s] = ox;
+      b.oy[s] = oy;
+      b.oxi[s] = oxi;
+      b.ux[s] = ux;
+      b.uy[s] = uy;
+      b.uz[s] = uz;
+      // lost when xi >= Lxi: home xi cell + local position >= nxi
+      const BR lk = (BR(h.sxi) + BR(0.5)) / BR(sp.ppxi) + oxi;
+      if (lk >= BR(p.nxi - (sp.k0 + h.kxi))) {
+        b.w[s] = BR(0);
+        my_lost = 1;
+      } else {
+        const BeamCic<BR> cn = beam_cic<BR>(h, sp, ox, oy, oxi, p);
+        BR S, JZ, JX, JY;
+        const BR q = BR(sp.Z) * w * BR(1.0 / (p.dx * p.dy * p.dxi));
+        beam_sources(ux, uy, uz, q, S, JZ, JX, JY);
+        beam_deposit(src, cn, p, S, JZ, JX, JY);
+      }
+    }
+  }
+  const int nl = __syncthreads_count(my_lost);
+  if (threadIdx.x == 0 && nl) atomicAdd(lost, (unsigned long long)nl);
+}
+
+// Conversion between host fp64 arrays (canonical id order, absolute positions) and the
+// device layout.
+template <typename BR>
+__global__ void beam_from_host_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp,
+                                      const double* x, const double* y, const double* xi,
+                                      const double* ux, const double* uy, const double* uz,
+                                      const double* w) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= b.n) return;
+  const Home h = home_of(s, p.nx, p.ny, sp);
+  const long long id = h.id;
+  const double hx = h.ix + (h.sx + 0.5) / sp.ppx, hy = h.iy + (h.sy + 0.5) / sp.ppy;
+  const double hk = sp.k0 + h.kxi + (h.sxi + 0.5) / sp.ppxi;
+  // offsets from home, with the periodic image nearest to home
+  double ox = x[id] / p.dx - hx, oy = y[id] / p.dy - hy;
+  ox -= p.nx * rint(ox / p.nx);
+  oy -= p.ny * rint(oy / p.ny);
+  b.ox[s] = BR(ox);
+  b.oy[s] = BR(oy);
+  b.oxi[s] = BR(xi[id] / p.dxi - hk);
+  b.ux[s] = BR(ux[id]);
+  b.uy[s] = BR(uy[id]);
+  b.uz[s] = uz[id];
+  b.w[s] = BR(w[id]);
+}
+
+template <typename BR>
+__global__ void beam_to_host_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp, double* x,
+                                    double* y, double* xi, double* ux, double* uy, double* uz,
+                                    double* w) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= b.n) return;
+  const Home h = home_of(s, p.nx, p.ny, sp);
+  const long long id = h.id;
+  const double hx = h.ix + (h.sx + 0.5) / sp.ppx, hy = h.iy + (h.sy + 0.5) / sp.ppy;
+  const double hk = sp.k0 + h.kxi + (h.sxi + 0.5) / sp.ppxi;
+  double xx = (hx + (double)b.ox[s]) * p.dx, yy = (hy + (double)b.oy[s]) * p.dy;
+  xx -= p.Lx * floor(xx / p.Lx);
+  yy -= p.Ly * floor(yy / p.Ly);
+  x[id] = xx;
+  y[id] = yy;
+  xi[id] = (hk + (double)b.oxi[s]) * p.dxi;
+  ux[id] = (double)b.ux[s];
+  uy[id] = (double)b.uy[s];
+  uz[id] = b.uz[s];
+  w[id] = (double)b.w[s];
+}
+
+}  // namespace qsa

@@ -1,0 +1,208 @@
+// Shared device helpers of the QS-PIC kernels: complex type, device parameters, bounded grid
+// barrier, block reductions, float/double atomics and the Philox-4x32-10 generator.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qsa {
+
+template <typename R>
+struct C {
+  R x, y;
+};
+template <typename R>
+__device__ __forceinline__ C<R> cmk(R a, R b) { return C<R>{a, b}; }
+template <typename R>
+__device__ __forceinline__ C<R> cadd(C<R> a, C<R> b) { return C<R>{a.x + b.x, a.y + b.y}; }
+template <typename R>
+__device__ __forceinline__ C<R> csub(C<R> a, C<R> b) { return C<R>{a.x - b.x, a.y - b.y}; }
+template <typename R>
+__device__ __forceinline__ C<R> cmul(C<R> a, C<R> b) {
+  return C<R>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename R>
+__device__ __forceinline__ C<R> cconj(C<R> a) { return C<R>{a.x, -a.y}; }
+template <typename R>
+__device__ __forceinline__ C<R> cscale(C<R> a, R s) { return C<R>{a.x * s, a.y * s}; }
+// i * a
+template <typename R>
+__device__ __forceinline__ C<R> cmuli(C<R> a) { return C<R>{-a.y, a.x}; }
+
+// Status bits latched in the device status word.
+enum : int { ST_TIMEOUT = 1, ST_NONFINITE = 2, ST_FLOOR = 4 };
+
+// Largest radix plan: n = 2^a 3^b <= 512 needs at most 9 stages.
+constexpr int kMaxStages = 12;
+
+struct FftPlan {
+  int n;
+  int nstages;
+  int radix[kMaxStages];
+};
+
+struct DevParams {
+  int nx, ny, nxi, nk;        // nk = nxi + 1 slices/nodes
+  int nxh;                    // nx/2 + 1 half-spectrum columns
+  int ppx, ppy, ppc, np;      // plasma lattice
+  int n_pc;
+  int nsmem_rows;             // tile rows of the plasma deposit (4)
+  double Lx, Ly, Lxi, dx, dy, dxi, dt;
+  double psi_floor;
+  long long spin_limit;
+  FftPlan px, py;
+};
+
+// ---------------------------------------------------------------------------------------
+// Grid-wide barrier for a cooperative launch.  Sense by generation counter; every wait is
+// bounded by spin_limit polls, after which the status word gets ST_TIMEOUT and the barrier
+// reports failure so that every block leaves the kernel.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+struct Barrier {
+  unsigned* count;
+  unsigned* gen;
+  int* status;
+  long long spin_limit;
+};
+
+// Returns true when every block arrived; false (uniformly for the block) on timeout or when
+// a timeout was already latched.
+__device__ __forceinline__ bool grid_sync(const Barrier& b) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (*((volatile int*)b.status) & ST_TIMEOUT) {
+      ok = 0;
+    } else {
+      unsigned g = ld_acquire_u32(b.gen);
+      __threadfence();
+      unsigned arrived = atomicAdd(b.count, 1u);
+      if (arrived == gridDim.x - 1) {
+        atomicExch(b.count, 0u);
+        __threadfence();
+        st_release_u32(b.gen, g + 1u);
+      } else {
+        long long it = 0;
+        while (ld_acquire_u32(b.gen) == g) {
+          if (++it > b.spin_limit) {
+            atomicOr(b.status, ST_TIMEOUT);
+            ok = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __threadfence();
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------------------
+// Block reductions (blockDim.x a multiple of 32, <= 1024).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_min(T v) {
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// Sum over the block; the result is valid in thread 0.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* scratch /* >= 32 */) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  T r = 0;
+  if (w == 0) {
+    r = (lane < (int)(blockDim.x >> 5)) ? scratch[lane] : T(0);
+    r = warp_sum(r);
+  }
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T* scratch) {
+  v = warp_max(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  T r = v;
+  if (w == 0) {
+    r = (lane < (int)(blockDim.x >> 5)) ? scratch[lane] : scratch[0];
+    r = warp_max(r);
+  }
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ T block_min(T v, T* scratch) {
+  v = warp_min(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  T r = v;
+  if (w == 0) {
+    r = (lane < (int)(blockDim.x >> 5)) ? scratch[lane] : scratch[0];
+    r = warp_min(r);
+  }
+  return r;
+}
+
+// Non-negative doubles order like their bit patterns: max/min through 64-bit integer atomics.
+__device__ __forceinline__ void atomic_max_nonneg(double* p, double v) {
+  atomicMax((unsigned long long*)p, (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ void atomic_min_nonneg(double* p, double v) {
+  atomicMin((unsigned long long*)p, (unsigned long long)__double_as_longlong(v));
+}
+
+// ---------------------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): multipliers 0xD2511F53, 0xCD9E8D57,
+// Weyl key increments 0x9E3779B9, 0xBB67AE85, ten rounds.
+// ---------------------------------------------------------------------------------------
+struct U4 {
+  uint32_t a, b, c, d;
+};
+__device__ __forceinline__ U4 philox4x32_10(U4 ctr, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * ctr.a, hi0 = __umulhi(0xD2511F53u, ctr.a);
+    const uint32_t lo1 = 0xCD9E8D57u * ctr.c, hi1 = __umulhi(0xCD9E8D57u, ctr.c);
+    ctr = U4{hi1 ^ ctr.b ^ k0, lo1, hi0 ^ ctr.d ^ k1, lo0};
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return ctr;
+}
+__device__ __forceinline__ double u01(uint32_t r) { return ((double)r + 0.5) * (1.0 / 4294967296.0); }
+
+// Periodic index helpers.
+__device__ __forceinline__ int wrap(int i, int n) {
+  int r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+}  // namespace qsa

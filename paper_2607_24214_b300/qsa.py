@@ -1,0 +1,270 @@
+"""Python binding of the QS-PIC C ABI (include/qsa.h): argument marshalling only.
+
+Every step of the hot path runs in the CUDA kernels of libqsa.so.  PyTorch supplies device
+memory (its caching allocator, through the ABI's allocator callbacks) and the CUDA stream.
+There is no fallback: if the library is missing or no GPU is present, construction raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import config
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libqsa.so")
+
+QSA_OK = 0
+QSA_ERR_ARG = -1
+QSA_ERR_CUDA = -2
+QSA_ERR_OOM = -3
+QSA_ERR_TIMEOUT = -4
+QSA_ERR_NONFINITE = -5
+QSA_ERR_STATE = -6
+QSA_WARN_PSI_FLOOR = 1
+
+FIELDS = ("Wx", "Wy", "Ez", "Bx", "By", "Bz")   # Wx = E_x - B_y, Wy = E_y + B_x
+SOURCES = ("Sb", "Jz", "Jx", "Jy")
+
+EXPORTS = ("qsa_init", "qsa_set_beam", "qsa_get_beam", "qsa_plasma_sweep", "qsa_beam_step",
+           "qsa_diagnostics", "qsa_copy_field", "qsa_copy_source", "qsa_field_solve",
+           "qsa_launch_count", "qsa_device_bytes", "qsa_last_error", "qsa_destroy")
+
+
+class QsaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"qsa error {code}: {msg}")
+        self.code = code
+
+
+class Species(ct.Structure):
+    _fields_ = [("Z", ct.c_double), ("M", ct.c_double), ("alpha", ct.c_double),
+                ("gamma_b", ct.c_double), ("gamma_spread_rel", ct.c_double),
+                ("uperp_spread", ct.c_double), ("noise_rel", ct.c_double),
+                ("ppc_x", ct.c_int32), ("ppc_y", ct.c_int32), ("ppc_xi", ct.c_int32),
+                ("seeded", ct.c_int32), ("xi_front", ct.c_double), ("xi_back", ct.c_double)]
+
+
+class Mode(ct.Structure):
+    _fields_ = [("mx", ct.c_int32), ("my", ct.c_int32), ("amplitude", ct.c_double),
+                ("phase", ct.c_double)]
+
+
+class ParamsC(ct.Structure):
+    _fields_ = [("nx", ct.c_int32), ("ny", ct.c_int32), ("nxi", ct.c_int32),
+                ("ppc_plasma_x", ct.c_int32), ("ppc_plasma_y", ct.c_int32),
+                ("n_species", ct.c_int32), ("n_modes", ct.c_int32), ("precision", ct.c_int32),
+                ("n_pc_iter", ct.c_int32), ("_reserved", ct.c_int32),
+                ("Lx", ct.c_double), ("Ly", ct.c_double), ("Lxi", ct.c_double),
+                ("dt", ct.c_double), ("psi_floor", ct.c_double), ("seed", ct.c_uint64),
+                ("spin_limit", ct.c_int64), ("species", Species * 4), ("modes", Mode * 16)]
+
+
+_DP = ct.POINTER(ct.c_double)
+
+
+class Diag(ct.Structure):
+    _fields_ = [("energy", _DP), ("psi0", _DP), ("ez0", _DP), ("jz_mean", _DP),
+                ("kappa2", _DP), ("opp_min", _DP), ("n_floor", _DP), ("invariant", _DP),
+                ("charge", _DP), ("pc_residual", _DP), ("beam_lost", ct.c_int64),
+                ("sweeps", ct.c_int64)]
+
+
+ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_void_p)
+FREE_FN = ct.CFUNCTYPE(None, ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_void_p)
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libqsa.so (built by paper_2607_24214_b300.build) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m "
+                          f"paper_2607_24214_b300.build` (nvcc, sm_103a)")
+    lib = ct.CDLL(path)
+    P = ct.c_void_p
+    lib.qsa_init.argtypes = [ct.POINTER(ParamsC), P, ALLOC_FN, FREE_FN, P, ct.POINTER(P)]
+    lib.qsa_init.restype = ct.c_int
+    lib.qsa_set_beam.argtypes = [P, ct.c_int, ct.c_int64] + [_DP] * 7
+    lib.qsa_set_beam.restype = ct.c_int
+    lib.qsa_get_beam.argtypes = [P, ct.c_int, ct.c_int64] + [_DP] * 7 + [ct.POINTER(ct.c_int64)]
+    lib.qsa_get_beam.restype = ct.c_int
+    for name in ("qsa_plasma_sweep", "qsa_beam_step"):
+        getattr(lib, name).argtypes = [P]
+        getattr(lib, name).restype = ct.c_int
+    lib.qsa_diagnostics.argtypes = [P, ct.POINTER(Diag)]
+    lib.qsa_diagnostics.restype = ct.c_int
+    lib.qsa_copy_field.argtypes = [P, ct.c_int, ct.c_int, ct.c_int, _DP]
+    lib.qsa_copy_field.restype = ct.c_int
+    lib.qsa_copy_source.argtypes = [P, ct.c_int, ct.c_int, ct.c_int, _DP]
+    lib.qsa_copy_source.restype = ct.c_int
+    lib.qsa_field_solve.argtypes = [P] + [_DP] * 6 + [ct.c_double, _DP]
+    lib.qsa_field_solve.restype = ct.c_int
+    lib.qsa_launch_count.argtypes = [P]
+    lib.qsa_launch_count.restype = ct.c_int64
+    lib.qsa_device_bytes.argtypes = [P]
+    lib.qsa_device_bytes.restype = ct.c_int64
+    lib.qsa_last_error.argtypes = [P]
+    lib.qsa_last_error.restype = ct.c_char_p
+    lib.qsa_destroy.argtypes = [P]
+    lib.qsa_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def to_c_params(p: config.Params) -> ParamsC:
+    c = ParamsC()
+    c.nx, c.ny, c.nxi = p.nx, p.ny, p.nxi
+    c.ppc_plasma_x, c.ppc_plasma_y = p.ppc_plasma_x, p.ppc_plasma_y
+    c.n_species = len(p.species)
+    c.n_modes = len(p.modes)
+    c.precision = 0 if p.precision == "fp64" else 1
+    c.n_pc_iter = p.n_pc_iter
+    c.Lx, c.Ly, c.Lxi, c.dt = p.Lx, p.Ly, p.Lxi, p.dt
+    c.psi_floor = p.psi_floor
+    c.seed = p.seed
+    c.spin_limit = p.spin_limit
+    for i, s in enumerate(p.species):
+        cs = c.species[i]
+        cs.Z, cs.M, cs.alpha, cs.gamma_b = s.Z, s.M, s.alpha, s.gamma_b
+        cs.gamma_spread_rel, cs.uperp_spread, cs.noise_rel = (s.gamma_spread_rel,
+                                                              s.uperp_spread, s.noise_rel)
+        cs.ppc_x, cs.ppc_y, cs.ppc_xi = s.ppc_x, s.ppc_y, s.ppc_xi
+        cs.seeded = 1 if s.seeded else 0
+        cs.xi_front, cs.xi_back = s.xi_front, s.xi_back
+    for i, m in enumerate(p.modes):
+        c.modes[i].mx, c.modes[i].my = m.mx, m.my
+        c.modes[i].amplitude, c.modes[i].phase = m.amplitude, m.phase
+    return c
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_DP)
+
+
+class QSA:
+    """One QS-PIC instance on the current CUDA device and stream."""
+
+    def __init__(self, p: config.Params, stream=None, torch_allocator: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("QSA needs a CUDA device")
+        self.lib = load_library()
+        self.p = p
+        self.device = torch.cuda.current_device()
+        self._torch_stream = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = ct.c_void_p(self._torch_stream.cuda_stream)
+        if torch_allocator:
+            dev = self.device
+
+            def _alloc(nbytes, ctx, strm):
+                try:
+                    return torch.cuda.caching_allocator_alloc(nbytes, dev, strm)
+                except Exception:
+                    return None
+
+            def _free(ptr, nbytes, ctx, strm):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc = ALLOC_FN(_alloc)
+            self._free = FREE_FN(_free)
+        else:
+            self._alloc = ALLOC_FN()
+            self._free = FREE_FN()
+        self._cp = to_c_params(p)
+        h = ct.c_void_p()
+        rc = self.lib.qsa_init(ct.byref(self._cp), self.stream, self._alloc, self._free, None,
+                               ct.byref(h))
+        if rc != QSA_OK:
+            raise QsaError(rc, self.lib.qsa_last_error(None).decode())
+        self.h = h
+        self.nk = p.nxi + 1
+
+    # -- helpers
+    def _check(self, rc):
+        if rc < 0:
+            raise QsaError(rc, self.lib.qsa_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.qsa_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- the hot path
+    def sweep(self):
+        return self._check(self.lib.qsa_plasma_sweep(self.h))
+
+    def beam_step(self):
+        return self._check(self.lib.qsa_beam_step(self.h))
+
+    # -- data in / out
+    def set_beam(self, si: int, b: dict):
+        arrs = [np.ascontiguousarray(b[k], dtype=np.float64)
+                for k in ("x", "y", "xi", "ux", "uy", "uz", "w")]
+        n = arrs[0].size
+        return self._check(self.lib.qsa_set_beam(self.h, si, n, *[_ptr(a) for a in arrs]))
+
+    def get_beam(self, si: int, n: int) -> dict:
+        keys = ("x", "y", "xi", "ux", "uy", "uz", "w")
+        arrs = [np.empty(n) for _ in keys]
+        nout = ct.c_int64()
+        self._check(self.lib.qsa_get_beam(self.h, si, n, *[_ptr(a) for a in arrs],
+                                          ct.byref(nout)))
+        return dict(zip(keys, arrs))
+
+    def diagnostics(self) -> dict:
+        nk = self.nk
+        out = {k: np.zeros(nk) for k in ("psi0", "ez0", "jz_mean", "kappa2", "opp_min",
+                                          "n_floor", "invariant", "charge", "pc_residual")}
+        out["energy"] = np.zeros((nk, 6))
+        d = Diag()
+        for k, v in out.items():
+            setattr(d, k, _ptr(v))
+        rc = self.lib.qsa_diagnostics(self.h, ct.byref(d))
+        out["status"] = rc
+        out["beam_lost"] = d.beam_lost
+        out["sweeps"] = d.sweeps
+        self._check(rc)
+        return out
+
+    def field(self, f, j0=0, j1=None) -> np.ndarray:
+        j1 = self.nk if j1 is None else j1
+        fi = FIELDS.index(f) if isinstance(f, str) else int(f)
+        out = np.empty((j1 - j0, self.p.ny, self.p.nx))
+        self._check(self.lib.qsa_copy_field(self.h, fi, j0, j1, _ptr(out)))
+        return out
+
+    def slab(self, j0=0, j1=None) -> np.ndarray:
+        """Fields of slices j0..j1-1 as [j, 6, ny, nx] (Wx, Wy, Ez, Bx, By, Bz)."""
+        return np.stack([self.field(f, j0, j1) for f in range(6)], axis=1)
+
+    def source(self, q, j0=0, j1=None) -> np.ndarray:
+        j1 = self.nk if j1 is None else j1
+        qi = SOURCES.index(q) if isinstance(q, str) else int(q)
+        out = np.empty((j1 - j0, self.p.ny, self.p.nx))
+        self._check(self.lib.qsa_copy_source(self.h, qi, j0, j1, _ptr(out)))
+        return out
+
+    def field_solve(self, S, Jx, Jy, Jz, Dx, Dy, kappa2=0.0) -> dict:
+        ins = [np.ascontiguousarray(a, dtype=np.float64) for a in (S, Jx, Jy, Jz, Dx, Dy)]
+        out = np.empty((7, self.p.ny, self.p.nx))
+        self._check(self.lib.qsa_field_solve(self.h, *[_ptr(a) for a in ins], kappa2, _ptr(out)))
+        return dict(zip(("psi", "gpx", "gpy", "Ez", "Bz", "Bx", "By"), out))
+
+    def launch_count(self) -> int:
+        return int(self.lib.qsa_launch_count(self.h))
+
+    def device_bytes(self) -> int:
+        return int(self.lib.qsa_device_bytes(self.h))
