@@ -223,8 +223,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--steps-ref", type=int, default=2)
     ap.add_argument("--warmup-ref", type=int, default=0)
+    ap.add_argument("--nxi", type=int, default=0,
+                    help="override the number of slices (small profiling cases only)")
     args = ap.parse_args()
     p = config.c2_mixed_electron_beam()
+    if args.nxi:
+        p = p.with_(nxi=args.nxi, Lxi=p.dxi * args.nxi)
     rank, world, local = dist_info()
     if world > 1:
         import torch.distributed as dist

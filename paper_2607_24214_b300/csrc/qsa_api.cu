@@ -114,6 +114,8 @@ struct State {
   unsigned* bar = nullptr;  // [0] count, [1] generation
   int* status = nullptr;
   C<R>* tw = nullptr;
+  double* bref = nullptr;          // [nk] beam J_z reference density per node (device)
+  std::vector<double> bref_s, bref_jz;  // host copies of the S_b and J_z references
   size_t smem = 0;
   int grid = 0;
 };
@@ -163,7 +165,8 @@ int setup(qsa_handle* h) {
       !(s->diag = (double*)A((size_t)D_COUNT * dp.nk * sizeof(double))) ||
       !(s->lost = (unsigned long long*)A(sizeof(unsigned long long))) ||
       !(s->bar = (unsigned*)A(2 * sizeof(unsigned))) ||
-      !(s->status = (int*)A(sizeof(int))))
+      !(s->status = (int*)A(sizeof(int))) ||
+      !(s->bref = (double*)A((size_t)dp.nk * sizeof(double))))
     return fail(h, QSA_ERR_OOM, "sweep buffers");
   // twiddles exp(-2 pi i m/n), built in FP64 on the host
   std::vector<C<R>> tw(dp.nx + dp.ny);
@@ -226,12 +229,18 @@ int setup(qsa_handle* h) {
     sp.nkb = (int)std::lround(back / dp.dxi) - sp.k0;
     sp.seeded = q.seeded;
     sp.index = si;
+    sp.wbar = q.alpha * dp.dx * dp.dy * dp.dxi / sp.ppc;
+    sp.qbar = q.Z * q.alpha / sp.ppc;
+    {
+      const double uzb = std::sqrt(q.gamma_b * q.gamma_b - 1.0);
+      sp.omvbar = 1.0 / (q.gamma_b * (q.gamma_b + uzb));
+    }
     BeamArrays<R> b{};
     b.n = (long long)dp.nx * dp.ny * sp.nkb * sp.ppc;
     const size_t n = (size_t)b.n;
     if (!(b.ox = (R*)A(n * sizeof(R))) || !(b.oy = (R*)A(n * sizeof(R))) ||
         !(b.oxi = (R*)A(n * sizeof(R))) || !(b.ux = (R*)A(n * sizeof(R))) ||
-        !(b.uy = (R*)A(n * sizeof(R))) || !(b.w = (R*)A(n * sizeof(R))) ||
+        !(b.uy = (R*)A(n * sizeof(R))) || !(b.dw = (R*)A(n * sizeof(R))) ||
         !(b.uz = (double*)A(n * sizeof(double))))
       return fail(h, QSA_ERR_OOM, "beam arrays");
     s->species.push_back(sp);
@@ -243,6 +252,24 @@ int setup(qsa_handle* h) {
       CK(cudaGetLastError());
     }
   }
+  // uniform reference of the beam sources per node (k = 0 only): Z alpha (1 - v_z) and
+  // Z alpha v_z of the reference momentum, times the lattice fill of the node (1 inside the
+  // beam, 1/2 on its first and last node)
+  s->bref_s.assign(dp.nk, 0.0);
+  s->bref_jz.assign(dp.nk, 0.0);
+  for (size_t si = 0; si < s->species.size(); ++si) {
+    const SpeciesDev& sp = s->species[si];
+    if (sp.nkb < 1) continue;
+    for (int k = sp.k0; k <= sp.k0 + sp.nkb && k < dp.nk; ++k) {
+      const double e = (k == sp.k0 || k == sp.k0 + sp.nkb) ? 0.5 : 1.0;
+      const double rho = sp.Z * P.species[si].alpha * e;
+      s->bref_s[k] += rho * sp.omvbar;
+      s->bref_jz[k] += rho * (1.0 - sp.omvbar);
+    }
+  }
+  CK(cudaMemcpyAsync(s->bref, s->bref_jz.data(), dp.nk * sizeof(double), cudaMemcpyHostToDevice,
+                     h->stream));
+  a.bref = s->bref;
   CK(cudaStreamSynchronize(h->stream));
   return QSA_OK;
 }
@@ -351,7 +378,6 @@ int diagnostics(qsa_handle* h, qsa_diag* out) {
   CK(cudaStreamSynchronize(h->stream));
   auto row = [&](int r) { return d.data() + (size_t)r * nk; };
   const double npc = (double)h->dp.ppc * h->dp.nx * h->dp.ny;
-  const double area = h->prm.Lx * h->prm.Ly;
   for (int j = 0; j < nk; ++j) {
     if (out->energy)
       for (int f = 0; f < 6; ++f) out->energy[(size_t)j * 6 + f] = row(D_E0 + f)[j];
@@ -362,7 +388,7 @@ int diagnostics(qsa_handle* h, qsa_diag* out) {
     if (out->opp_min) out->opp_min[j] = key_to_double(row(D_OPPMIN)[j]);
     if (out->n_floor) out->n_floor[j] = row(D_NFLOOR)[j];
     if (out->invariant) out->invariant[j] = row(D_INV)[j];
-    if (out->charge) out->charge[j] = std::fabs(row(D_CHARGE)[j] + area);
+    if (out->charge) out->charge[j] = std::fabs(row(D_CHARGE)[j]);
     if (out->pc_residual) {
       const double den = row(D_PCDEN)[j];
       out->pc_residual[j] = den > 0 ? std::sqrt(row(D_PCNUM)[j] / den) : 0.0;
@@ -388,6 +414,11 @@ int copy_field(qsa_handle* h, int field, int j0, int j1, double* out, bool sourc
                      h->stream));
   CK(cudaStreamSynchronize(h->stream));
   for (size_t i = 0; i < (size_t)(j1 - j0) * g; ++i) out[i] = (double)tmp[i * stride + field];
+  if (source && (field == 0 || field == 1)) {  // add the uniform reference left out of the slab
+    const std::vector<double>& ref = field == 0 ? s->bref_s : s->bref_jz;
+    for (int j = j0; j < j1; ++j)
+      for (size_t i = 0; i < g; ++i) out[(size_t)(j - j0) * g + i] += ref[j];
+  }
   return QSA_OK;
 }
 
@@ -514,7 +545,7 @@ int validate(const qsa_params* p, std::string& why) {
   const double dxi = p->Lxi / p->nxi;
   for (int s = 0; s < p->n_species; ++s) {
     const qsa_species& q = p->species[s];
-    if (!(q.M > 0) || !(q.gamma_b >= 1) || q.alpha < 0) return bad("species Z/M/gamma/alpha");
+    if (!(q.M > 0) || !(q.gamma_b >= 1) || !(q.alpha > 0)) return bad("species M/gamma/alpha");
     if (q.ppc_x < 1 || q.ppc_y < 1 || q.ppc_xi < 1) return bad("species ppc must be >= 1");
     const double back = q.xi_back < 0 ? p->Lxi : q.xi_back;
     if (q.xi_front < 0 || back > p->Lxi * (1 + 1e-12) || back <= q.xi_front)

@@ -6,6 +6,11 @@
 // neighbouring cells of one sub-lattice position).  Positions are offsets, in cells, from
 // the particle's lattice home; this keeps the slow transverse and longitudinal drifts of an
 // ultrarelativistic beam (1e-6 cells per step) exact in FP32.  u_z is FP64 in both paths.
+// The weight is stored as its relative deviation dw = w / wbar - 1 from the species' nominal
+// weight wbar = alpha dx dy dxi / ppc (dw = -1 marks a lost particle), and the beam sources
+// are deposited as deviations from the reference beam (nominal weight, at home, u = (0, 0,
+// sqrt(gamma_b^2 - 1))): the reference is uniform in x, y (k = 0 only) and is kept in FP64
+// per node, so FP32 sums keep the 1e-4 density noise of the fluctuations.
 #pragma once
 #include "qsa_common.cuh"
 
@@ -13,13 +18,16 @@ namespace qsa {
 
 template <typename BR>
 struct BeamArrays {
-  BR *ox, *oy, *oxi, *ux, *uy, *w;
+  BR *ox, *oy, *oxi, *ux, *uy, *dw;
   double* uz;
   long long n;
 };
 
 struct SpeciesDev {
   double Z, M, alpha, gamma_b, gamma_spread_rel, uperp_spread, noise_rel;
+  double wbar;   // nominal weight alpha dx dy dxi / ppc
+  double qbar;   // Z wbar / (dx dy dxi): reference density per particle
+  double omvbar; // 1 - v_z of the reference momentum
   int ppx, ppy, ppxi, ppc;
   int k0, nkb;  // first xi cell and number of xi cells
   int seeded, index;
@@ -66,18 +74,18 @@ __global__ void beam_init_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp, M
   sincospi(2.0 * u01(r.b), &s1, &c1);
   sincospi(2.0 * u01(r.d), &s3, &c3);
   const double n0 = a0 * c1, n1 = a0 * s1, n2 = a1 * c3, n3 = a1 * s3;
-  double w = sp.alpha * p.dx * p.dy * p.dxi / sp.ppc * (1.0 + sp.noise_rel * n0);
+  // w / wbar = (1 + noise n0) * (1 + sum_m a_m cos(k_m . x + phi_m)), stored minus one
+  double mm = 0.0;  // mode factor minus one
   if (sp.seeded && md.n > 0) {
     const double x = (h.ix + (h.sx + 0.5) / sp.ppx) * p.dx;
     const double y = (h.iy + (h.sy + 0.5) / sp.ppy) * p.dy;
-    double m = 1.0;
     for (int k = 0; k < md.n; ++k) {
       const double kx = 6.283185307179586476925 * md.mx[k] / p.Lx;
       const double ky = 6.283185307179586476925 * md.my[k] / p.Ly;
-      m += md.amp[k] * cos(kx * x + ky * y + md.phase[k]);
+      mm += md.amp[k] * cos(kx * x + ky * y + md.phase[k]);
     }
-    w *= m;
   }
+  const double dw = mm + sp.noise_rel * n0 * (1.0 + mm);
   const double ux = sp.uperp_spread * n1, uy = sp.uperp_spread * n2;
   const double gam = sp.gamma_b * (1.0 + sp.gamma_spread_rel * n3);
   b.ox[s] = BR(0);
@@ -86,7 +94,7 @@ __global__ void beam_init_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp, M
   b.ux[s] = BR(ux);
   b.uy[s] = BR(uy);
   b.uz[s] = sqrt(gam * gam - 1.0 - ux * ux - uy * uy);
-  b.w[s] = BR(w);
+  b.dw[s] = BR(dw);
 }
 
 // ------------------------------------------------------------------ deposit
@@ -128,48 +136,100 @@ __device__ __forceinline__ void red4(double* a, double s, double z, double x, do
   atomicAdd(a + 3, y);
 }
 
+// Deposit, per source quantity, dev W(x) + ref (W(x) - W(home)) (ref = 0 for J_x, J_y).  In
+// the home cell the trilinear weight differences come from the offsets without cancellation.
 template <typename BR>
-__device__ __forceinline__ void beam_deposit(BR* src, const BeamCic<BR>& c, const DevParams& p,
-                                             BR s, BR jz, BR jx, BR jy) {
-  const BR gx = BR(1) - c.fx, gy = BR(1) - c.fy, gk = BR(1) - c.fk;
+__device__ __forceinline__ void beam_deposit(BR* src, const Home& h, const SpeciesDev& sp, BR ox,
+                                             BR oy, BR oxi, const DevParams& p, BR dS, BR dJz,
+                                             BR jx, BR jy, BR refS, BR refJz) {
+  const BR hx = (BR(h.sx) + BR(0.5)) / BR(sp.ppx);
+  const BR hy = (BR(h.sy) + BR(0.5)) / BR(sp.ppy);
+  const BR hk = (BR(h.sxi) + BR(0.5)) / BR(sp.ppxi);
+  const BR lx = hx + ox, ly = hy + oy, lk = hk + oxi;
+  const bool home = lx >= BR(0) && lx < BR(1) && ly >= BR(0) && ly < BR(1) && lk >= BR(0) &&
+                    lk < BR(1);
+  if (home) {
+    const int k0 = sp.k0 + h.kxi;
+    const int x1 = (h.ix + 1 == p.nx) ? 0 : h.ix + 1, y1 = (h.iy + 1 == p.ny) ? 0 : h.iy + 1;
 #pragma unroll
-  for (int dk = 0; dk < 2; ++dk) {
-    const int k = c.k0 + dk;
-    if (k < 0 || k >= p.nk) continue;
-    const BR wk = dk ? c.fk : gk;
+    for (int ck = 0; ck < 2; ++ck) {
+      const int k = k0 + ck;
+      if (k >= p.nk) continue;
+      const BR a3 = ck ? hk : BR(1) - hk, d3 = ck ? oxi : -oxi;
 #pragma unroll
-    for (int dy = 0; dy < 2; ++dy) {
-      const int y = dy ? c.y1 : c.y0;
-      const BR wy = wk * (dy ? c.fy : gy);
+      for (int cy = 0; cy < 2; ++cy) {
+        const BR a2 = cy ? hy : BR(1) - hy, d2 = cy ? oy : -oy;
 #pragma unroll
-      for (int dx = 0; dx < 2; ++dx) {
-        const int x = dx ? c.x1 : c.x0;
-        const BR wt = wy * (dx ? c.fx : gx);
-        red4(src + (((size_t)k * p.ny + y) * p.nx + x) * 4, wt * s, wt * jz, wt * jx, wt * jy);
+        for (int cx = 0; cx < 2; ++cx) {
+          const BR a1 = cx ? hx : BR(1) - hx, d1 = cx ? ox : -ox;
+          const BR w = (a1 + d1) * (a2 + d2) * (a3 + d3);
+          const BR dW = d1 * a2 * a3 + a1 * d2 * a3 + a1 * a2 * d3 + d1 * d2 * a3 +
+                        d1 * a2 * d3 + a1 * d2 * d3 + d1 * d2 * d3;
+          const int y = cy ? y1 : h.iy, x = cx ? x1 : h.ix;
+          red4(src + (((size_t)k * p.ny + y) * p.nx + x) * 4, dS * w + refS * dW,
+               dJz * w + refJz * dW, jx * w, jy * w);
+        }
+      }
+    }
+    return;
+  }
+  // left the home cell: full weights at the new corners, minus the reference at home
+  const BeamCic<BR> c = beam_cic<BR>(h, sp, ox, oy, oxi, p);
+  const BeamCic<BR> o = beam_cic<BR>(h, sp, BR(0), BR(0), BR(0), p);
+#pragma unroll
+  for (int pass = 0; pass < 2; ++pass) {
+    const BeamCic<BR>& e = pass ? o : c;
+    const BR s0 = pass ? -refS : dS + refS, z0 = pass ? -refJz : dJz + refJz;
+    const BR x0v = pass ? BR(0) : jx, y0v = pass ? BR(0) : jy;
+    const BR gx = BR(1) - e.fx, gy = BR(1) - e.fy, gk = BR(1) - e.fk;
+#pragma unroll
+    for (int dk = 0; dk < 2; ++dk) {
+      const int k = e.k0 + dk;
+      if (k < 0 || k >= p.nk) continue;
+      const BR wk = dk ? e.fk : gk;
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const int y = dy ? e.y1 : e.y0;
+        const BR wy = wk * (dy ? e.fy : gy);
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+          const int x = dx ? e.x1 : e.x0;
+          const BR wt = wy * (dx ? e.fx : gx);
+          red4(src + (((size_t)k * p.ny + y) * p.nx + x) * 4, wt * s0, wt * z0, wt * x0v,
+               wt * y0v);
+        }
       }
     }
   }
 }
 
-// Source densities of one particle: q = Z w/(dx dy dxi); S_b = q (1 - v_z), J = q u/gamma.
-__device__ __forceinline__ void beam_sources(double ux, double uy, double uz, double q,
-                                             double& s, double& jz, double& jx, double& jy) {
+// Source deviations of one particle with q = qbar (1 + dw): dS = q(1 - v_z) - qbar omvbar,
+// dJz = q v_z - qbar (1 - omvbar); J_perp = q u_perp/gamma (reference zero).
+__device__ __forceinline__ void beam_sources(double ux, double uy, double uz, double dw,
+                                             const SpeciesDev& sp, double& dS, double& dJz,
+                                             double& jx, double& jy) {
   const double up2 = ux * ux + uy * uy;
   const double g = sqrt(1.0 + up2 + uz * uz);
-  s = q * (1.0 + up2) / (g * (g + uz));
-  jz = q * uz / g;
+  const double omv = (1.0 + up2) / (g * (g + uz));
+  const double q = sp.qbar * (1.0 + dw);
+  dS = sp.qbar * (dw * omv + (omv - sp.omvbar));
+  dJz = sp.qbar * (dw * (1.0 - omv) - (omv - sp.omvbar));
   jx = q * ux / g;
   jy = q * uy / g;
 }
-__device__ __forceinline__ void beam_sources(float ux, float uy, double uz, float q, float& s,
-                                             float& jz, float& jx, float& jy) {
+__device__ __forceinline__ void beam_sources(float ux, float uy, double uz, float dw,
+                                             const SpeciesDev& sp, float& dS, float& dJz,
+                                             float& jx, float& jy) {
   const float up2 = ux * ux + uy * uy;
   const float uzf = (float)uz;
   const float d = (1.0f + up2) / (sqrtf(1.0f + up2 + uzf * uzf) + uzf);  // gamma - u_z
   const float g = uzf + d;
   const float omv = d / g;                                               // 1 - v_z
-  s = q * omv;
-  jz = q * (1.0f - omv);
+  const float qb = (float)sp.qbar;
+  const float domv = omv - (float)sp.omvbar;
+  dS = qb * (dw * omv + domv);
+  dJz = qb * (dw * (1.0f - omv) - domv);
+  const float q = qb * (1.0f + dw);
   jx = q * ux / g;
   jy = q * uy / g;
 }
@@ -178,14 +238,16 @@ template <typename BR>
 __global__ void beam_deposit_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp, BR* src) {
   const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= b.n) return;
-  const BR w = b.w[s];
-  if (w == BR(0)) return;
+  const BR dw = b.dw[s];
   const Home h = home_of(s, p.nx, p.ny, sp);
-  const BeamCic<BR> c = beam_cic<BR>(h, sp, b.ox[s], b.oy[s], b.oxi[s], p);
-  BR S, JZ, JX, JY;
-  const BR q = BR(sp.Z) * w * BR(1.0 / (p.dx * p.dy * p.dxi));
-  beam_sources(b.ux[s], b.uy[s], b.uz[s], q, S, JZ, JX, JY);
-  beam_deposit(src, c, p, S, JZ, JX, JY);
+  const BR refS = BR(sp.qbar * sp.omvbar), refJz = BR(sp.qbar * (1.0 - sp.omvbar));
+  if (dw == BR(-1)) {  // lost: only the reference is removed (it sits at home)
+    beam_deposit(src, h, sp, BR(0), BR(0), BR(0), p, -refS, -refJz, BR(0), BR(0), refS, refJz);
+    return;
+  }
+  BR dS, dJz, JX, JY;
+  beam_sources(b.ux[s], b.uy[s], b.uz[s], dw, sp, dS, dJz, JX, JY);
+  beam_deposit(src, h, sp, b.ox[s], b.oy[s], b.oxi[s], p, dS, dJz, JX, JY, refS, refJz);
 }
 
 // ------------------------------------------------------------------ push
@@ -267,9 +329,12 @@ __global__ void beam_push_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp, c
   const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int my_lost = 0;
   if (s < b.n) {
-    const BR w = b.w[s];
-    if (w != BR(0)) {
-      const Home h = home_of(s, p.nx, p.ny, sp);
+    const BR dw = b.dw[s];
+    const Home h = home_of(s, p.nx, p.ny, sp);
+    const BR refS = BR(sp.qbar * sp.omvbar), refJz = BR(sp.qbar * (1.0 - sp.omvbar));
+    if (dw == BR(-1)) {
+      beam_deposit(src, h, sp, BR(0), BR(0), BR(0), p, -refS, -refJz, BR(0), BR(0), refS, refJz);
+    } else {
       BR ox = b.ox[s], oy = b.oy[s], oxi = b.oxi[s];
       const BeamCic<BR> c = beam_cic<BR>(h, sp, ox, oy, oxi, p);
       BR F[6];
@@ -304,14 +369,14 @@ __global__ void beam_push_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp, c
       // lost when xi >= Lxi: home xi cell + local position >= nxi
       const BR lk = (BR(h.sxi) + BR(0.5)) / BR(sp.ppxi) + oxi;
       if (lk >= BR(p.nxi - (sp.k0 + h.kxi))) {
-        b.w[s] = BR(0);
+        b.dw[s] = BR(-1);
         my_lost = 1;
+        beam_deposit(src, h, sp, BR(0), BR(0), BR(0), p, -refS, -refJz, BR(0), BR(0), refS,
+                     refJz);
       } else {
-        const BeamCic<BR> cn = beam_cic<BR>(h, sp, ox, oy, oxi, p);
-        BR S, JZ, JX, JY;
-        const BR q = BR(sp.Z) * w * BR(1.0 / (p.dx * p.dy * p.dxi));
-        beam_sources(ux, uy, uz, q, S, JZ, JX, JY);
-        beam_deposit(src, cn, p, S, JZ, JX, JY);
+        BR dS, dJz, JX, JY;
+        beam_sources(ux, uy, uz, dw, sp, dS, dJz, JX, JY);
+        beam_deposit(src, h, sp, ox, oy, oxi, p, dS, dJz, JX, JY, refS, refJz);
       }
     }
   }
@@ -342,7 +407,7 @@ __global__ void beam_from_host_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev 
   b.ux[s] = BR(ux[id]);
   b.uy[s] = BR(uy[id]);
   b.uz[s] = uz[id];
-  b.w[s] = BR(w[id]);
+  b.dw[s] = (w[id] == 0.0) ? BR(-1) : BR(w[id] / sp.wbar - 1.0);
 }
 
 template <typename BR>
@@ -364,7 +429,7 @@ __global__ void beam_to_host_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp
   ux[id] = (double)b.ux[s];
   uy[id] = (double)b.uy[s];
   uz[id] = b.uz[s];
-  w[id] = (double)b.w[s];
+  w[id] = (b.dw[s] == BR(-1)) ? 0.0 : sp.wbar * (1.0 + (double)b.dw[s]);
 }
 
 }  // namespace qsa

@@ -65,6 +65,7 @@ struct SweepArgs {
   const R* src;                             // [nk][ny][nx][4] beam S_b, J_z, J_x, J_y
   R* slab;                                  // [nk][ny][nx][8]
   double* diag;                             // [D_COUNT][nk]
+  const double* bref;                       // [nk] beam J_z reference density per node
   Barrier bar;
 };
 
@@ -122,6 +123,39 @@ __device__ __forceinline__ void deposit(R* tile, R* ovf, const Cic<R>& c, int f,
   }
 }
 
+// Deposit v_dev W(x) + v_ref (W(x) - W(home)) for a particle of home cell (ix, crow), home
+// sub-cell position (hx, hy) and offset (ox, oy) in cells.  v_ref W(home), summed over the
+// quiet lattice, is uniform (k = 0 only) and is carried analytically by the caller; keeping
+// it out of the grid sums lets FP32 accumulation resolve the fluctuations.  While the
+// particle is in its home cell the weight differences are formed from the offsets without
+// cancellation.
+template <typename R>
+__device__ __forceinline__ void deposit_ref(R* tile, R* ovf, int ix, int crow, R hx, R hy, R ox,
+                                            R oy, int f, int nf, int nx, int ny, R v_dev,
+                                            R v_ref) {
+  const R lx = hx + ox, ly = hy + oy;
+  if (lx >= R(0) && lx < R(1) && ly >= R(0) && ly < R(1)) {
+    const R ax = R(1) - hx, ay = R(1) - hy;
+    const R oxy = ox * oy;
+    const R d00 = -ox * ay - oy * ax + oxy, d01 = ox * ay - hx * oy - oxy;
+    const R d10 = ax * oy - ox * hy - oxy, d11 = hx * oy + ox * hy + oxy;
+    const R w00 = (ax - ox) * (ay - oy), w01 = lx * (ay - oy), w10 = (ax - ox) * ly,
+            w11 = lx * ly;
+    const int x0 = ix, x1 = (ix + 1 == nx) ? 0 : ix + 1;
+    R* r0 = tile + (size_t)1 * nx * nf;  // home row crow is tile row 1
+    R* r1 = r0 + (size_t)nx * nf;
+    atomicAdd(r0 + x0 * nf + f, v_dev * w00 + v_ref * d00);
+    atomicAdd(r0 + x1 * nf + f, v_dev * w01 + v_ref * d01);
+    atomicAdd(r1 + x0 * nf + f, v_dev * w10 + v_ref * d10);
+    atomicAdd(r1 + x1 * nf + f, v_dev * w11 + v_ref * d11);
+  } else {
+    const Cic<R> c = cic<R>(ix, crow, lx, ly, nx, ny, crow);
+    deposit(tile, ovf, c, f, nf, nx, v_dev + v_ref);
+    const Cic<R> h = cic<R>(ix, crow, hx, hy, nx, ny, crow);
+    deposit(tile, ovf, h, f, nf, nx, -v_ref);
+  }
+}
+
 // gamma/(1+psi) from the quasistatic invariant gamma - u_z = 1 + psi.
 template <typename R>
 __device__ __forceinline__ R g_over_opp(R ux, R uy, R opp) {
@@ -152,6 +186,11 @@ enum DepMode : int { DEP_INIT = 0, DEP_TRIAL = 1, DEP_COMMIT = 2 };
 template <typename R>
 __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, double psi0,
                           bool first, bool last) {
+  // reference state of the deposits: a particle at rest at its lattice home with psi = psi0
+  // carries rho - J_z = -w and u_z/(1+psi) = c0 = -psi0 (2 + psi0) / (2 (1+psi0)^2)
+  const double opp0d = 1.0 + psi0;
+  const R opp0 = R(opp0d);
+  const R c0 = R(-psi0 * (2.0 + psi0) / (2.0 * opp0d * opp0d));
   const DevParams& p = a.p;
   const int nx = p.nx, ny = p.ny;
   const int nf = (mode == DEP_TRIAL) ? kNF : 3;
@@ -174,21 +213,20 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
       const int sub = t / nx, ix = t - sub * nx;
       const int sx = sub % p.ppx, sy = sub / p.ppx;
       const R hx = (R(sx) + R(0.5)) / R(p.ppx), hy = (R(sy) + R(0.5)) / R(p.ppy);
-      if (mode == DEP_INIT) {
+      if (mode == DEP_INIT) {  // at home: rho - J_z equals its reference, nothing to add
         a.pox[i] = R(0);
         a.poy[i] = R(0);
         a.pux[i] = R(0);
         a.puy[i] = R(0);
         a.ppsi[i] = R(0);
-        Cic<R> c = cic<R>(ix, crow, hx, hy, nx, ny, crow);
-        deposit(tile, a.ovf, c, 0, nf, nx, -wn);
         continue;
       }
       const R ox = a.pox[i], oy = a.poy[i];
       R ux = a.pux[i], uy = a.puy[i];
       const R pprev = a.ppsi[i];
       const Cic<R> c = cic<R>(ix, crow, hx + ox, hy + oy, nx, ny, crow);
-      const R psi_p = R(psi0 + (double)gather(a.psi, c, nx));
+      const R psi_fl = gather(a.psi, c, nx);
+      const R psi_p = R(psi0 + (double)psi_fl);
       const R gxp = gather(a.gpx, c, nx), gyp = gather(a.gpy, c, nx);
       const R bxp = gather(a.bx, c, nx), byp = gather(a.by, c, nx), bzp = gather(a.bz, c, nx);
       const R opp_raw = R(1) + psi_p;
@@ -208,9 +246,14 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
         // u_z from gamma - u_z = 1 + psi without cancellation: (u^2 - psi (2 + psi)) / (2(1+psi))
         const R uzj = (u2 - pe * (R(2) + pe)) / (R(2) * opp);
         const R q = -wn / opp;
+        // u_z/(1+psi) - c0 = u^2/(2 opp^2) + (1/opp^2 - 1/opp0^2)/2, the second term formed
+        // from the psi fluctuation opp - opp0 without cancellation
+        const R dpsi = (opp_raw < floor_) ? R((double)floor_ - opp0d) : psi_fl;
+        const R iop2 = R(1) / (opp * opp);
+        const R dz = R(0.5) * u2 * iop2 - R(0.5) * dpsi * (opp0 + opp) * iop2 / (opp0 * opp0);
         deposit(tile, a.ovf, c, 0, nf, nx, q * uxj);
         deposit(tile, a.ovf, c, 1, nf, nx, q * uyj);
-        deposit(tile, a.ovf, c, 2, nf, nx, q * uzj);
+        deposit_ref(tile, a.ovf, ix, crow, hx, hy, ox, oy, 2, nf, nx, ny, -wn * dz, -wn * c0);
         deposit(tile, a.ovf, ch, 3, nf, nx, jxh);
         deposit(tile, a.ovf, ch, 4, nf, nx, jyh);
         if (first) {
@@ -229,9 +272,8 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
         a.pux[i] = ux;
         a.puy[i] = uy;
         a.ppsi[i] = psi_p;
-        const Cic<R> cn = cic<R>(ix, crow, hx + ox + sf * ux * idx, hy + oy + sf * uy * idy, nx,
-                                 ny, crow);
-        deposit(tile, a.ovf, cn, 0, nf, nx, -wn);
+        deposit_ref(tile, a.ovf, ix, crow, hx, hy, ox + sf * ux * idx, oy + sf * uy * idy, 0, nf,
+                    nx, ny, R(0), -wn);
         deposit(tile, a.ovf, ch, 1, nf, nx, jxh);
         deposit(tile, a.ovf, ch, 2, nf, nx, jyh);
       }
@@ -353,8 +395,10 @@ __device__ __forceinline__ Kv kvec(const DevParams& p, int kx, int ky) {
 }
 
 // ------------------------------------------------------------------ column phase: B, E_z
+// jz_ref: the uniform parts of J_z left out of the grid deposits (plasma reference state and
+// beam reference density), added to <J_z> for the k = 0 mode.
 template <typename R>
-__device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, int j, bool last) {
+__device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, int j, bool last, double jz_ref) {
   const DevParams& p = a.p;
   const int ny = p.ny, nxh = p.nxh;
   C<R>* A = buf;
@@ -377,7 +421,8 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, int j, bool last) 
       const C<R> Jx = Z[ky], Jy = Z[ny + ky], Jz = Z[2 * ny + ky];
       const C<R> Jxh = Z[3 * ny + ky], Jyh = Z[4 * ny + ky];
       const size_t ix0 = (size_t)kx * ny + ky, ix1 = ((size_t)nxh + kx) * ny + ky;
-      if (kx == 0 && ky == 0) a.diag[D_JZ * p.nk + j] = (double)Jz.x / ((double)p.nx * p.ny);
+      if (kx == 0 && ky == 0)
+        a.diag[D_JZ * p.nk + j] = (double)Jz.x / ((double)p.nx * p.ny) + jz_ref;
       const Kv k = kvec(p, kx, ky);
       C<R> obx{0, 0}, oby{0, 0}, obz{0, 0}, oez{0, 0};
       if (k.k2 > 0.0) {
@@ -568,13 +613,15 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<R> a) {
 
   for (int j = 0; j < p.nk; ++j) {
     double ez0n = ez0h, ez0j = ez0h;
+    const double opp0 = 1.0 + psi0;
+    const double jz_ref = psi0 * (2.0 + psi0) / (2.0 * opp0 * opp0) + (a.bref ? a.bref[j] : 0.0);
     for (int it = 0; it < p.n_pc; ++it) {
       const bool first = (it == 0), last = (it == p.n_pc - 1);
       dep_phase(a, tile, DEP_TRIAL, j, psi0, first, last);
       if (!grid_sync(a.bar)) return;
       row_phase(a, buf, DEP_TRIAL, j);
       if (!grid_sync(a.bar)) return;
-      col_phase_b(a, buf, j, last);
+      col_phase_b(a, buf, j, last, jz_ref);
       if (!grid_sync(a.bar)) return;
       if (last) {
         const double jz = *((volatile double*)&a.diag[D_JZ * p.nk + j]);
@@ -613,7 +660,7 @@ __global__ void __launch_bounds__(256) solve_kernel(SweepArgs<R> a, int which) {
   if (which == 0) {
     row_phase(a, buf, DEP_TRIAL, 0);
     if (!grid_sync(a.bar)) return;
-    col_phase_b(a, buf, 0, false);
+    col_phase_b(a, buf, 0, false, 0.0);
     if (!grid_sync(a.bar)) return;
     irow_phase(a, buf, false, 0, false, 0.0);
   } else {
