@@ -166,6 +166,13 @@ int qsa_field_solve(qsa_handle* h, const double* S, const double* Jx, const doub
                     const double* Jz, const double* Dx, const double* Dy, double kappa2,
                     double* out);
 
+/* Phase timing of the last sweep (tracing): out[(j * 32 + ph) * 2 + 0] is the device
+ * globaltimer (ns) when the last block arrived at the barrier closing phase ph of slice j,
+ * out[... + 1] when block 0 left it, for slices j < 8 and phases ph < 32 (trial iteration it,
+ * step k in {deposit, row FFT, column FFT + solve, inverse row FFT}: ph = 4 it + k; commit:
+ * ph = 4 n_pc_iter + k).  Zero where not recorded.  cap >= 512.  Synchronises. */
+int qsa_phase_times(qsa_handle* h, int64_t* out, int cap);
+
 /* Kernel launches made by this handle since qsa_init (for launch accounting). */
 int64_t qsa_launch_count(const qsa_handle* h);
 

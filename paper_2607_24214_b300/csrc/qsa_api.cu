@@ -115,6 +115,8 @@ struct State {
   int* status = nullptr;
   C<R>* tw = nullptr;
   double* bref = nullptr;          // [nk] beam J_z reference density per node (device)
+  unsigned long long* ptimes = nullptr;  // phase timestamps of the first slices
+  R* ktab = nullptr;                     // wavenumber table of the k-space solves
   std::vector<double> bref_s, bref_jz;  // host copies of the S_b and J_z references
   size_t smem = 0;
   int grid = 0;
@@ -131,11 +133,7 @@ State<R>* S(qsa_handle* h) { return reinterpret_cast<State<R>*>(h->st); }
 
 template <typename R>
 size_t sweep_smem(const DevParams& dp) {
-  size_t tile = (size_t)kTileRows * dp.nx * kNF * sizeof(R);
-  size_t row = (size_t)2 * 3 * dp.nx * sizeof(C<R>);
-  size_t col = (size_t)2 * kNF * dp.ny * sizeof(C<R>);
-  size_t m = tile > row ? tile : row;
-  return m > col ? m : col;
+  return sweep_smem_bytes<R>(dp.nx, dp.ny);
 }
 
 template <typename R>
@@ -151,8 +149,7 @@ int setup(qsa_handle* h) {
   const size_t np = (size_t)dp.np;
   R** pl[5] = {&a.pox, &a.poy, &a.pux, &a.puy, &a.ppsi};
   for (auto p : pl) if (!(*p = (R*)A(np * sizeof(R)))) return fail(h, QSA_ERR_OOM, "plasma");
-  R** gr[7] = {&a.psi, &a.gpx, &a.gpy, &a.bx, &a.by, &a.bz, &a.ez};
-  for (auto p : gr) if (!(*p = (R*)A(g * sizeof(R)))) return fail(h, QSA_ERR_OOM, "grids");
+  if (!(a.fg = (R*)A(g * kFG * sizeof(R)))) return fail(h, QSA_ERR_OOM, "grids");
   if (!(a.part = (R*)A((size_t)dp.ny * kTileRows * dp.nx * kNF * sizeof(R))) ||
       !(a.ovf = (R*)A(g * kNF * sizeof(R))) ||
       !(a.rspec = (C<R>*)A(kNF * spec * sizeof(C<R>))) ||
@@ -166,8 +163,31 @@ int setup(qsa_handle* h) {
       !(s->lost = (unsigned long long*)A(sizeof(unsigned long long))) ||
       !(s->bar = (unsigned*)A(2 * sizeof(unsigned))) ||
       !(s->status = (int*)A(sizeof(int))) ||
-      !(s->bref = (double*)A((size_t)dp.nk * sizeof(double))))
+      !(s->bref = (double*)A((size_t)dp.nk * sizeof(double))) ||
+      !(s->ptimes = (unsigned long long*)A(kTimedSlices * kTimedPhases * 2 * 8)) ||
+      !(s->ktab = (R*)A((size_t)(2 * dp.nxh + 2 * dp.ny) * sizeof(R))))
     return fail(h, QSA_ERR_OOM, "sweep buffers");
+  a.ptimes = s->ptimes;
+  {
+    // k_x = 2 pi m / Lx (m = 0..nx/2), k_y = 2 pi m / Ly (m in numpy.fft order), and the
+    // first-derivative symbols, zero at the Nyquist index of an even grid
+    std::vector<R> kt(2 * dp.nxh + 2 * dp.ny);
+    for (int m = 0; m < dp.nxh; ++m) {
+      const double k = 2.0 * M_PI * m / dp.Lx;
+      kt[m] = R(k);
+      kt[dp.nxh + m] = (dp.nx % 2 == 0 && 2 * m == dp.nx) ? R(0) : R(k);
+    }
+    for (int m = 0; m < dp.ny; ++m) {
+      const int mm = (m <= dp.ny / 2) ? m : m - dp.ny;
+      const double k = 2.0 * M_PI * mm / dp.Ly;
+      kt[2 * dp.nxh + m] = R(k);
+      kt[2 * dp.nxh + dp.ny + m] = (dp.ny % 2 == 0 && 2 * m == dp.ny) ? R(0) : R(k);
+    }
+    CK(cudaMemcpyAsync(s->ktab, kt.data(), kt.size() * sizeof(R), cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    a.ktab = s->ktab;
+  }
   // twiddles exp(-2 pi i m/n), built in FP64 on the host
   std::vector<C<R>> tw(dp.nx + dp.ny);
   for (int m = 0; m < dp.nx; ++m) {
@@ -186,7 +206,7 @@ int setup(qsa_handle* h) {
   a.src = s->src;
   a.slab = s->slab;
   a.diag = s->diag;
-  a.bar = Barrier{s->bar, s->bar + 1, s->status, (long long)h->prm.spin_limit};
+  a.bar = Barrier{s->bar, s->status, (long long)h->prm.spin_limit};
   CK(cudaMemsetAsync(s->bar, 0, 2 * sizeof(unsigned), h->stream));
   CK(cudaMemsetAsync(s->status, 0, sizeof(int), h->stream));
   CK(cudaMemsetAsync(s->lost, 0, sizeof(unsigned long long), h->stream));
@@ -198,6 +218,10 @@ int setup(qsa_handle* h) {
                           (int)s->smem));
   CK(cudaFuncSetAttribute(solve_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)s->smem));
+  CK(cudaFuncSetAttribute(beam_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)beam_smem_bytes<R>(dp.nx)));
+  CK(cudaFuncSetAttribute(beam_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)beam_smem_bytes<R>(dp.nx)));
   int per_sm = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<R>, kThreads, s->smem));
   int per_sm2 = 0;
@@ -282,8 +306,9 @@ int deposit_sources(qsa_handle* h) {
   for (size_t si = 0; si < s->beams.size(); ++si) {
     const auto& b = s->beams[si];
     if (b.n == 0) continue;
-    const unsigned blocks = (unsigned)((b.n + kThreads - 1) / kThreads);
-    beam_deposit_kernel<R><<<blocks, kThreads, 0, h->stream>>>(b, dp, s->species[si], s->src);
+    const unsigned groups = (unsigned)(s->species[si].nkb * dp.ny);
+    beam_kernel<R, false><<<groups, kThreads, beam_smem_bytes<R>(dp.nx), h->stream>>>(
+        b, dp, s->species[si], s->slab, s->src, nullptr);
     ++h->launches;
     CK(cudaGetLastError());
   }
@@ -314,10 +339,9 @@ int sweep(qsa_handle* h) {
   SweepArgs<R>& a = s->sa;
   CK(cudaMemsetAsync(a.ovf, 0, g * kNF * sizeof(R), h->stream));
   CK(cudaMemsetAsync(a.bold, 0, 2 * spec * sizeof(C<R>), h->stream));
-  CK(cudaMemsetAsync(a.bx, 0, g * sizeof(R), h->stream));
-  CK(cudaMemsetAsync(a.by, 0, g * sizeof(R), h->stream));
-  CK(cudaMemsetAsync(a.bz, 0, g * sizeof(R), h->stream));
+  CK(cudaMemsetAsync(a.fg, 0, g * kFG * sizeof(R), h->stream));
   CK(cudaMemsetAsync(s->bar, 0, sizeof(unsigned), h->stream));
+  CK(cudaMemsetAsync(s->ptimes, 0, kTimedSlices * kTimedPhases * 2 * 8, h->stream));
   const int nd = D_COUNT * dp.nk;
   diag_init_kernel<<<(nd + 255) / 256, 256, 0, h->stream>>>(s->diag, dp.nk);
   ++h->launches;
@@ -338,9 +362,9 @@ int beam_step(qsa_handle* h) {
   for (size_t si = 0; si < s->beams.size(); ++si) {
     const auto& b = s->beams[si];
     if (b.n == 0) continue;
-    const unsigned blocks = (unsigned)((b.n + kThreads - 1) / kThreads);
-    beam_push_kernel<R><<<blocks, kThreads, 0, h->stream>>>(b, dp, s->species[si], s->slab,
-                                                            s->src, s->lost);
+    const unsigned groups = (unsigned)(s->species[si].nkb * dp.ny);
+    beam_kernel<R, true><<<groups, kThreads, beam_smem_bytes<R>(dp.nx), h->stream>>>(
+        b, dp, s->species[si], s->slab, s->src, s->lost);
     ++h->launches;
     CK(cudaGetLastError());
   }
@@ -482,13 +506,14 @@ int field_solve(qsa_handle* h, const double* const* in, double kappa2, double* o
   CK(cudaMemsetAsync(a.part, 0, (size_t)dp.ny * kTileRows * dp.nx * kNF * sizeof(R), h->stream));
   CK(cudaMemsetAsync(a.jprev, 0, 2 * (size_t)dp.nxh * dp.ny * sizeof(C<R>), h->stream));
   CK(cudaMemsetAsync(a.bold, 0, 2 * (size_t)dp.nxh * dp.ny * sizeof(C<R>), h->stream));
-  // B solve: trial fields Jx, Jy, Jz, Jx^{+1/2} = D_x dxi, Jy^{+1/2} = D_y dxi (J^{-1/2} = 0)
+  // B solve: trial fields Jx, Jy, Jz, Jx^{+1/2} = D_x dxi, Jy^{+1/2} = D_y dxi (J^{-1/2} = 0),
+  // placed field-major in the overflow grid
   for (size_t i = 0; i < g; ++i) {
-    ov[i * kNF + 0] = R(in[1][i]);
-    ov[i * kNF + 1] = R(in[2][i]);
-    ov[i * kNF + 2] = R(in[3][i]);
-    ov[i * kNF + 3] = R(in[4][i] * dp.dxi);
-    ov[i * kNF + 4] = R(in[5][i] * dp.dxi);
+    ov[0 * g + i] = R(in[1][i]);
+    ov[1 * g + i] = R(in[2][i]);
+    ov[2 * g + i] = R(in[3][i]);
+    ov[3 * g + i] = R(in[4][i] * dp.dxi);
+    ov[4 * g + i] = R(in[5][i] * dp.dxi);
   }
   CK(cudaMemcpyAsync(a.ovf, ov.data(), ov.size() * sizeof(R), cudaMemcpyHostToDevice,
                      h->stream));
@@ -498,20 +523,24 @@ int field_solve(qsa_handle* h, const double* const* in, double kappa2, double* o
   CK(cudaLaunchCooperativeKernel((void*)solve_kernel<R>, dim3(s->grid), dim3(kThreads), args,
                                  s->smem, h->stream));
   ++h->launches;
-  std::vector<R> tmp(g);
-  auto get = [&](const R* d, double* o) -> int {
-    CK(cudaMemcpyAsync(tmp.data(), d, g * sizeof(R), cudaMemcpyDeviceToHost, h->stream));
+  std::vector<R> tmp(g * kFG);
+  auto get = [&](const int* comps, double* const* o, int n) -> int {
+    CK(cudaMemcpyAsync(tmp.data(), a.fg, g * kFG * sizeof(R), cudaMemcpyDeviceToHost,
+                       h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    for (size_t i = 0; i < g; ++i) o[i] = (double)tmp[i];
+    for (int c = 0; c < n; ++c)
+      for (size_t i = 0; i < g; ++i) o[c][i] = (double)tmp[i * kFG + comps[c]];
     return QSA_OK;
   };
   int rc;
-  if ((rc = get(a.ez, out + 3 * g)) || (rc = get(a.bz, out + 4 * g)) ||
-      (rc = get(a.bx, out + 5 * g)) || (rc = get(a.by, out + 6 * g)))
-    return rc;
+  {
+    const int comps[4] = {FG_EZ, FG_BZ, FG_BX, FG_BY};
+    double* const o[4] = {out + 3 * g, out + 4 * g, out + 5 * g, out + 6 * g};
+    if ((rc = get(comps, o, 4))) return rc;
+  }
   // psi solve: S in field 0 of three
   std::fill(ov.begin(), ov.end(), R(0));
-  for (size_t i = 0; i < g; ++i) ov[i * 3] = R(in[0][i]);
+  for (size_t i = 0; i < g; ++i) ov[i] = R(in[0][i]);
   CK(cudaMemcpyAsync(a.ovf, ov.data(), g * 3 * sizeof(R), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemsetAsync(a.part, 0, (size_t)dp.ny * kTileRows * dp.nx * kNF * sizeof(R), h->stream));
   CK(cudaMemsetAsync(s->bar, 0, sizeof(unsigned), h->stream));
@@ -519,8 +548,11 @@ int field_solve(qsa_handle* h, const double* const* in, double kappa2, double* o
   CK(cudaLaunchCooperativeKernel((void*)solve_kernel<R>, dim3(s->grid), dim3(kThreads), args,
                                  s->smem, h->stream));
   ++h->launches;
-  if ((rc = get(a.psi, out)) || (rc = get(a.gpx, out + g)) || (rc = get(a.gpy, out + 2 * g)))
-    return rc;
+  {
+    const int comps[3] = {FG_PSI, FG_GX, FG_GY};
+    double* const o[3] = {out, out + g, out + 2 * g};
+    if ((rc = get(comps, o, 3))) return rc;
+  }
   int st = 0;
   CK(cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -695,6 +727,16 @@ int qsa_field_solve(qsa_handle* h, const double* S_, const double* Jx, const dou
   if (!(kappa2 >= 0)) return fail(h, QSA_ERR_ARG, "kappa2 must be >= 0");
   const double* in[6] = {S_, Jx, Jy, Jz, Dx, Dy};
   return h->fp64 ? field_solve<double>(h, in, kappa2, out) : field_solve<float>(h, in, kappa2, out);
+}
+
+int qsa_phase_times(qsa_handle* h, int64_t* out, int cap) {
+  if (!h || !out) return QSA_ERR_ARG;
+  const int n = kTimedSlices * kTimedPhases * 2;
+  if (cap < n) return fail(h, QSA_ERR_ARG, "capacity below 512");
+  unsigned long long* dev = h->fp64 ? S<double>(h)->ptimes : S<float>(h)->ptimes;
+  CK(cudaMemcpyAsync(out, dev, n * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return QSA_OK;
 }
 
 int64_t qsa_launch_count(const qsa_handle* h) { return h ? h->launches : 0; }

@@ -97,34 +97,11 @@ __global__ void beam_init_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp, M
   b.dw[s] = BR(dw);
 }
 
-// ------------------------------------------------------------------ deposit
-// Linear-in-xi x CIC deposit of the four source densities of one particle into the source
-// slab [nk][ny][nx][4] (global atomics).
-template <typename BR>
-struct BeamCic {
-  int x0, x1, y0, y1, k0;
-  BR fx, fy, fk;
-};
-
-template <typename BR>
-__device__ __forceinline__ BeamCic<BR> beam_cic(const Home& h, const SpeciesDev& sp, BR ox,
-                                                BR oy, BR oxi, const DevParams& p) {
-  BeamCic<BR> c;
-  const BR lx = (BR(h.sx) + BR(0.5)) / BR(sp.ppx) + ox;
-  const BR ly = (BR(h.sy) + BR(0.5)) / BR(sp.ppy) + oy;
-  const BR lk = (BR(h.sxi) + BR(0.5)) / BR(sp.ppxi) + oxi;
-  const BR fx = floor(lx), fy = floor(ly), fk = floor(lk);
-  c.fx = lx - fx;
-  c.fy = ly - fy;
-  c.fk = lk - fk;
-  const int gx = h.ix + (int)fx, gy = h.iy + (int)fy;
-  c.x0 = wrap(gx, p.nx);
-  c.x1 = wrap(gx + 1, p.nx);
-  c.y0 = wrap(gy, p.ny);
-  c.y1 = wrap(gy + 1, p.ny);
-  c.k0 = sp.k0 + h.kxi + (int)fk;
-  return c;
-}
+// ------------------------------------------------------------------ deposit and push
+// A block handles one group of a species: the ppc * nx particles whose home is xi cell k and
+// row iy.  Their deposits land in a shared-memory tile of the nodes (k, k+1) x rows
+// (iy-1 .. iy+2) x every x, which is flushed to the source slab with one vector atomic per
+// touched node; a deposit outside the tile goes straight to global memory.
 
 __device__ __forceinline__ void red4(float* a, float s, float z, float x, float y) {
   atomicAdd(reinterpret_cast<float4*>(a), make_float4(s, z, x, y));
@@ -136,67 +113,85 @@ __device__ __forceinline__ void red4(double* a, double s, double z, double x, do
   atomicAdd(a + 3, y);
 }
 
-// Deposit, per source quantity, dev W(x) + ref (W(x) - W(home)) (ref = 0 for J_x, J_y).  In
-// the home cell the trilinear weight differences come from the offsets without cancellation.
 template <typename BR>
-__device__ __forceinline__ void beam_deposit(BR* src, const Home& h, const SpeciesDev& sp, BR ox,
-                                             BR oy, BR oxi, const DevParams& p, BR dS, BR dJz,
-                                             BR jx, BR jy, BR refS, BR refJz) {
-  const BR hx = (BR(h.sx) + BR(0.5)) / BR(sp.ppx);
-  const BR hy = (BR(h.sy) + BR(0.5)) / BR(sp.ppy);
-  const BR hk = (BR(h.sxi) + BR(0.5)) / BR(sp.ppxi);
+struct Group {
+  int kabs, iy;  // home xi node and row of the group
+  BR* tile;      // [2][4][nx][4]: S_b, J_z, J_x, J_y deviations
+};
+
+// Add weight * (s, z, jx, jy) at node k, unwrapped row gy, wrapped column x.
+template <typename BR>
+__device__ __forceinline__ void put(const Group<BR>& g, BR* src, const DevParams& p, int k, int gy,
+                                    int x, BR wt, BR s, BR z, BR jx, BR jy) {
+  const int dk = k - g.kabs, r = gy - (g.iy - 1);
+  if (dk >= 0 && dk < 2 && r >= 0 && r < 4) {
+    BR* t = g.tile + ((size_t)(dk * 4 + r) * p.nx + x) * 4;
+    atomicAdd(t, wt * s);
+    atomicAdd(t + 1, wt * z);
+    atomicAdd(t + 2, wt * jx);
+    atomicAdd(t + 3, wt * jy);
+  } else if (k >= 0 && k < p.nk) {
+    red4(src + (((size_t)k * p.ny + wrap(gy, p.ny)) * p.nx + x) * 4, wt * s, wt * z, wt * jx,
+         wt * jy);
+  }
+}
+
+// Deposit, per source quantity, dev W(x) + ref (W(x) - W(home)) (ref = 0 for J_x, J_y) for a
+// particle of home column ix, home sub-cell position (hx, hy, hk) and offsets (ox, oy, oxi) in
+// cells.  In the home cell the trilinear weight differences come from the offsets without
+// cancellation.
+template <typename BR>
+__device__ __forceinline__ void deposit_particle(const Group<BR>& g, BR* src, const DevParams& p,
+                                                 int ix, BR hx, BR hy, BR hk, BR ox, BR oy,
+                                                 BR oxi, BR dS, BR dJz, BR jx, BR jy, BR refS,
+                                                 BR refJz) {
   const BR lx = hx + ox, ly = hy + oy, lk = hk + oxi;
-  const bool home = lx >= BR(0) && lx < BR(1) && ly >= BR(0) && ly < BR(1) && lk >= BR(0) &&
-                    lk < BR(1);
-  if (home) {
-    const int k0 = sp.k0 + h.kxi;
-    const int x1 = (h.ix + 1 == p.nx) ? 0 : h.ix + 1, y1 = (h.iy + 1 == p.ny) ? 0 : h.iy + 1;
+  const int nx = p.nx;
+  if (lx >= BR(0) && lx < BR(1) && ly >= BR(0) && ly < BR(1) && lk >= BR(0) && lk < BR(1)) {
+    const int x1 = (ix + 1 == nx) ? 0 : ix + 1;
 #pragma unroll
     for (int ck = 0; ck < 2; ++ck) {
-      const int k = k0 + ck;
-      if (k >= p.nk) continue;
+      if (g.kabs + ck >= p.nk) continue;
       const BR a3 = ck ? hk : BR(1) - hk, d3 = ck ? oxi : -oxi;
 #pragma unroll
       for (int cy = 0; cy < 2; ++cy) {
         const BR a2 = cy ? hy : BR(1) - hy, d2 = cy ? oy : -oy;
+        BR* row = g.tile + (size_t)(ck * 4 + 1 + cy) * nx * 4;
 #pragma unroll
         for (int cx = 0; cx < 2; ++cx) {
           const BR a1 = cx ? hx : BR(1) - hx, d1 = cx ? ox : -ox;
           const BR w = (a1 + d1) * (a2 + d2) * (a3 + d3);
           const BR dW = d1 * a2 * a3 + a1 * d2 * a3 + a1 * a2 * d3 + d1 * d2 * a3 +
                         d1 * a2 * d3 + a1 * d2 * d3 + d1 * d2 * d3;
-          const int y = cy ? y1 : h.iy, x = cx ? x1 : h.ix;
-          red4(src + (((size_t)k * p.ny + y) * p.nx + x) * 4, dS * w + refS * dW,
-               dJz * w + refJz * dW, jx * w, jy * w);
+          BR* t = row + (size_t)(cx ? x1 : ix) * 4;
+          atomicAdd(t, dS * w + refS * dW);
+          atomicAdd(t + 1, dJz * w + refJz * dW);
+          atomicAdd(t + 2, jx * w);
+          atomicAdd(t + 3, jy * w);
         }
       }
     }
     return;
   }
   // left the home cell: full weights at the new corners, minus the reference at home
-  const BeamCic<BR> c = beam_cic<BR>(h, sp, ox, oy, oxi, p);
-  const BeamCic<BR> o = beam_cic<BR>(h, sp, BR(0), BR(0), BR(0), p);
-#pragma unroll
+#pragma unroll 1
   for (int pass = 0; pass < 2; ++pass) {
-    const BeamCic<BR>& e = pass ? o : c;
+    const BR mx = pass ? hx : lx, my = pass ? hy : ly, mk = pass ? hk : lk;
+    const BR fx = floor(mx), fy = floor(my), fk = floor(mk);
+    const BR ex = mx - fx, ey = my - fy, ek = mk - fk;
+    const int gx = ix + (int)fx, gy = g.iy + (int)fy, gk = g.kabs + (int)fk;
     const BR s0 = pass ? -refS : dS + refS, z0 = pass ? -refJz : dJz + refJz;
     const BR x0v = pass ? BR(0) : jx, y0v = pass ? BR(0) : jy;
-    const BR gx = BR(1) - e.fx, gy = BR(1) - e.fy, gk = BR(1) - e.fk;
 #pragma unroll
-    for (int dk = 0; dk < 2; ++dk) {
-      const int k = e.k0 + dk;
-      if (k < 0 || k >= p.nk) continue;
-      const BR wk = dk ? e.fk : gk;
+    for (int ck = 0; ck < 2; ++ck) {
+      const BR wk = ck ? ek : BR(1) - ek;
 #pragma unroll
-      for (int dy = 0; dy < 2; ++dy) {
-        const int y = dy ? e.y1 : e.y0;
-        const BR wy = wk * (dy ? e.fy : gy);
+      for (int cy = 0; cy < 2; ++cy) {
+        const BR wy = wk * (cy ? ey : BR(1) - ey);
 #pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-          const int x = dx ? e.x1 : e.x0;
-          const BR wt = wy * (dx ? e.fx : gx);
-          red4(src + (((size_t)k * p.ny + y) * p.nx + x) * 4, wt * s0, wt * z0, wt * x0v,
-               wt * y0v);
+        for (int cx = 0; cx < 2; ++cx) {
+          const BR wt = wy * (cx ? ex : BR(1) - ex);
+          put(g, src, p, gk + ck, gy + cy, wrap(gx + cx, nx), wt, s0, z0, x0v, y0v);
         }
       }
     }
@@ -234,45 +229,42 @@ __device__ __forceinline__ void beam_sources(float ux, float uy, double uz, floa
   jy = q * uy / g;
 }
 
-template <typename BR>
-__global__ void beam_deposit_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp, BR* src) {
-  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (s >= b.n) return;
-  const BR dw = b.dw[s];
-  const Home h = home_of(s, p.nx, p.ny, sp);
-  const BR refS = BR(sp.qbar * sp.omvbar), refJz = BR(sp.qbar * (1.0 - sp.omvbar));
-  if (dw == BR(-1)) {  // lost: only the reference is removed (it sits at home)
-    beam_deposit(src, h, sp, BR(0), BR(0), BR(0), p, -refS, -refJz, BR(0), BR(0), refS, refJz);
-    return;
-  }
-  BR dS, dJz, JX, JY;
-  beam_sources(b.ux[s], b.uy[s], b.uz[s], dw, sp, dS, dJz, JX, JY);
-  beam_deposit(src, h, sp, b.ox[s], b.oy[s], b.oxi[s], p, dS, dJz, JX, JY, refS, refJz);
+// Trilinear gather of the six slab fields (CIC in x, y, linear in xi) at unwrapped node
+// (gk, gy, gx) + fractions (ek, ey, ex).
+__device__ __forceinline__ void ldslab(const float* e, float v[6]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(e));
+  const float2 b = __ldg(reinterpret_cast<const float2*>(e + 4));
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y;
 }
-
-// ------------------------------------------------------------------ push
+__device__ __forceinline__ void ldslab(const double* e, double v[6]) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(e));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(e + 2));
+  const double2 c = __ldg(reinterpret_cast<const double2*>(e + 4));
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+}
 template <typename BR>
-__device__ __forceinline__ void gather_slab(const BR* __restrict__ slab, const BeamCic<BR>& c,
-                                            const DevParams& p, BR F[6]) {
+__device__ __forceinline__ void gather_slab(const BR* __restrict__ slab, const DevParams& p, int gk,
+                                            int gy, int gx, BR ek, BR ey, BR ex, BR F[6]) {
 #pragma unroll
   for (int f = 0; f < 6; ++f) F[f] = BR(0);
-  const BR gx = BR(1) - c.fx, gy = BR(1) - c.fy, gk = BR(1) - c.fk;
+  const int y0 = wrap(gy, p.ny), y1 = wrap(gy + 1, p.ny);
+  const int x0 = wrap(gx, p.nx), x1 = wrap(gx + 1, p.nx);
 #pragma unroll
-  for (int dk = 0; dk < 2; ++dk) {
-    const int k = c.k0 + dk;
+  for (int ck = 0; ck < 2; ++ck) {
+    const int k = gk + ck;
     if (k < 0 || k >= p.nk) continue;
-    const BR wk = dk ? c.fk : gk;
+    const BR wk = ck ? ek : BR(1) - ek;
 #pragma unroll
-    for (int dy = 0; dy < 2; ++dy) {
-      const int y = dy ? c.y1 : c.y0;
-      const BR wy = wk * (dy ? c.fy : gy);
+    for (int cy = 0; cy < 2; ++cy) {
+      const BR wy = wk * (cy ? ey : BR(1) - ey);
+      const BR* row = slab + ((size_t)k * p.ny + (cy ? y1 : y0)) * p.nx * 8;
 #pragma unroll
-      for (int dx = 0; dx < 2; ++dx) {
-        const int x = dx ? c.x1 : c.x0;
-        const BR wt = wy * (dx ? c.fx : gx);
-        const BR* e = slab + (((size_t)k * p.ny + y) * p.nx + x) * 8;
+      for (int cx = 0; cx < 2; ++cx) {
+        const BR wt = wy * (cx ? ex : BR(1) - ex);
+        BR v[6];
+        ldslab(row + (size_t)(cx ? x1 : x0) * 8, v);
 #pragma unroll
-        for (int f = 0; f < 6; ++f) F[f] += wt * e[f];
+        for (int f = 0; f < 6; ++f) F[f] += wt * v[f];
       }
     }
   }
@@ -303,8 +295,7 @@ __device__ __forceinline__ void boris(float& ux, float& uy, double& uz, const fl
                                       float h) {
   const float Wx = F[0], Wy = F[1], Ez = F[2], Bx = F[3], By = F[4], Bz = F[5];
   const float mx = ux + h * (Wx + By), my = uy + h * (Wy - Bx);
-  const double mz = uz + (double)(h * Ez);
-  const float mzf = (float)mz;
+  const float mzf = (float)uz + h * Ez;
   const float mp2 = mx * mx + my * my;
   const float gm = sqrtf(1.0f + mp2 + mzf * mzf);
   const float dm = (1.0f + mp2) / (gm + mzf);  // gamma^- - m_z
@@ -320,68 +311,106 @@ __device__ __forceinline__ void boris(float& ux, float& uy, double& uz, const fl
   const float eps = (dm + gm * t2 - (mx * ty - my * tx)) * ig / (1.0f + t2);
   ux = ux + 2.0f * h * Wx + 2.0f * h * By * eps + pyp * sz;
   uy = uy + 2.0f * h * Wy - 2.0f * h * Bx * eps - pxp * sz;
-  uz = mz + (double)(h * Ez + pxp * sy - pyp * sx);
+  uz = uz + (double)(2.0f * h * Ez + pxp * sy - pyp * sx);
+}
+
+// PUSH = false: deposit the current beam (sources of the first sweep).  PUSH = true: push
+// every live particle by dt through the slab, drop those with xi >= Lxi, and deposit the
+// sources of the next sweep.  Grid: one block per (xi cell, row) group of the species.
+template <typename BR, bool PUSH>
+__global__ void __launch_bounds__(256, 2) beam_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp,
+                                                   const BR* __restrict__ slab, BR* src,
+                                                   unsigned long long* lost) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Group<BR> g;
+  g.tile = reinterpret_cast<BR*>(smem);
+  const int grp = blockIdx.x;
+  g.iy = grp % p.ny;
+  g.kabs = sp.k0 + grp / p.ny;
+  const int nx = p.nx;
+  const int tn = 2 * 4 * nx * 4;
+  for (int e = threadIdx.x; e < tn; e += blockDim.x) g.tile[e] = BR(0);
+  __syncthreads();
+  const size_t base = (size_t)grp * sp.ppc * nx;
+  const BR refS = BR(sp.qbar * sp.omvbar), refJz = BR(sp.qbar * (1.0 - sp.omvbar));
+  const BR hdt = BR(0.5 * sp.Z * p.dt / sp.M);
+  const BR cdx = BR(p.dt / p.dx), cdy = BR(p.dt / p.dy), cdk = BR(p.dt / p.dxi);
+  const int kleft = p.nxi - g.kabs;  // lost when the local xi position reaches this
+  int my_lost = 0;
+  for (int sub = 0; sub < sp.ppc; ++sub) {
+    const int sx = sub % sp.ppx, sy = (sub / sp.ppx) % sp.ppy, sxi = sub / (sp.ppx * sp.ppy);
+    const BR hx = (BR(sx) + BR(0.5)) / BR(sp.ppx), hy = (BR(sy) + BR(0.5)) / BR(sp.ppy);
+    const BR hk = (BR(sxi) + BR(0.5)) / BR(sp.ppxi);
+    for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
+      const size_t s = base + (size_t)sub * nx + ix;
+      const BR dw = b.dw[s];
+      if (dw == BR(-1)) {  // lost: only its reference, at home, is removed
+        deposit_particle(g, src, p, ix, hx, hy, hk, BR(0), BR(0), BR(0), -refS, -refJz, BR(0),
+                         BR(0), refS, refJz);
+        continue;
+      }
+      BR ox = b.ox[s], oy = b.oy[s], oxi = b.oxi[s];
+      BR ux = b.ux[s], uy = b.uy[s];
+      double uz = b.uz[s];
+      if (PUSH) {
+        const BR lx = hx + ox, ly = hy + oy, lk = hk + oxi;
+        const BR fx = floor(lx), fy = floor(ly), fk = floor(lk);
+        BR F[6];
+        gather_slab(slab, p, g.kabs + (int)fk, g.iy + (int)fy, ix + (int)fx, lk - fk, ly - fy,
+                    lx - fx, F);
+        boris(ux, uy, uz, F, hdt);
+        // dx/dt = u/gamma, dxi/dt = 1 - v_z = (1 + u_perp^2)/(gamma (gamma + u_z))
+        BR ig, omv;
+        {
+          const BR up2 = ux * ux + uy * uy;
+          if (sizeof(BR) == 8) {
+            const double gg = sqrt(1.0 + (double)up2 + uz * uz);
+            ig = BR(1.0 / gg);
+            omv = BR((1.0 + (double)up2) / (gg * (gg + uz)));
+          } else {
+            const float uzf = (float)uz;
+            const float d = (1.0f + (float)up2) / (sqrtf(1.0f + (float)up2 + uzf * uzf) + uzf);
+            ig = BR(1.0f / (uzf + d));
+            omv = BR(d) * ig;
+          }
+        }
+        ox += cdx * ux * ig;
+        oy += cdy * uy * ig;
+        oxi += cdk * omv;
+        b.ox[s] = ox;
+        b.oy[s] = oy;
+        b.oxi[s] = oxi;
+        b.ux[s] = ux;
+        b.uy[s] = uy;
+        b.uz[s] = uz;
+        if (hk + oxi >= BR(kleft)) {
+          b.dw[s] = BR(-1);
+          ++my_lost;
+          deposit_particle(g, src, p, ix, hx, hy, hk, BR(0), BR(0), BR(0), -refS, -refJz, BR(0),
+                           BR(0), refS, refJz);
+          continue;
+        }
+      }
+      BR dS, dJz, JX, JY;
+      beam_sources(ux, uy, uz, dw, sp, dS, dJz, JX, JY);
+      deposit_particle(g, src, p, ix, hx, hy, hk, ox, oy, oxi, dS, dJz, JX, JY, refS, refJz);
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * 4 * nx; e += blockDim.x) {
+    const int dk = e / (4 * nx), r = (e / nx) % 4, x = e % nx;
+    const int k = g.kabs + dk;
+    const BR* t = g.tile + (size_t)e * 4;
+    if (k < p.nk && (t[0] != BR(0) || t[1] != BR(0) || t[2] != BR(0) || t[3] != BR(0)))
+      red4(src + (((size_t)k * p.ny + wrap(g.iy - 1 + r, p.ny)) * nx + x) * 4, t[0], t[1], t[2],
+           t[3]);
+  }
+  if (my_lost && lost) atomicAdd(lost, (unsigned long long)my_lost);
 }
 
 template <typename BR>
-__global__ void beam_push_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp, const BR* slab,
-                                 BR* src, unsigned long long* lost) {
-  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  int my_lost = 0;
-  if (s < b.n) {
-    const BR dw = b.dw[s];
-    const Home h = home_of(s, p.nx, p.ny, sp);
-    const BR refS = BR(sp.qbar * sp.omvbar), refJz = BR(sp.qbar * (1.0 - sp.omvbar));
-    if (dw == BR(-1)) {
-      beam_deposit(src, h, sp, BR(0), BR(0), BR(0), p, -refS, -refJz, BR(0), BR(0), refS, refJz);
-    } else {
-      BR ox = b.ox[s], oy = b.oy[s], oxi = b.oxi[s];
-      const BeamCic<BR> c = beam_cic<BR>(h, sp, ox, oy, oxi, p);
-      BR F[6];
-      gather_slab(slab, c, p, F);
-      BR ux = b.ux[s], uy = b.uy[s];
-      double uz = b.uz[s];
-      boris(ux, uy, uz, F, BR(0.5 * sp.Z * p.dt / sp.M));
-      // positions: dx/dt = u/gamma, dxi/dt = 1 - v_z = (1 + u_perp^2)/(gamma (gamma + u_z))
-      BR g, omv;
-      {
-        const BR up2 = ux * ux + uy * uy;
-        if (sizeof(BR) == 8) {
-          const double gg = sqrt(1.0 + (double)up2 + uz * uz);
-          g = BR(gg);
-          omv = BR((1.0 + (double)up2) / (gg * (gg + uz)));
-        } else {
-          const float uzf = (float)uz;
-          const float d = (1.0f + (float)up2) / (sqrtf(1.0f + (float)up2 + uzf * uzf) + uzf);
-          g = BR(uzf + d);
-          omv = BR(d / (uzf + d));
-        }
-      }
-      ox += BR(p.dt / p.dx) * ux / g;
-      oy += BR(p.dt / p.dy) * uy / g;
-      oxi += BR(p.dt / p.dxi) * omv;
-      b.ox[s] = ox;
-      b.oy[s] = oy;
-      b.oxi[s] = oxi;
-      b.ux[s] = ux;
-      b.uy[s] = uy;
-      b.uz[s] = uz;
-      // lost when xi >= Lxi: home xi cell + local position >= nxi
-      const BR lk = (BR(h.sxi) + BR(0.5)) / BR(sp.ppxi) + oxi;
-      if (lk >= BR(p.nxi - (sp.k0 + h.kxi))) {
-        b.dw[s] = BR(-1);
-        my_lost = 1;
-        beam_deposit(src, h, sp, BR(0), BR(0), BR(0), p, -refS, -refJz, BR(0), BR(0), refS,
-                     refJz);
-      } else {
-        BR dS, dJz, JX, JY;
-        beam_sources(ux, uy, uz, dw, sp, dS, dJz, JX, JY);
-        beam_deposit(src, h, sp, ox, oy, oxi, p, dS, dJz, JX, JY, refS, refJz);
-      }
-    }
-  }
-  const int nl = __syncthreads_count(my_lost);
-  if (threadIdx.x == 0 && nl) atomicAdd(lost, (unsigned long long)nl);
+__host__ __device__ inline size_t beam_smem_bytes(int nx) {
+  return (size_t)2 * 4 * nx * 4 * sizeof(BR);
 }
 
 // Conversion between host fp64 arrays (canonical id order, absolute positions) and the

@@ -53,9 +53,9 @@ struct DevParams {
 };
 
 // ---------------------------------------------------------------------------------------
-// Grid-wide barrier for a cooperative launch.  Sense by generation counter; every wait is
-// bounded by spin_limit polls, after which the status word gets ST_TIMEOUT and the barrier
-// reports failure so that every block leaves the kernel.
+// Grid-wide barrier for a cooperative launch.  Every wait is bounded by spin_limit polls,
+// after which the status word gets ST_TIMEOUT and the barrier reports failure so that every
+// block leaves the kernel.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
@@ -68,44 +68,53 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
 
 struct Barrier {
   unsigned* count;
-  unsigned* gen;
   int* status;
   long long spin_limit;
 };
 
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
+               : "memory");
+  return old;
+}
+
+// Monotonic arrival counter (zeroed before each launch): the epoch-th barrier of a launch is
+// passed once the counter reaches (epoch + 1) * gridDim.x.  Each block's thread 0 adds one
+// with acquire-release semantics (publishing the block's writes, ordered by the preceding
+// __syncthreads) and polls with acquire loads; the last arriver does not wait.
 // Returns true when every block arrived; false (uniformly for the block) on timeout or when
-// a timeout was already latched.
-__device__ __forceinline__ bool grid_sync(const Barrier& b) {
+// a timeout was already latched.  arrive (optional): max over blocks of the arrival time.
+__device__ __forceinline__ bool grid_sync(const Barrier& b, unsigned& epoch,
+                                          unsigned long long* arrive = nullptr) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
+    if (arrive) atomicMax(arrive, globaltimer());
     int ok = 1;
+    const unsigned target = (epoch + 1u) * gridDim.x;
     if (*((volatile int*)b.status) & ST_TIMEOUT) {
       ok = 0;
-    } else {
-      unsigned g = ld_acquire_u32(b.gen);
-      __threadfence();
-      unsigned arrived = atomicAdd(b.count, 1u);
-      if (arrived == gridDim.x - 1) {
-        atomicExch(b.count, 0u);
-        __threadfence();
-        st_release_u32(b.gen, g + 1u);
-      } else {
-        long long it = 0;
-        while (ld_acquire_u32(b.gen) == g) {
-          if (++it > b.spin_limit) {
-            atomicOr(b.status, ST_TIMEOUT);
-            ok = 0;
-            break;
-          }
-          __nanosleep(32);
+    } else if (atom_add_acq_rel_u32(b.count, 1u) + 1u != target) {
+      long long it = 0;
+      while (ld_acquire_u32(b.count) < target) {
+        if (++it > b.spin_limit) {
+          atomicOr(b.status, ST_TIMEOUT);
+          ok = 0;
+          break;
         }
       }
-      __threadfence();
     }
     s_ok = ok;
   }
   __syncthreads();
+  ++epoch;
   return s_ok != 0;
 }
 
@@ -142,6 +151,22 @@ __device__ __forceinline__ T block_sum(T v, T* scratch /* >= 32 */) {
   }
   return r;
 }
+// N sums over the block in one exchange (FP64 results, valid in thread 0); scratch >= 32.
+template <int N, typename T>
+__device__ __forceinline__ void block_sum_n(const T v[N], double out[N], double* scratch) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double r[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) r[k] = warp_sum((double)v[k]);
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    __syncthreads();
+    if (lane == 0) scratch[w] = r[k];
+    __syncthreads();
+    if (w == 0) out[k] = warp_sum(lane < nw ? scratch[lane] : 0.0);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T block_max(T v, T* scratch) {
   v = warp_max(v);
@@ -199,9 +224,12 @@ __device__ __forceinline__ U4 philox4x32_10(U4 ctr, uint32_t k0, uint32_t k1) {
 }
 __device__ __forceinline__ double u01(uint32_t r) { return ((double)r + 0.5) * (1.0 / 4294967296.0); }
 
-// Periodic index helpers.
+// Periodic index: i mod n in [0, n), without a division when i is within one period.
 __device__ __forceinline__ int wrap(int i, int n) {
-  int r = i % n;
+  if ((unsigned)i < (unsigned)n) return i;
+  if (i < 0 && i >= -n) return i + n;
+  if (i >= n && i < 2 * n) return i - n;
+  const int r = i % n;
   return r < 0 ? r + n : r;
 }
 

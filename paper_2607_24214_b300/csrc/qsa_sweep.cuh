@@ -14,11 +14,15 @@
 //     S at x^{j+1} and J_perp^{j+1/2}, FFT, solve psi and its gradient for slice j+1.
 // The k = 0 mode (psi0, E_z0) is integrated in FP64 registers by every block identically.
 //
-// Plasma particles are stored [home row iy][sub-lattice index][ix]: a warp holds 32
-// neighbouring cells, and a block owns one home row (a "chunk") whose deposits land in a
-// four-row shared-memory tile [iy-1, iy+2]; the tile goes to a per-chunk partial buffer that
-// the row phase sums without atomics.  Particles that moved out of their tile deposit with
-// global atomics into an overflow grid.
+// Layouts: plasma particles [home row iy][sub-lattice index][ix] (a warp holds 32 neighbouring
+// cells); real-space fields interleaved per node, fg[iy][ix][8] = (psi, d_x psi, d_y psi, B_x,
+// B_y, B_z, E_z, -) so that a CIC gather is two 16-byte loads per corner; deposit tiles,
+// per-chunk partials and the overflow grid field-major; spectra [field][kx][ky] after the row
+// phase and [field][ky][kx] after the column phase, so that every transpose is a strided
+// write followed by contiguous reads.  A block owns one home row (a chunk) of particles whose
+// deposits land in a four-row shared-memory tile [iy-1, iy+2]; the tile goes to a per-chunk
+// partial buffer that the row phase sums without atomics; particles that left their tile
+// deposit with global atomics into the overflow grid.
 #pragma once
 #include "qsa_common.cuh"
 #include "qsa_fft.cuh"
@@ -27,13 +31,20 @@ namespace qsa {
 
 constexpr int kNF = 5;  // deposit fields of a trial phase
 constexpr int kTileRows = 4;
+constexpr int kFG = 8;  // components of the interleaved field grid
+enum FgComp : int { FG_PSI = 0, FG_GX, FG_GY, FG_BX, FG_BY, FG_BZ, FG_EZ };
+// Phase timing of the first slices: for slice j < kTimedSlices and phase ph < kTimedPhases
+// (trial iteration it, step k: ph = 4 it + k; commit: ph = 4 n_pc + k), the globaltimer of
+// the last block's arrival at the barrier and of block 0's exit from it.
+constexpr int kTimedSlices = 8;
+constexpr int kTimedPhases = 32;
 
 enum Diag : int {
   D_KAPPA = 0,  // sum 1/(1+psi) over particles -> kappa^2 after scaling
   D_JZ,         // <J_z> total
   D_PSI0,
   D_EZ0,
-  D_CHARGE,     // sum over cells of the plasma (rho - J_z), times dx dy
+  D_CHARGE,     // sum over cells of the plasma (rho - J_z) deviation, times dx dy
   D_PCNUM,
   D_PCDEN,
   D_OPPMIN,     // ordered-key minimum of 1 + psi
@@ -53,19 +64,21 @@ template <typename R>
 struct SweepArgs {
   DevParams p;
   R *pox, *poy, *pux, *puy, *ppsi;          // plasma state (offsets in cells)
-  R *psi, *gpx, *gpy, *bx, *by, *bz, *ez;   // real grids [ny][nx]
-  R* part;                                  // [ny][4][nx][nf]
-  R* ovf;                                   // [ny][nx][nf]
+  R* fg;                                    // [ny][nx][8] real-space fields
+  R* part;                                  // [ny chunks][nf][4][nx]
+  R* ovf;                                   // [kNF][ny][nx]
   C<R>* rspec;                              // [kNF][nxh][ny]
-  C<R>* cspec;                              // [4][nxh][ny]
+  C<R>* cspec;                              // [4][ny][nxh]
   C<R>* jprev;                              // [2][nxh][ny]  J_perp^{j-1/2} spectra
   C<R>* bold;                               // [2][nxh][ny]  B_perp spectra of the last solve
   const C<R>* twx;
   const C<R>* twy;
-  const R* src;                             // [nk][ny][nx][4] beam S_b, J_z, J_x, J_y
+  const R* src;                             // [nk][ny][nx][4] beam S_b, J_z, J_x, J_y deviations
   R* slab;                                  // [nk][ny][nx][8]
   double* diag;                             // [D_COUNT][nk]
+  const R* ktab;                            // wavenumber table, see kvec
   const double* bref;                       // [nk] beam J_z reference density per node
+  unsigned long long* ptimes;               // [kTimedSlices][kTimedPhases][2] or null
   Barrier bar;
 };
 
@@ -93,33 +106,54 @@ __device__ __forceinline__ Cic<R> cic(int ix, int iy, R lx, R ly, int nx, int ny
   return c;
 }
 
+// Bilinear gather of all components of the interleaved field grid.
+__device__ __forceinline__ void ld4(const float* p, float v[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double v[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
 template <typename R>
-__device__ __forceinline__ R gather(const R* __restrict__ F, const Cic<R>& c, int nx) {
-  const R a = F[c.y0 * nx + c.x0], b = F[c.y0 * nx + c.x1];
-  const R d = F[c.y1 * nx + c.x0], e = F[c.y1 * nx + c.x1];
+__device__ __forceinline__ void gather8(const R* __restrict__ fg, const Cic<R>& c, int nx,
+                                        R out[8]) {
+  R a[8], b[8], d[8], e[8];
+  const R* pa = fg + ((size_t)c.y0 * nx + c.x0) * kFG;
+  const R* pb = fg + ((size_t)c.y0 * nx + c.x1) * kFG;
+  const R* pd = fg + ((size_t)c.y1 * nx + c.x0) * kFG;
+  const R* pe = fg + ((size_t)c.y1 * nx + c.x1) * kFG;
+  ld4(pa, a); ld4(pa + 4, a + 4);
+  ld4(pb, b); ld4(pb + 4, b + 4);
+  ld4(pd, d); ld4(pd + 4, d + 4);
+  ld4(pe, e); ld4(pe + 4, e + 4);
   const R gx = R(1) - c.fx, gy = R(1) - c.fy;
-  return gy * (gx * a + c.fx * b) + c.fy * (gx * d + c.fx * e);
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    out[k] = gy * (gx * a[k] + c.fx * b[k]) + c.fy * (gx * d[k] + c.fx * e[k]);
 }
 
-// Deposit v (already a density) at the four corners into the tile, or to the overflow grid
-// when the rows fall outside the tile.
+// Deposit v (already a density) at the four corners into the field-major tile [nf][4][nx],
+// or into the overflow grid [kNF][ny][nx] when the rows fall outside the tile.
 template <typename R>
-__device__ __forceinline__ void deposit(R* tile, R* ovf, const Cic<R>& c, int f, int nf, int nx,
+__device__ __forceinline__ void deposit(R* tile, R* ovf, const Cic<R>& c, int f, int nx, int ny,
                                         R v) {
   const R gx = R(1) - c.fx, gy = R(1) - c.fy;
   const R w00 = gx * gy * v, w01 = c.fx * gy * v, w10 = gx * c.fy * v, w11 = c.fx * c.fy * v;
   if (c.ty >= 0 && c.ty <= kTileRows - 2) {
-    R* r0 = tile + (size_t)c.ty * nx * nf;
-    R* r1 = r0 + (size_t)nx * nf;
-    atomicAdd(r0 + c.x0 * nf + f, w00);
-    atomicAdd(r0 + c.x1 * nf + f, w01);
-    atomicAdd(r1 + c.x0 * nf + f, w10);
-    atomicAdd(r1 + c.x1 * nf + f, w11);
+    R* r0 = tile + ((size_t)f * kTileRows + c.ty) * nx;
+    R* r1 = r0 + nx;
+    atomicAdd(r0 + c.x0, w00);
+    atomicAdd(r0 + c.x1, w01);
+    atomicAdd(r1 + c.x0, w10);
+    atomicAdd(r1 + c.x1, w11);
   } else {
-    atomicAdd(ovf + ((size_t)c.y0 * nx + c.x0) * nf + f, w00);
-    atomicAdd(ovf + ((size_t)c.y0 * nx + c.x1) * nf + f, w01);
-    atomicAdd(ovf + ((size_t)c.y1 * nx + c.x0) * nf + f, w10);
-    atomicAdd(ovf + ((size_t)c.y1 * nx + c.x1) * nf + f, w11);
+    R* o = ovf + (size_t)f * ny * nx;
+    atomicAdd(o + (size_t)c.y0 * nx + c.x0, w00);
+    atomicAdd(o + (size_t)c.y0 * nx + c.x1, w01);
+    atomicAdd(o + (size_t)c.y1 * nx + c.x0, w10);
+    atomicAdd(o + (size_t)c.y1 * nx + c.x1, w11);
   }
 }
 
@@ -131,8 +165,7 @@ __device__ __forceinline__ void deposit(R* tile, R* ovf, const Cic<R>& c, int f,
 // cancellation.
 template <typename R>
 __device__ __forceinline__ void deposit_ref(R* tile, R* ovf, int ix, int crow, R hx, R hy, R ox,
-                                            R oy, int f, int nf, int nx, int ny, R v_dev,
-                                            R v_ref) {
+                                            R oy, int f, int nx, int ny, R v_dev, R v_ref) {
   const R lx = hx + ox, ly = hy + oy;
   if (lx >= R(0) && lx < R(1) && ly >= R(0) && ly < R(1)) {
     const R ax = R(1) - hx, ay = R(1) - hy;
@@ -142,38 +175,35 @@ __device__ __forceinline__ void deposit_ref(R* tile, R* ovf, int ix, int crow, R
     const R w00 = (ax - ox) * (ay - oy), w01 = lx * (ay - oy), w10 = (ax - ox) * ly,
             w11 = lx * ly;
     const int x0 = ix, x1 = (ix + 1 == nx) ? 0 : ix + 1;
-    R* r0 = tile + (size_t)1 * nx * nf;  // home row crow is tile row 1
-    R* r1 = r0 + (size_t)nx * nf;
-    atomicAdd(r0 + x0 * nf + f, v_dev * w00 + v_ref * d00);
-    atomicAdd(r0 + x1 * nf + f, v_dev * w01 + v_ref * d01);
-    atomicAdd(r1 + x0 * nf + f, v_dev * w10 + v_ref * d10);
-    atomicAdd(r1 + x1 * nf + f, v_dev * w11 + v_ref * d11);
+    R* r0 = tile + ((size_t)f * kTileRows + 1) * nx;  // home row crow is tile row 1
+    R* r1 = r0 + nx;
+    atomicAdd(r0 + x0, v_dev * w00 + v_ref * d00);
+    atomicAdd(r0 + x1, v_dev * w01 + v_ref * d01);
+    atomicAdd(r1 + x0, v_dev * w10 + v_ref * d10);
+    atomicAdd(r1 + x1, v_dev * w11 + v_ref * d11);
   } else {
     const Cic<R> c = cic<R>(ix, crow, lx, ly, nx, ny, crow);
-    deposit(tile, ovf, c, f, nf, nx, v_dev + v_ref);
+    deposit(tile, ovf, c, f, nx, ny, v_dev + v_ref);
     const Cic<R> h = cic<R>(ix, crow, hx, hy, nx, ny, crow);
-    deposit(tile, ovf, h, f, nf, nx, -v_ref);
+    deposit(tile, ovf, h, f, nx, ny, -v_ref);
   }
-}
-
-// gamma/(1+psi) from the quasistatic invariant gamma - u_z = 1 + psi.
-template <typename R>
-__device__ __forceinline__ R g_over_opp(R ux, R uy, R opp) {
-  return (R(1) + ux * ux + uy * uy + opp * opp) / (R(2) * opp * opp);
 }
 
 // xi push u^{j-1/2} -> u^{j+1/2}: half kick, counter-clockwise rotation by
 // 2 atan(dxi B_z/(2(1+psi))), half kick; gamma/(1+psi) of both kicks taken at the predicted
-// pre-rotation momentum (the rotation keeps |u_perp|).
+// pre-rotation momentum (the rotation keeps |u_perp|).  From the quasistatic invariant
+// gamma - u_z = 1 + psi: gamma/(1+psi) = (1 + u^2 + (1+psi)^2) / (2 (1+psi)^2).
 template <typename R>
-__device__ __forceinline__ void push_xi(R& ux, R& uy, R opp, R gx, R gy, R bx, R by, R bz,
-                                        R dxi) {
+__device__ __forceinline__ void push_xi(R& ux, R& uy, R opp, R iopp, R gx, R gy, R bx, R by,
+                                        R bz, R dxi) {
   const R h = R(0.5) * dxi;
-  const R g0 = g_over_opp(ux, uy, opp);
-  const R g = g_over_opp(ux + h * (g0 * gx - by), uy + h * (g0 * gy + bx), opp);
+  const R hi2 = R(0.5) * iopp * iopp;
+  const R g0 = (R(1) + ux * ux + uy * uy + opp * opp) * hi2;
+  const R px0 = ux + h * (g0 * gx - by), py0 = uy + h * (g0 * gy + bx);
+  const R g = (R(1) + px0 * px0 + py0 * py0 + opp * opp) * hi2;
   const R kx = h * (g * gx - by), ky = h * (g * gy + bx);
   const R mx = ux + kx, my = uy + ky;
-  const R t = h * bz / opp;
+  const R t = h * bz * iopp;
   const R s = R(2) * t / (R(1) + t * t);
   const R px = mx - t * my, py = my + t * mx;
   const R qx = mx - s * py, qy = my + s * px;
@@ -191,6 +221,7 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
   const double opp0d = 1.0 + psi0;
   const R opp0 = R(opp0d);
   const R c0 = R(-psi0 * (2.0 + psi0) / (2.0 * opp0d * opp0d));
+  const R iopp02 = R(1.0 / (opp0d * opp0d));
   const DevParams& p = a.p;
   const int nx = p.nx, ny = p.ny;
   const int nf = (mode == DEP_TRIAL) ? kNF : 3;
@@ -200,9 +231,17 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
   const R idx = R(1) / R(p.dx), idy = R(1) / R(p.dy);
   const R floor_ = R(p.psi_floor);
   const int tile_elems = kTileRows * nx * nf;
-  double kap = 0.0, inv = 0.0, omin = 1e300;
+  // per-thread diagnostics accumulate in R (FP64 arithmetic is scarce on this GPU); the block
+  // reductions below are FP64
+  R kap = R(0), inv = R(0), omin = R(1e30);
+  const R psi0r = R(psi0);
   unsigned long long nfloor = 0;
   __shared__ double red[32];
+  R* __restrict__ pox = a.pox;
+  R* __restrict__ poy = a.poy;
+  R* __restrict__ pux = a.pux;
+  R* __restrict__ puy = a.puy;
+  R* __restrict__ pps = a.ppsi;
 
   for (int crow = blockIdx.x; crow < ny; crow += gridDim.x) {
     for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) tile[e] = R(0);
@@ -214,68 +253,71 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
       const int sx = sub % p.ppx, sy = sub / p.ppx;
       const R hx = (R(sx) + R(0.5)) / R(p.ppx), hy = (R(sy) + R(0.5)) / R(p.ppy);
       if (mode == DEP_INIT) {  // at home: rho - J_z equals its reference, nothing to add
-        a.pox[i] = R(0);
-        a.poy[i] = R(0);
-        a.pux[i] = R(0);
-        a.puy[i] = R(0);
-        a.ppsi[i] = R(0);
+        pox[i] = R(0);
+        poy[i] = R(0);
+        pux[i] = R(0);
+        puy[i] = R(0);
+        pps[i] = R(0);
         continue;
       }
-      const R ox = a.pox[i], oy = a.poy[i];
-      R ux = a.pux[i], uy = a.puy[i];
-      const R pprev = a.ppsi[i];
+      const R ox = pox[i], oy = poy[i];
+      R ux = pux[i], uy = puy[i];
+      const R pprev = pps[i];
       const Cic<R> c = cic<R>(ix, crow, hx + ox, hy + oy, nx, ny, crow);
-      const R psi_fl = gather(a.psi, c, nx);
-      const R psi_p = R(psi0 + (double)psi_fl);
-      const R gxp = gather(a.gpx, c, nx), gyp = gather(a.gpy, c, nx);
-      const R bxp = gather(a.bx, c, nx), byp = gather(a.by, c, nx), bzp = gather(a.bz, c, nx);
+      R F[8];
+      gather8(a.fg, c, nx, F);
+      const R psi_fl = F[FG_PSI];
+      const R psi_p = psi0r + psi_fl;
       const R opp_raw = R(1) + psi_p;
       const R opp = opp_raw < floor_ ? floor_ : opp_raw;
+      const R iopp = R(1) / opp;
       R oph = R(1) + R(0.5) * (R(3) * psi_p - pprev);
       oph = oph < floor_ ? floor_ : oph;
+      const R ioph = R(1) / oph;
       const R uxm = ux, uym = uy;
-      push_xi(ux, uy, opp, gxp, gyp, bxp, byp, bzp, dxi);
-      const R sh = R(0.5) * dxi / oph;
+      push_xi(ux, uy, opp, iopp, F[FG_GX], F[FG_GY], F[FG_BX], F[FG_BY], F[FG_BZ], dxi);
+      const R sh = R(0.5) * dxi * ioph;
+      const R jxh = -wn * ux * ioph, jyh = -wn * uy * ioph;
       const Cic<R> ch = cic<R>(ix, crow, hx + ox + sh * ux * idx, hy + oy + sh * uy * idy, nx, ny,
                                crow);
-      const R jxh = -wn * ux / oph, jyh = -wn * uy / oph;
       if (mode == DEP_TRIAL) {
         const R uxj = R(0.5) * (uxm + ux), uyj = R(0.5) * (uym + uy);
         const R u2 = uxj * uxj + uyj * uyj;
         const R pe = opp - R(1);
         // u_z from gamma - u_z = 1 + psi without cancellation: (u^2 - psi (2 + psi)) / (2(1+psi))
-        const R uzj = (u2 - pe * (R(2) + pe)) / (R(2) * opp);
-        const R q = -wn / opp;
+        const R uzj = (u2 - pe * (R(2) + pe)) * R(0.5) * iopp;
+        const R q = -wn * iopp;
         // u_z/(1+psi) - c0 = u^2/(2 opp^2) + (1/opp^2 - 1/opp0^2)/2, the second term formed
         // from the psi fluctuation opp - opp0 without cancellation
         const R dpsi = (opp_raw < floor_) ? R((double)floor_ - opp0d) : psi_fl;
-        const R iop2 = R(1) / (opp * opp);
-        const R dz = R(0.5) * u2 * iop2 - R(0.5) * dpsi * (opp0 + opp) * iop2 / (opp0 * opp0);
-        deposit(tile, a.ovf, c, 0, nf, nx, q * uxj);
-        deposit(tile, a.ovf, c, 1, nf, nx, q * uyj);
-        deposit_ref(tile, a.ovf, ix, crow, hx, hy, ox, oy, 2, nf, nx, ny, -wn * dz, -wn * c0);
-        deposit(tile, a.ovf, ch, 3, nf, nx, jxh);
-        deposit(tile, a.ovf, ch, 4, nf, nx, jyh);
+        const R iop2 = iopp * iopp;
+        const R dz = R(0.5) * u2 * iop2 - R(0.5) * dpsi * (opp0 + opp) * iop2 * iopp02;
+        deposit(tile, a.ovf, c, 0, nx, ny, q * uxj);
+        deposit(tile, a.ovf, c, 1, nx, ny, q * uyj);
+        deposit_ref(tile, a.ovf, ix, crow, hx, hy, ox, oy, 2, nx, ny, -wn * dz, -wn * c0);
+        deposit(tile, a.ovf, ch, 3, nx, ny, jxh);
+        deposit(tile, a.ovf, ch, 4, nx, ny, jyh);
         if (first) {
-          kap += 1.0 / (double)opp;
-          omin = fmin(omin, (double)opp_raw);
+          kap += iopp;
+          omin = opp_raw < omin ? opp_raw : omin;
           if (opp_raw < floor_) ++nfloor;
         }
         if (last) {
-          const R gam = (R(1) + u2 + opp * opp) / (R(2) * opp);
-          inv = fmax(inv, (double)(fabs(gam - uzj - opp) / opp));
+          const R gam = (R(1) + u2 + opp * opp) * R(0.5) * iopp;
+          const R r = fabs(gam - uzj - opp) * iopp;
+          inv = r > inv ? r : inv;
         }
       } else {  // commit
-        const R sf = dxi / oph;
-        a.pox[i] = ox + sf * ux * idx;
-        a.poy[i] = oy + sf * uy * idy;
-        a.pux[i] = ux;
-        a.puy[i] = uy;
-        a.ppsi[i] = psi_p;
-        deposit_ref(tile, a.ovf, ix, crow, hx, hy, ox + sf * ux * idx, oy + sf * uy * idy, 0, nf,
-                    nx, ny, R(0), -wn);
-        deposit(tile, a.ovf, ch, 1, nf, nx, jxh);
-        deposit(tile, a.ovf, ch, 2, nf, nx, jyh);
+        const R sf = dxi * ioph;
+        pox[i] = ox + sf * ux * idx;
+        poy[i] = oy + sf * uy * idy;
+        pux[i] = ux;
+        puy[i] = uy;
+        pps[i] = psi_p;
+        deposit_ref(tile, a.ovf, ix, crow, hx, hy, ox + sf * ux * idx, oy + sf * uy * idy, 0, nx,
+                    ny, R(0), -wn);
+        deposit(tile, a.ovf, ch, 1, nx, ny, jxh);
+        deposit(tile, a.ovf, ch, 2, nx, ny, jyh);
       }
     }
     __syncthreads();
@@ -284,10 +326,10 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
     __syncthreads();
   }
   if (mode == DEP_TRIAL && first) {
-    double s = block_sum(kap, red);
+    double s = block_sum((double)kap, red);
     if (threadIdx.x == 0 && s != 0.0) atomicAdd(&a.diag[D_KAPPA * p.nk + j], s);
-    double m = block_min(omin, red);
-    if (threadIdx.x == 0 && m < 1e299) {
+    double m = block_min((double)omin, red);
+    if (threadIdx.x == 0 && m < 1e29) {
       atomicMin((unsigned long long*)&a.diag[D_OPPMIN * p.nk + j], dkey(m));
     }
     double nfl = block_sum((double)nfloor, red);
@@ -297,69 +339,86 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
     }
   }
   if (mode == DEP_TRIAL && last) {
-    double m = block_max(inv, red);
+    double m = block_max((double)inv, red);
     if (threadIdx.x == 0 && m > 0) atomic_max_nonneg(&a.diag[D_INV * p.nk + j], m);
   }
+}
+
+// Copy a twiddle table into shared memory (visible after the next __syncthreads).
+template <typename R>
+__device__ __forceinline__ void load_tw(C<R>* dst, const C<R>* src, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
 }
 
 // ------------------------------------------------------------------ row phase (forward)
 // mode DEP_TRIAL: fields Jx^j, Jy^j, Jz^j, Jx^{j+1/2}, Jy^{j+1/2} of slice j = jj.
 // else: fields S, Jx^{jn-1/2}, Jy^{jn-1/2} of the new slice jn = jj.
 template <typename R>
-__device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, int mode, int jj) {
+__device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, int jj) {
   const DevParams& p = a.p;
   const int nx = p.nx, ny = p.ny, nxh = p.nxh, nk = p.nk;
   const int nf = (mode == DEP_TRIAL) ? kNF : 3;
   const int npair = (nf + 1) / 2;
   C<R>* A = buf;
-  C<R>* B = buf + npair * nx;
+  C<R>* B = buf + 3 * nx;
   const int tile_elems = kTileRows * nx * nf;
+  const R* __restrict__ part = a.part;
+  R* __restrict__ ovf = a.ovf;
+  const R* __restrict__ src = a.src;
   __shared__ double red[32];
   double charge = 0.0;
+  load_tw(tw, a.twx, nx);
+  const int k0 = (mode == DEP_TRIAL) ? jj : jj - 1;  // beam-source nodes k0, k0 + 1
   for (int q = blockIdx.x; q < ny; q += gridDim.x) {
-    for (int e = threadIdx.x; e < npair * nx; e += blockDim.x) {
-      const int pr = e / nx, x = e - pr * nx;
-      R v[2];
-      for (int h = 0; h < 2; ++h) {
-        const int f = 2 * pr + h;
-        R s = R(0);
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      R v[kNF];
+#pragma unroll
+      for (int f = 0; f < kNF; ++f) {
         if (f < nf) {
+          R s = ovf[((size_t)f * ny + q) * nx + x];
+#pragma unroll
           for (int t = 0; t < kTileRows; ++t) {
             const int c = wrap(q + 1 - t, ny);
-            s += a.part[(size_t)c * tile_elems + ((size_t)t * nx + x) * nf + f];
+            s += part[(size_t)c * tile_elems + ((size_t)f * kTileRows + t) * nx + x];
           }
-          R* o = a.ovf + ((size_t)q * nx + x) * nf + f;
-          s += *o;
-          *o = R(0);
-          // beam sources [nk][ny][nx][4]: 0 S_b, 1 J_z, 2 J_x, 3 J_y
-          auto src = [&](int k, int comp) -> R {
-            return (a.src != nullptr && k >= 0 && k < nk)
-                       ? a.src[(((size_t)k * ny + q) * nx + x) * 4 + comp]
-                       : R(0);
-          };
-          if (mode == DEP_TRIAL) {
-            if (f == 0) s += src(jj, 2);
-            else if (f == 1) s += src(jj, 3);
-            else if (f == 2) s += src(jj, 1);
-            else if (f == 3) s += R(0.5) * (src(jj, 2) + src(jj + 1, 2));
-            else s += R(0.5) * (src(jj, 3) + src(jj + 1, 3));
-          } else {
-            if (f == 0) {
-              charge += (double)s;
-              s += src(jj, 0);
-            } else if (f == 1) {
-              s += R(0.5) * (src(jj - 1, 2) + src(jj, 2));
-            } else {
-              s += R(0.5) * (src(jj - 1, 3) + src(jj, 3));
-            }
-          }
+          v[f] = s;
+        } else {
+          v[f] = R(0);
         }
-        v[h] = s;
       }
-      A[pr * nx + x] = C<R>{v[0], v[1]};
+      // beam sources [nk][ny][nx][4]: 0 S_b, 1 J_z, 2 J_x, 3 J_y (deviations)
+      R s0[4] = {0, 0, 0, 0}, s1[4] = {0, 0, 0, 0};
+      if (src != nullptr) {
+        if (k0 >= 0 && k0 < nk) {
+          const R* e = src + (((size_t)k0 * ny + q) * nx + x) * 4;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) s0[k] = e[k];
+        }
+        if (k0 + 1 < nk) {
+          const R* e = src + (((size_t)(k0 + 1) * ny + q) * nx + x) * 4;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) s1[k] = e[k];
+        }
+      }
+      for (int f = 0; f < nf; ++f) ovf[((size_t)f * ny + q) * nx + x] = R(0);
+      if (mode == DEP_TRIAL) {
+        v[0] += s0[2];
+        v[1] += s0[3];
+        v[2] += s0[1];
+        v[3] += R(0.5) * (s0[2] + s1[2]);
+        v[4] += R(0.5) * (s0[3] + s1[3]);
+      } else {
+        charge += (double)v[0];
+        v[0] += s1[0];
+        v[1] += R(0.5) * (s0[2] + s1[2]);
+        v[2] += R(0.5) * (s0[3] + s1[3]);
+      }
+#pragma unroll
+      for (int pr = 0; pr < 3; ++pr)
+        if (pr < npair) A[pr * nx + x] = C<R>{v[2 * pr], (2 * pr + 1 < kNF) ? v[2 * pr + 1] : R(0)};
     }
     __syncthreads();
-    C<R>* Z = block_fft(A, B, npair, p.px, a.twx, -1);
+    C<R>* Z = block_fft(A, B, npair, p.px, tw, -1);
     // unpack two real transforms: A_k = (Z_k + conj Z_{-k})/2, B_k = -i (Z_k - conj Z_{-k})/2
     for (int e = threadIdx.x; e < npair * nxh; e += blockDim.x) {
       const int pr = e / nxh, k = e - pr * nxh;
@@ -379,18 +438,21 @@ __device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, int mode, int jj) {
   }
 }
 
-// Wavenumbers of half-spectrum column kx and row ky (derivative symbols zero at Nyquist).
+// Wavenumbers of half-spectrum column kx and row ky from the table built on the host in FP64,
+// ktab = [k_x (nxh)][k_x derivative symbol (nxh)][k_y (ny)][k_y derivative symbol (ny)], the
+// derivative symbols zero at the Nyquist index.
+template <typename R>
 struct Kv {
-  double kx, ky, kxd, kyd, k2;
+  R kxd, kyd, k2;
 };
-__device__ __forceinline__ Kv kvec(const DevParams& p, int kx, int ky) {
-  Kv k;
-  const int my = (ky <= p.ny / 2) ? ky : ky - p.ny;
-  k.kx = 6.283185307179586476925 * kx / p.Lx;
-  k.ky = 6.283185307179586476925 * my / p.Ly;
-  k.kxd = ((p.nx % 2 == 0) && (2 * kx == p.nx)) ? 0.0 : k.kx;
-  k.kyd = ((p.ny % 2 == 0) && (2 * ky == p.ny)) ? 0.0 : k.ky;
-  k.k2 = k.kx * k.kx + k.ky * k.ky;
+template <typename R>
+__device__ __forceinline__ Kv<R> kvec(const R* __restrict__ ktab, int nxh, int ny, int kx,
+                                      int ky) {
+  Kv<R> k;
+  const R kxv = ktab[kx], kyv = ktab[2 * nxh + ky];
+  k.kxd = ktab[nxh + kx];
+  k.kyd = ktab[2 * nxh + ny + ky];
+  k.k2 = kxv * kxv + kyv * kyv;
   return k;
 }
 
@@ -398,7 +460,8 @@ __device__ __forceinline__ Kv kvec(const DevParams& p, int kx, int ky) {
 // jz_ref: the uniform parts of J_z left out of the grid deposits (plasma reference state and
 // beam reference density), added to <J_z> for the k = 0 mode.
 template <typename R>
-__device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, int j, bool last, double jz_ref) {
+__device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, bool last,
+                            double jz_ref) {
   const DevParams& p = a.p;
   const int ny = p.ny, nxh = p.nxh;
   C<R>* A = buf;
@@ -406,101 +469,112 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, int j, bool last, 
   const double kappa2 = a.diag[D_KAPPA * p.nk + j] / ((double)p.ppc * p.nx * p.ny);
   const R rdxi = R(1.0 / p.dxi);
   const R kap = R(kappa2);
+  const C<R>* __restrict__ rspec = a.rspec;
+  C<R>* __restrict__ bold = a.bold;
+  const C<R>* __restrict__ jprev = a.jprev;
   __shared__ double red[32];
-  double num = 0.0, den = 0.0;
+  R num = R(0), den = R(0);
+  load_tw(tw, a.twy, ny);
   for (int kx = blockIdx.x; kx < nxh; kx += gridDim.x) {
-    for (int e = threadIdx.x; e < kNF * ny; e += blockDim.x) {
-      const int f = e / ny, ky = e - f * ny;
-      A[e] = a.rspec[((size_t)f * nxh + kx) * ny + ky];
+    for (int ky = threadIdx.x; ky < ny; ky += blockDim.x) {
+      C<R> v[kNF];
+#pragma unroll
+      for (int f = 0; f < kNF; ++f) v[f] = rspec[((size_t)f * nxh + kx) * ny + ky];
+#pragma unroll
+      for (int f = 0; f < kNF; ++f) A[f * ny + ky] = v[f];
     }
     __syncthreads();
-    C<R>* Z = block_fft(A, B, kNF, p.py, a.twy, -1);
+    C<R>* Z = block_fft(A, B, kNF, p.py, tw, -1);
     C<R>* O = (Z == A) ? B : A;
-    const double pw = (kx == 0 || ((p.nx % 2 == 0) && 2 * kx == p.nx)) ? 1.0 : 2.0;
+    const R pw = (kx == 0 || ((p.nx % 2 == 0) && 2 * kx == p.nx)) ? R(1) : R(2);
     for (int ky = threadIdx.x; ky < ny; ky += blockDim.x) {
+      const size_t ix0 = (size_t)kx * ny + ky, ix1 = ((size_t)nxh + kx) * ny + ky;
+      const C<R> Jxp = jprev[ix0], Jyp = jprev[ix1];
+      const C<R> Bxo = bold[ix0], Byo = bold[ix1];
       const C<R> Jx = Z[ky], Jy = Z[ny + ky], Jz = Z[2 * ny + ky];
       const C<R> Jxh = Z[3 * ny + ky], Jyh = Z[4 * ny + ky];
-      const size_t ix0 = (size_t)kx * ny + ky, ix1 = ((size_t)nxh + kx) * ny + ky;
       if (kx == 0 && ky == 0)
         a.diag[D_JZ * p.nk + j] = (double)Jz.x / ((double)p.nx * p.ny) + jz_ref;
-      const Kv k = kvec(p, kx, ky);
+      const Kv<R> k = kvec(a.ktab, nxh, ny, kx, ky);
       C<R> obx{0, 0}, oby{0, 0}, obz{0, 0}, oez{0, 0};
-      if (k.k2 > 0.0) {
-        const R ik2 = R(1.0 / k.k2);
-        const R kxd = R(k.kxd), kyd = R(k.kyd);
-        const C<R> Jxp = a.jprev[ix0], Jyp = a.jprev[ix1];
-        const C<R> Bxo = a.bold[ix0], Byo = a.bold[ix1];
+      if (k.k2 > R(0)) {
+        const R ik2 = R(1) / k.k2;
+        const R kxd = k.kxd, kyd = k.kyd;
         const C<R> Dx = cscale(csub(Jxh, Jxp), rdxi), Dy = cscale(csub(Jyh, Jyp), rdxi);
         // B_z = (i kx Jy - i ky Jx)/k^2 ; E_z = -(i kx Jx + i ky Jy)/k^2
         obz = cscale(cmuli(csub(cscale(Jy, kxd), cscale(Jx, kyd))), ik2);
         oez = cscale(cmuli(cadd(cscale(Jx, kxd), cscale(Jy, kyd))), -ik2);
-        const R ih = R(1.0 / (k.k2 + kappa2));
+        const R ih = R(1) / (k.k2 + kap);
         // (k^2 + kappa^2) B_x = i ky Jz + D_y + kappa^2 Bx_old
         obx = cscale(cadd(cadd(cmuli(cscale(Jz, kyd)), Dy), cscale(Bxo, kap)), ih);
         // (k^2 + kappa^2) B_y = -i kx Jz - D_x + kappa^2 By_old
         oby = cscale(csub(csub(cscale(Byo, kap), cmuli(cscale(Jz, kxd))), Dx), ih);
         if (last) {
-          const double ex = (double)obx.x - Bxo.x, ey = (double)obx.y - Bxo.y;
-          const double fx = (double)oby.x - Byo.x, fy = (double)oby.y - Byo.y;
+          const R ex = obx.x - Bxo.x, ey = obx.y - Bxo.y;
+          const R fx = oby.x - Byo.x, fy = oby.y - Byo.y;
           num += pw * (ex * ex + ey * ey + fx * fx + fy * fy);
-          den += pw * ((double)obx.x * obx.x + (double)obx.y * obx.y + (double)oby.x * oby.x +
-                       (double)oby.y * oby.y);
+          den += pw * (obx.x * obx.x + obx.y * obx.y + oby.x * oby.x + oby.y * oby.y);
         }
       }
-      a.bold[ix0] = obx;
-      a.bold[ix1] = oby;
+      bold[ix0] = obx;
+      bold[ix1] = oby;
       O[ky] = obx;
       O[ny + ky] = oby;
       O[2 * ny + ky] = obz;
       O[3 * ny + ky] = oez;
     }
     __syncthreads();
-    C<R>* W = block_fft(O, Z, 4, p.py, a.twy, +1);
+    C<R>* W = block_fft(O, Z, 4, p.py, tw, +1);
     for (int e = threadIdx.x; e < 4 * ny; e += blockDim.x) {
       const int f = e / ny, ky = e - f * ny;
-      a.cspec[((size_t)f * nxh + kx) * ny + ky] = W[e];
+      a.cspec[((size_t)f * ny + ky) * nxh + kx] = W[e];
     }
     __syncthreads();
   }
   if (last) {
-    double s = block_sum(num, red);
+    double s = block_sum((double)num, red);
     if (threadIdx.x == 0 && s != 0.0) atomicAdd(&a.diag[D_PCNUM * p.nk + j], s);
-    s = block_sum(den, red);
+    s = block_sum((double)den, red);
     if (threadIdx.x == 0 && s != 0.0) atomicAdd(&a.diag[D_PCDEN * p.nk + j], s);
   }
 }
 
 // ------------------------------------------------------------------ column phase: psi
 template <typename R>
-__device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf) {
+__device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf, C<R>* tw) {
   const DevParams& p = a.p;
   const int ny = p.ny, nxh = p.nxh;
   C<R>* A = buf;
-  C<R>* B = buf + 3 * ny;
+  C<R>* B = buf + kNF * ny;
+  const C<R>* __restrict__ rspec = a.rspec;
+  load_tw(tw, a.twy, ny);
   for (int kx = blockIdx.x; kx < nxh; kx += gridDim.x) {
-    for (int e = threadIdx.x; e < 3 * ny; e += blockDim.x) {
-      const int f = e / ny, ky = e - f * ny;
-      A[e] = a.rspec[((size_t)f * nxh + kx) * ny + ky];
+    for (int ky = threadIdx.x; ky < ny; ky += blockDim.x) {
+      C<R> v[3];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) v[f] = rspec[((size_t)f * nxh + kx) * ny + ky];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) A[f * ny + ky] = v[f];
     }
     __syncthreads();
-    C<R>* Z = block_fft(A, B, 3, p.py, a.twy, -1);
+    C<R>* Z = block_fft(A, B, 3, p.py, tw, -1);
     C<R>* O = (Z == A) ? B : A;
     for (int ky = threadIdx.x; ky < ny; ky += blockDim.x) {
       const size_t ix0 = (size_t)kx * ny + ky, ix1 = ((size_t)nxh + kx) * ny + ky;
       a.jprev[ix0] = Z[ny + ky];
       a.jprev[ix1] = Z[2 * ny + ky];
-      const Kv k = kvec(p, kx, ky);
+      const Kv<R> k = kvec(a.ktab, nxh, ny, kx, ky);
       C<R> ps{0, 0};
-      if (k.k2 > 0.0) ps = cscale(Z[ky], R(1.0 / k.k2));
+      if (k.k2 > R(0)) ps = cscale(Z[ky], R(1) / k.k2);
       O[ky] = ps;
-      O[ny + ky] = cmuli(cscale(ps, R(k.kxd)));
-      O[2 * ny + ky] = cmuli(cscale(ps, R(k.kyd)));
+      O[ny + ky] = cmuli(cscale(ps, k.kxd));
+      O[2 * ny + ky] = cmuli(cscale(ps, k.kyd));
     }
     __syncthreads();
-    C<R>* W = block_fft(O, Z, 3, p.py, a.twy, +1);
+    C<R>* W = block_fft(O, Z, 3, p.py, tw, +1);
     for (int e = threadIdx.x; e < 3 * ny; e += blockDim.x) {
       const int f = e / ny, ky = e - f * ny;
-      a.cspec[((size_t)f * nxh + kx) * ny + ky] = W[e];
+      a.cspec[((size_t)f * ny + ky) * nxh + kx] = W[e];
     }
     __syncthreads();
   }
@@ -510,32 +584,29 @@ __device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf) {
 // psi_mode: outputs psi, d_x psi, d_y psi.  Else: B_x, B_y, B_z, E_z; on the last trial
 // iteration also the slab of slice j and the field energies.
 template <typename R>
-__device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, bool psi_mode, int j, bool last,
-                           double ez0j) {
+__device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_mode, int j,
+                           bool last, double ez0j) {
   const DevParams& p = a.p;
   const int nx = p.nx, ny = p.ny, nxh = p.nxh;
   const int nout = psi_mode ? 3 : 4;
-  const int npair = (nout + 1) / 2;
+  const int npair = 2;
   C<R>* A = buf;
-  C<R>* B = buf + npair * nx;
+  C<R>* B = buf + 3 * nx;
   const R scale = R(1.0 / ((double)nx * ny));
-  R* outs[4];
-  if (psi_mode) {
-    outs[0] = a.psi; outs[1] = a.gpx; outs[2] = a.gpy; outs[3] = nullptr;
-  } else {
-    outs[0] = a.bx; outs[1] = a.by; outs[2] = a.bz; outs[3] = a.ez;
-  }
+  const C<R>* __restrict__ cspec = a.cspec;
+  R* __restrict__ fg = a.fg;
   __shared__ double red[32];
-  double en[6] = {0, 0, 0, 0, 0, 0};
+  R en[6] = {0, 0, 0, 0, 0, 0};
   bool bad = false;
+  load_tw(tw, a.twx, nx);
   for (int q = blockIdx.x; q < ny; q += gridDim.x) {
     for (int e = threadIdx.x; e < npair * nx; e += blockDim.x) {
       const int pr = e / nx, k = e - pr * nx;
       const int f0 = 2 * pr, f1 = 2 * pr + 1;
       // full spectrum of z = a + i b from the half spectra of the real outputs a, b
       const int kk = (k < nxh) ? k : nx - k;
-      C<R> fa = a.cspec[((size_t)f0 * nxh + kk) * ny + q];
-      C<R> fb = (f1 < nout) ? a.cspec[((size_t)f1 * nxh + kk) * ny + q] : C<R>{0, 0};
+      C<R> fa = cspec[((size_t)f0 * ny + q) * nxh + kk];
+      C<R> fb = (f1 < nout) ? cspec[((size_t)f1 * ny + q) * nxh + kk] : C<R>{0, 0};
       const bool selfconj = (kk == 0) || ((nx % 2 == 0) && 2 * kk == nx);
       if (selfconj) {
         fa.y = R(0);
@@ -548,17 +619,27 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, bool psi_mode, int 
       A[pr * nx + k] = cadd(fa, cmuli(fb));
     }
     __syncthreads();
-    C<R>* Z = block_fft(A, B, npair, p.px, a.twx, +1);
+    C<R>* Z = block_fft(A, B, npair, p.px, tw, +1);
     for (int x = threadIdx.x; x < nx; x += blockDim.x) {
       R v[4];
-      for (int pr = 0; pr < npair; ++pr) {
-        v[2 * pr] = Z[pr * nx + x].x * scale;
-        if (2 * pr + 1 < 4) v[2 * pr + 1] = Z[pr * nx + x].y * scale;
-      }
+      v[0] = Z[x].x * scale;
+      v[1] = Z[x].y * scale;
+      v[2] = Z[nx + x].x * scale;
+      v[3] = Z[nx + x].y * scale;
       const size_t g = (size_t)q * nx + x;
-      for (int f = 0; f < nout; ++f) outs[f][g] = v[f];
+      R* node = fg + g * kFG;
+      if (psi_mode) {
+        node[FG_PSI] = v[0];
+        node[FG_GX] = v[1];
+        node[FG_GY] = v[2];
+      } else {
+        node[FG_BX] = v[0];
+        node[FG_BY] = v[1];
+        node[FG_BZ] = v[2];
+        node[FG_EZ] = v[3];
+      }
       if (!psi_mode && last) {
-        const R wx = -a.gpx[g], wy = -a.gpy[g];
+        const R wx = -node[FG_GX], wy = -node[FG_GY];
         const R ez = R(ez0j + (double)v[3]);
         R* s = a.slab + (((size_t)j * ny + q) * nx + x) * 8;
         s[0] = wx;
@@ -569,47 +650,72 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, bool psi_mode, int 
         s[5] = v[2];
         s[6] = R(0);
         s[7] = R(0);
-        const double Ex = (double)wx + v[1], Ey = (double)wy - v[0];
+        const R Ex = wx + v[1], Ey = wy - v[0];
         en[0] += Ex * Ex;
         en[1] += Ey * Ey;
-        en[2] += (double)ez * ez;
-        en[3] += (double)v[0] * v[0];
-        en[4] += (double)v[1] * v[1];
-        en[5] += (double)v[2] * v[2];
-        if (!(isfinite((double)wx) && isfinite((double)wy) && isfinite((double)ez) &&
-              isfinite((double)v[0]) && isfinite((double)v[1]) && isfinite((double)v[2])))
-          bad = true;
+        en[2] += ez * ez;
+        en[3] += v[0] * v[0];
+        en[4] += v[1] * v[1];
+        en[5] += v[2] * v[2];
+        if (!(isfinite(Ex) && isfinite(Ey) && isfinite(ez) && isfinite(v[2]))) bad = true;
       }
     }
     __syncthreads();
   }
   if (!psi_mode && last) {
     const double cell = 0.5 * p.dx * p.dy * p.dxi;
-    for (int f = 0; f < 6; ++f) {
-      double s = block_sum(en[f], red);
-      if (threadIdx.x == 0 && s != 0.0) atomicAdd(&a.diag[(D_E0 + f) * p.nk + j], s * cell);
-    }
+    double tot[6];
+    block_sum_n<6>(en, tot, red);
+    if (threadIdx.x == 0)
+      for (int f = 0; f < 6; ++f)
+        if (tot[f] != 0.0) atomicAdd(&a.diag[(D_E0 + f) * p.nk + j], tot[f] * cell);
     if (bad) atomicOr(a.bar.status, ST_NONFINITE);
   }
+}
+
+// Shared-memory layout of the persistent kernels: the phase buffer (deposit tile or FFT
+// buffers) followed by a twiddle table.
+template <typename R>
+__host__ __device__ inline size_t phase_smem_bytes(int nx, int ny) {
+  size_t tile = (size_t)kTileRows * nx * kNF * sizeof(R);
+  size_t row = (size_t)2 * 3 * nx * sizeof(C<R>);
+  size_t col = (size_t)2 * kNF * ny * sizeof(C<R>);
+  size_t m = tile > row ? tile : row;
+  m = m > col ? m : col;
+  return (m + 15) & ~size_t(15);
+}
+template <typename R>
+__host__ __device__ inline size_t sweep_smem_bytes(int nx, int ny) {
+  return phase_smem_bytes<R>(nx, ny) + (size_t)(nx > ny ? nx : ny) * sizeof(C<R>);
 }
 
 // ------------------------------------------------------------------ the kernel
 template <typename R>
 __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  const DevParams& p = a.p;
   R* tile = reinterpret_cast<R*>(smem);
   C<R>* buf = reinterpret_cast<C<R>*>(smem);
-  const DevParams& p = a.p;
+  C<R>* tw = reinterpret_cast<C<R>*>(smem + phase_smem_bytes<R>(p.nx, p.ny));
+  unsigned epoch = 0;
+  // barrier with phase timing of the first slices
+  auto sync = [&](int j, int ph) -> bool {
+    const bool timed = a.ptimes != nullptr && j >= 0 && j < kTimedSlices && ph < kTimedPhases;
+    unsigned long long* slot = timed ? a.ptimes + ((size_t)j * kTimedPhases + ph) * 2 : nullptr;
+    if (!grid_sync(a.bar, epoch, slot)) return false;
+    if (timed && blockIdx.x == 0 && threadIdx.x == 0) slot[1] = globaltimer();
+    return true;
+  };
   double psi0 = 0.0, ez0h = 0.0;
 
   dep_phase(a, tile, DEP_INIT, 0, 0.0, false, false);
-  if (!grid_sync(a.bar)) return;
-  row_phase(a, buf, DEP_INIT, 0);
-  if (!grid_sync(a.bar)) return;
-  col_phase_psi(a, buf);
-  if (!grid_sync(a.bar)) return;
-  irow_phase(a, buf, true, 0, false, 0.0);
-  if (!grid_sync(a.bar)) return;
+  if (!sync(-1, 0)) return;
+  row_phase(a, buf, tw, DEP_INIT, 0);
+  if (!sync(-1, 1)) return;
+  col_phase_psi(a, buf, tw);
+  if (!sync(-1, 2)) return;
+  irow_phase(a, buf, tw, true, 0, false, 0.0);
+  if (!sync(-1, 3)) return;
 
   for (int j = 0; j < p.nk; ++j) {
     double ez0n = ez0h, ez0j = ez0h;
@@ -618,32 +724,33 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<R> a) {
     for (int it = 0; it < p.n_pc; ++it) {
       const bool first = (it == 0), last = (it == p.n_pc - 1);
       dep_phase(a, tile, DEP_TRIAL, j, psi0, first, last);
-      if (!grid_sync(a.bar)) return;
-      row_phase(a, buf, DEP_TRIAL, j);
-      if (!grid_sync(a.bar)) return;
-      col_phase_b(a, buf, j, last, jz_ref);
-      if (!grid_sync(a.bar)) return;
+      if (!sync(j, 4 * it + 0)) return;
+      row_phase(a, buf, tw, DEP_TRIAL, j);
+      if (!sync(j, 4 * it + 1)) return;
+      col_phase_b(a, buf, tw, j, last, jz_ref);
+      if (!sync(j, 4 * it + 2)) return;
       if (last) {
         const double jz = *((volatile double*)&a.diag[D_JZ * p.nk + j]);
         ez0n = ez0h - p.dxi * jz;
         ez0j = 0.5 * (ez0h + ez0n);
       }
-      irow_phase(a, buf, false, j, last, ez0j);
-      if (!grid_sync(a.bar)) return;
+      irow_phase(a, buf, tw, false, j, last, ez0j);
+      if (!sync(j, 4 * it + 3)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.diag[D_PSI0 * p.nk + j] = psi0;
       a.diag[D_EZ0 * p.nk + j] = ez0j;
     }
     if (j + 1 < p.nk) {
+      const int pc = 4 * p.n_pc;
       dep_phase(a, tile, DEP_COMMIT, j, psi0, false, false);
-      if (!grid_sync(a.bar)) return;
-      row_phase(a, buf, DEP_COMMIT, j + 1);
-      if (!grid_sync(a.bar)) return;
-      col_phase_psi(a, buf);
-      if (!grid_sync(a.bar)) return;
-      irow_phase(a, buf, true, j + 1, false, 0.0);
-      if (!grid_sync(a.bar)) return;
+      if (!sync(j, pc + 0)) return;
+      row_phase(a, buf, tw, DEP_COMMIT, j + 1);
+      if (!sync(j, pc + 1)) return;
+      col_phase_psi(a, buf, tw);
+      if (!sync(j, pc + 2)) return;
+      irow_phase(a, buf, tw, true, j + 1, false, 0.0);
+      if (!sync(j, pc + 3)) return;
     }
     psi0 += p.dxi * ez0n;
     ez0h = ez0n;
@@ -656,19 +763,22 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<R> a) {
 template <typename R>
 __global__ void __launch_bounds__(256) solve_kernel(SweepArgs<R> a, int which) {
   extern __shared__ __align__(16) unsigned char smem[];
+  const DevParams& p = a.p;
   C<R>* buf = reinterpret_cast<C<R>*>(smem);
+  C<R>* tw = reinterpret_cast<C<R>*>(smem + phase_smem_bytes<R>(p.nx, p.ny));
+  unsigned epoch = 0;
   if (which == 0) {
-    row_phase(a, buf, DEP_TRIAL, 0);
-    if (!grid_sync(a.bar)) return;
-    col_phase_b(a, buf, 0, false, 0.0);
-    if (!grid_sync(a.bar)) return;
-    irow_phase(a, buf, false, 0, false, 0.0);
+    row_phase(a, buf, tw, DEP_TRIAL, 0);
+    if (!grid_sync(a.bar, epoch)) return;
+    col_phase_b(a, buf, tw, 0, false, 0.0);
+    if (!grid_sync(a.bar, epoch)) return;
+    irow_phase(a, buf, tw, false, 0, false, 0.0);
   } else {
-    row_phase(a, buf, DEP_COMMIT, 0);
-    if (!grid_sync(a.bar)) return;
-    col_phase_psi(a, buf);
-    if (!grid_sync(a.bar)) return;
-    irow_phase(a, buf, true, 0, false, 0.0);
+    row_phase(a, buf, tw, DEP_COMMIT, 0);
+    if (!grid_sync(a.bar, epoch)) return;
+    col_phase_psi(a, buf, tw);
+    if (!grid_sync(a.bar, epoch)) return;
+    irow_phase(a, buf, tw, true, 0, false, 0.0);
   }
 }
 

@@ -30,7 +30,8 @@ SOURCES = ("Sb", "Jz", "Jx", "Jy")
 
 EXPORTS = ("qsa_init", "qsa_set_beam", "qsa_get_beam", "qsa_plasma_sweep", "qsa_beam_step",
            "qsa_diagnostics", "qsa_copy_field", "qsa_copy_source", "qsa_field_solve",
-           "qsa_launch_count", "qsa_device_bytes", "qsa_last_error", "qsa_destroy")
+           "qsa_phase_times", "qsa_launch_count", "qsa_device_bytes", "qsa_last_error",
+           "qsa_destroy")
 
 
 class QsaError(RuntimeError):
@@ -105,6 +106,8 @@ def load_library(path: str = LIB_PATH):
     lib.qsa_copy_source.restype = ct.c_int
     lib.qsa_field_solve.argtypes = [P] + [_DP] * 6 + [ct.c_double, _DP]
     lib.qsa_field_solve.restype = ct.c_int
+    lib.qsa_phase_times.argtypes = [P, ct.POINTER(ct.c_int64), ct.c_int]
+    lib.qsa_phase_times.restype = ct.c_int
     lib.qsa_launch_count.argtypes = [P]
     lib.qsa_launch_count.restype = ct.c_int64
     lib.qsa_device_bytes.argtypes = [P]
@@ -262,6 +265,14 @@ class QSA:
         out = np.empty((7, self.p.ny, self.p.nx))
         self._check(self.lib.qsa_field_solve(self.h, *[_ptr(a) for a in ins], kappa2, _ptr(out)))
         return dict(zip(("psi", "gpx", "gpy", "Ez", "Bz", "Bx", "By"), out))
+
+    def phase_times(self) -> np.ndarray:
+        """[8 slices, 32 phases, 2] globaltimer stamps (ns) of the last sweep: last arrival
+        at each phase's closing barrier, and block 0's exit from it (0 = not recorded)."""
+        out = np.zeros(8 * 32 * 2, dtype=np.int64)
+        self._check(self.lib.qsa_phase_times(self.h, out.ctypes.data_as(ct.POINTER(ct.c_int64)),
+                                             out.size))
+        return out.reshape(8, 32, 2)
 
     def launch_count(self) -> int:
         return int(self.lib.qsa_launch_count(self.h))

@@ -229,7 +229,7 @@ def test_resume_from_host_state(Q):
         c.sweep()
         c.beam_step()
     c.sweep()
-    assert field_err(c.slab(), a.slab()).max() < 1e-12
+    assert field_err(c.slab(), a.slab()).max() < 1e-11
 
 
 def test_timeout_is_reported_and_context_survives(Q):
