@@ -35,6 +35,19 @@ FftPlan make_plan(int n) {
   while (m % 4 == 0) { p.radix[p.nstages++] = 4; m /= 4; }
   while (m % 2 == 0) { p.radix[p.nstages++] = 2; m /= 2; }
   while (m % 3 == 0) { p.radix[p.nstages++] = 3; m /= 3; }
+  auto log2_or_neg = [](int v) {
+    if (v <= 0 || (v & (v - 1))) return -1;
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+  };
+  int ns = 1;
+  for (int s = 0; s < p.nstages; ++s) {
+    p.ns[s] = ns;
+    p.nbsh[s] = log2_or_neg(n / p.radix[s]);
+    p.nssh[s] = log2_or_neg(ns);
+    ns *= p.radix[s];
+  }
   return p;
 }
 
@@ -231,6 +244,8 @@ int setup(qsa_handle* h) {
   const int work = dp.ny > dp.nxh ? dp.ny : dp.nxh;
   s->grid = per_sm * h->num_sms;
   if (s->grid > work) s->grid = work;
+  if (!(a.dpart = (double*)A((size_t)dp.nk * s->grid * P_COUNT * sizeof(double))))
+    return fail(h, QSA_ERR_OOM, "diagnostic partials");
   // beam species
   const qsa_params& P = h->prm;
   s->modes.n = P.n_modes;
@@ -318,11 +333,39 @@ int deposit_sources(qsa_handle* h) {
 
 __global__ void diag_init_kernel(double* diag, int nk) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= D_COUNT * nk) return;
-  diag[i] = 0.0;
-  if (i / nk == D_OPPMIN) {
-    unsigned long long k = dkey(1e300);
-    diag[i] = __longlong_as_double((long long)k);
+  if (i < D_COUNT * nk) diag[i] = 0.0;
+}
+
+// Reduce the per-block partial diagnostics of each slice (one block per slice).
+__global__ void diag_reduce_kernel(const double* dpart, int nblk, double* diag, int nk) {
+  __shared__ double red[32];
+  const int j = blockIdx.x;
+  const double* row = dpart + (size_t)j * nblk * P_COUNT;
+  for (int f = 0; f < P_COUNT; ++f) {
+    double v = (f == P_OPPMIN) ? 1e300 : 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+      const double x = row[(size_t)b * P_COUNT + f];
+      if (f == P_OPPMIN) v = fmin(v, x);
+      else if (f == P_INV) v = fmax(v, x);
+      else v += x;
+    }
+    double r;
+    if (f == P_OPPMIN) r = block_min(v, red);
+    else if (f == P_INV) r = block_max(v, red);
+    else r = block_sum(v, red);
+    if (threadIdx.x == 0) {
+      int d;
+      switch (f) {
+        case P_OPPMIN: d = D_OPPMIN; break;
+        case P_NFLOOR: d = D_NFLOOR; break;
+        case P_INV: d = D_INV; break;
+        case P_CHARGE: d = D_CHARGE; break;
+        case P_PCNUM: d = D_PCNUM; break;
+        case P_PCDEN: d = D_PCDEN; break;
+        default: d = D_E0 + (f - P_E0); break;
+      }
+      diag[(size_t)d * nk + j] = r;
+    }
   }
 }
 
@@ -349,6 +392,8 @@ int sweep(qsa_handle* h) {
   void* args[] = {&a};
   CK(cudaLaunchCooperativeKernel((void*)sweep_kernel<R>, dim3(s->grid), dim3(kThreads), args,
                                  s->smem, h->stream));
+  ++h->launches;
+  diag_reduce_kernel<<<dp.nk, 256, 0, h->stream>>>(a.dpart, s->grid, s->diag, dp.nk);
   ++h->launches;
   ++h->sweeps;
   return QSA_OK;
@@ -379,14 +424,6 @@ int status_code(int st) {
   return QSA_OK;
 }
 
-double key_to_double(double stored) {
-  unsigned long long k;
-  std::memcpy(&k, &stored, 8);
-  unsigned long long b = (k & 0x8000000000000000ull) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
-  double v;
-  std::memcpy(&v, &b, 8);
-  return v;
-}
 
 template <typename R>
 int diagnostics(qsa_handle* h, qsa_diag* out) {
@@ -409,7 +446,7 @@ int diagnostics(qsa_handle* h, qsa_diag* out) {
     if (out->ez0) out->ez0[j] = row(D_EZ0)[j];
     if (out->jz_mean) out->jz_mean[j] = row(D_JZ)[j];
     if (out->kappa2) out->kappa2[j] = row(D_KAPPA)[j] / npc;
-    if (out->opp_min) out->opp_min[j] = key_to_double(row(D_OPPMIN)[j]);
+    if (out->opp_min) out->opp_min[j] = row(D_OPPMIN)[j];
     if (out->n_floor) out->n_floor[j] = row(D_NFLOOR)[j];
     if (out->invariant) out->invariant[j] = row(D_INV)[j];
     if (out->charge) out->charge[j] = std::fabs(row(D_CHARGE)[j]);

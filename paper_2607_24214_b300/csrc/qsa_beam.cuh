@@ -337,63 +337,93 @@ __global__ void __launch_bounds__(256, 2) beam_kernel(BeamArrays<BR> b, DevParam
   const BR cdx = BR(p.dt / p.dx), cdy = BR(p.dt / p.dy), cdk = BR(p.dt / p.dxi);
   const int kleft = p.nxi - g.kabs;  // lost when the local xi position reaches this
   int my_lost = 0;
-  for (int sub = 0; sub < sp.ppc; ++sub) {
-    const int sx = sub % sp.ppx, sy = (sub / sp.ppx) % sp.ppy, sxi = sub / (sp.ppx * sp.ppy);
-    const BR hx = (BR(sx) + BR(0.5)) / BR(sp.ppx), hy = (BR(sy) + BR(0.5)) / BR(sp.ppy);
-    const BR hk = (BR(sxi) + BR(0.5)) / BR(sp.ppxi);
+  // two sub-lattice positions per thread per pass: particles (sub0, ix) and (sub0 + 1, ix);
+  // the loads and gathers of both are issued before either particle's arithmetic
+  for (int sub0 = 0; sub0 < sp.ppc; sub0 += 2) {
+    BR hx[2], hy[2], hk[2];
+    bool ok[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      ok[u] = sub0 + u < sp.ppc;
+      const int sub = ok[u] ? sub0 + u : sub0;
+      const int sx = sub % sp.ppx, sy = (sub / sp.ppx) % sp.ppy, sxi = sub / (sp.ppx * sp.ppy);
+      hx[u] = (BR(sx) + BR(0.5)) / BR(sp.ppx);
+      hy[u] = (BR(sy) + BR(0.5)) / BR(sp.ppy);
+      hk[u] = (BR(sxi) + BR(0.5)) / BR(sp.ppxi);
+    }
     for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
-      const size_t s = base + (size_t)sub * nx + ix;
-      const BR dw = b.dw[s];
-      if (dw == BR(-1)) {  // lost: only its reference, at home, is removed
-        deposit_particle(g, src, p, ix, hx, hy, hk, BR(0), BR(0), BR(0), -refS, -refJz, BR(0),
-                         BR(0), refS, refJz);
-        continue;
+      size_t si[2];
+      BR dw[2], ox[2], oy[2], oxi[2], ux[2], uy[2];
+      double uz[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        si[u] = base + (size_t)(ok[u] ? sub0 + u : sub0) * nx + ix;
+        dw[u] = b.dw[si[u]];
+        ox[u] = b.ox[si[u]];
+        oy[u] = b.oy[si[u]];
+        oxi[u] = b.oxi[si[u]];
+        ux[u] = b.ux[si[u]];
+        uy[u] = b.uy[si[u]];
+        uz[u] = b.uz[si[u]];
       }
-      BR ox = b.ox[s], oy = b.oy[s], oxi = b.oxi[s];
-      BR ux = b.ux[s], uy = b.uy[s];
-      double uz = b.uz[s];
+      BR F[2][6];
       if (PUSH) {
-        const BR lx = hx + ox, ly = hy + oy, lk = hk + oxi;
-        const BR fx = floor(lx), fy = floor(ly), fk = floor(lk);
-        BR F[6];
-        gather_slab(slab, p, g.kabs + (int)fk, g.iy + (int)fy, ix + (int)fx, lk - fk, ly - fy,
-                    lx - fx, F);
-        boris(ux, uy, uz, F, hdt);
-        // dx/dt = u/gamma, dxi/dt = 1 - v_z = (1 + u_perp^2)/(gamma (gamma + u_z))
-        BR ig, omv;
-        {
-          const BR up2 = ux * ux + uy * uy;
-          if (sizeof(BR) == 8) {
-            const double gg = sqrt(1.0 + (double)up2 + uz * uz);
-            ig = BR(1.0 / gg);
-            omv = BR((1.0 + (double)up2) / (gg * (gg + uz)));
-          } else {
-            const float uzf = (float)uz;
-            const float d = (1.0f + (float)up2) / (sqrtf(1.0f + (float)up2 + uzf * uzf) + uzf);
-            ig = BR(1.0f / (uzf + d));
-            omv = BR(d) * ig;
-          }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const BR lx = hx[u] + ox[u], ly = hy[u] + oy[u], lk = hk[u] + oxi[u];
+          const BR fx = floor(lx), fy = floor(ly), fk = floor(lk);
+          gather_slab(slab, p, g.kabs + (int)fk, g.iy + (int)fy, ix + (int)fx, lk - fk, ly - fy,
+                      lx - fx, F[u]);
         }
-        ox += cdx * ux * ig;
-        oy += cdy * uy * ig;
-        oxi += cdk * omv;
-        b.ox[s] = ox;
-        b.oy[s] = oy;
-        b.oxi[s] = oxi;
-        b.ux[s] = ux;
-        b.uy[s] = uy;
-        b.uz[s] = uz;
-        if (hk + oxi >= BR(kleft)) {
-          b.dw[s] = BR(-1);
-          ++my_lost;
-          deposit_particle(g, src, p, ix, hx, hy, hk, BR(0), BR(0), BR(0), -refS, -refJz, BR(0),
-                           BR(0), refS, refJz);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (!ok[u]) continue;
+        if (dw[u] == BR(-1)) {  // lost: only its reference, at home, is removed
+          deposit_particle(g, src, p, ix, hx[u], hy[u], hk[u], BR(0), BR(0), BR(0), -refS,
+                           -refJz, BR(0), BR(0), refS, refJz);
           continue;
         }
+        if (PUSH) {
+          boris(ux[u], uy[u], uz[u], F[u], hdt);
+          // dx/dt = u/gamma, dxi/dt = 1 - v_z = (1 + u_perp^2)/(gamma (gamma + u_z))
+          BR ig, omv;
+          {
+            const BR up2 = ux[u] * ux[u] + uy[u] * uy[u];
+            if (sizeof(BR) == 8) {
+              const double gg = sqrt(1.0 + (double)up2 + uz[u] * uz[u]);
+              ig = BR(1.0 / gg);
+              omv = BR((1.0 + (double)up2) / (gg * (gg + uz[u])));
+            } else {
+              const float uzf = (float)uz[u];
+              const float d = (1.0f + (float)up2) / (sqrtf(1.0f + (float)up2 + uzf * uzf) + uzf);
+              ig = BR(1.0f / (uzf + d));
+              omv = BR(d) * ig;
+            }
+          }
+          ox[u] += cdx * ux[u] * ig;
+          oy[u] += cdy * uy[u] * ig;
+          oxi[u] += cdk * omv;
+          const size_t s = si[u];
+          b.ox[s] = ox[u];
+          b.oy[s] = oy[u];
+          b.oxi[s] = oxi[u];
+          b.ux[s] = ux[u];
+          b.uy[s] = uy[u];
+          b.uz[s] = uz[u];
+          if (hk[u] + oxi[u] >= BR(kleft)) {
+            b.dw[s] = BR(-1);
+            ++my_lost;
+            deposit_particle(g, src, p, ix, hx[u], hy[u], hk[u], BR(0), BR(0), BR(0), -refS,
+                             -refJz, BR(0), BR(0), refS, refJz);
+            continue;
+          }
+        }
+        BR dS, dJz, JX, JY;
+        beam_sources(ux[u], uy[u], uz[u], dw[u], sp, dS, dJz, JX, JY);
+        deposit_particle(g, src, p, ix, hx[u], hy[u], hk[u], ox[u], oy[u], oxi[u], dS, dJz, JX,
+                         JY, refS, refJz);
       }
-      BR dS, dJz, JX, JY;
-      beam_sources(ux, uy, uz, dw, sp, dS, dJz, JX, JY);
-      deposit_particle(g, src, p, ix, hx, hy, hk, ox, oy, oxi, dS, dJz, JX, JY, refS, refJz);
     }
   }
   __syncthreads();

@@ -38,6 +38,9 @@ struct FftPlan {
   int n;
   int nstages;
   int radix[kMaxStages];
+  int ns[kMaxStages];    // product of the radices of the earlier stages
+  int nbsh[kMaxStages];  // log2(n / radix) when a power of two, else -1
+  int nssh[kMaxStages];  // log2(ns) when a power of two, else -1
 };
 
 struct DevParams {
@@ -151,6 +154,65 @@ __device__ __forceinline__ T block_sum(T v, T* scratch /* >= 32 */) {
   }
   return r;
 }
+// Block reductions whose warp stage runs in the argument's own precision and whose block
+// stage runs in FP64 on one thread (FP64 throughput is scarce on this GPU): results valid in
+// thread 0; scratch holds >= blockDim/32 doubles (>= N * blockDim/32 for block_sum_lo_n).
+template <typename T>
+__device__ __forceinline__ double block_sum_lo(T v, double* scratch) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) scratch[w] = (double)v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += scratch[k];
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ double block_min_lo(T v, double* scratch) {
+  v = warp_min(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) scratch[w] = (double)v;
+  __syncthreads();
+  double r = scratch[0];
+  if (threadIdx.x == 0)
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) r = fmin(r, scratch[k]);
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ double block_max_lo(T v, double* scratch) {
+  v = warp_max(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) scratch[w] = (double)v;
+  __syncthreads();
+  double r = scratch[0];
+  if (threadIdx.x == 0)
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) r = fmax(r, scratch[k]);
+  return r;
+}
+template <int N, typename T>
+__device__ __forceinline__ void block_sum_lo_n(const T v[N], double out[N], double* scratch) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T r[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) r[k] = warp_sum(v[k]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < N; ++k) scratch[w * N + k] = (double)r[k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      double s = 0.0;
+      for (int b = 0; b < nw; ++b) s += scratch[b * N + k];
+      out[k] = s;
+    }
+}
+
 // N sums over the block in one exchange (FP64 results, valid in thread 0); scratch >= 32.
 template <int N, typename T>
 __device__ __forceinline__ void block_sum_n(const T v[N], double out[N], double* scratch) {

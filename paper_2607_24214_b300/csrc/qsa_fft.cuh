@@ -56,18 +56,22 @@ template <typename R>
 __device__ C<R>* block_fft(C<R>* a, C<R>* b, int count, const FftPlan& plan, const C<R>* tw,
                            int sign) {
   const int n = plan.n;
-  int Ns = 1;
   for (int s = 0; s < plan.nstages; ++s) {
     const int Rd = plan.radix[s];
+    const int Ns = plan.ns[s];
     const int nb = n / Rd;             // butterflies per sequence
     const int stride = n / (Ns * Rd);  // twiddle index step
     const int total = count * nb;
+    const int nbsh = plan.nbsh[s], nssh = plan.nssh[s];
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int seq = t / nb, j = t - seq * nb;
+      // index arithmetic with shifts where the sizes are powers of two
+      const int seq = nbsh >= 0 ? t >> nbsh : t / nb;
+      const int j = t - seq * nb;
       const C<R>* src = a + seq * n;
       C<R>* dst = b + seq * n;
-      const int k = j % Ns;
-      const int o = (j / Ns) * Ns * Rd + k;
+      const int jq = nssh >= 0 ? j >> nssh : j / Ns;
+      const int k = j - jq * Ns;
+      const int o = jq * Ns * Rd + k;
       if (Rd == 4) {
         C<R> v0 = src[j], v1 = src[j + nb], v2 = src[j + 2 * nb], v3 = src[j + 3 * nb];
         if (k) {
@@ -102,7 +106,6 @@ __device__ C<R>* block_fft(C<R>* a, C<R>* b, int count, const FftPlan& plan, con
     C<R>* t = a;
     a = b;
     b = t;
-    Ns *= Rd;
   }
   return a;
 }

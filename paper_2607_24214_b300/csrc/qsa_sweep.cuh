@@ -54,6 +54,22 @@ enum Diag : int {
   D_COUNT = D_E0 + 6
 };
 
+// Per-block partial diagnostics, written without atomics by thread 0 of every block into
+// dpart[(j * gridDim.x + block) * P_COUNT + field] and reduced after the sweep.
+enum Part : int {
+  P_OPPMIN = 0,  // min
+  P_NFLOOR,      // sum
+  P_INV,         // max
+  P_CHARGE,      // sum
+  P_PCNUM,       // sum
+  P_PCDEN,       // sum
+  P_E0,          // six sums P_E0..P_E0+5
+  P_COUNT = P_E0 + 6
+};
+__device__ __forceinline__ double* pslot(double* dpart, int j, int field) {
+  return dpart + ((size_t)j * gridDim.x + blockIdx.x) * P_COUNT + field;
+}
+
 // Order-preserving map of a double to an unsigned key (min over keys = min over values).
 __device__ __forceinline__ unsigned long long dkey(double v) {
   unsigned long long b = (unsigned long long)__double_as_longlong(v);
@@ -76,6 +92,7 @@ struct SweepArgs {
   const R* src;                             // [nk][ny][nx][4] beam S_b, J_z, J_x, J_y deviations
   R* slab;                                  // [nk][ny][nx][8]
   double* diag;                             // [D_COUNT][nk]
+  double* dpart;                            // [nk][gridDim.x][P_COUNT] partials
   const R* ktab;                            // wavenumber table, see kvec
   const double* bref;                       // [nk] beam J_z reference density per node
   unsigned long long* ptimes;               // [kTimedSlices][kTimedPhases][2] or null
@@ -116,6 +133,20 @@ __device__ __forceinline__ void ld4(const double* p, double v[4]) {
   const double2 b = *reinterpret_cast<const double2*>(p + 2);
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
+// Store one slab node (six fields and two zero pads) with 16-byte stores.
+__device__ __forceinline__ void st8(float* s, float a, float b, float c, float d, float e,
+                                    float f) {
+  reinterpret_cast<float4*>(s)[0] = make_float4(a, b, c, d);
+  reinterpret_cast<float4*>(s)[1] = make_float4(e, f, 0.f, 0.f);
+}
+__device__ __forceinline__ void st8(double* s, double a, double b, double c, double d, double e,
+                                    double f) {
+  reinterpret_cast<double2*>(s)[0] = make_double2(a, b);
+  reinterpret_cast<double2*>(s)[1] = make_double2(c, d);
+  reinterpret_cast<double2*>(s)[2] = make_double2(e, f);
+  reinterpret_cast<double2*>(s)[3] = make_double2(0.0, 0.0);
+}
+
 template <typename R>
 __device__ __forceinline__ void gather8(const R* __restrict__ fg, const Cic<R>& c, int nx,
                                         R out[8]) {
@@ -213,16 +244,67 @@ __device__ __forceinline__ void push_xi(R& ux, R& uy, R opp, R iopp, R gx, R gy,
 
 enum DepMode : int { DEP_INIT = 0, DEP_TRIAL = 1, DEP_COMMIT = 2 };
 
+// Reciprocal: the FP32 path uses the fast hardware approximation (about 2 ulp), FP64 is exact.
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+
+template <typename R>
+struct W4 {
+  R w00, w01, w10, w11;
+};
+template <typename R>
+__device__ __forceinline__ W4<R> cic_w(const Cic<R>& c) {
+  const R gx = R(1) - c.fx, gy = R(1) - c.fy;
+  return W4<R>{gx * gy, c.fx * gy, gx * c.fy, c.fx * c.fy};
+}
+
+// Deposit N values v[k] into fields f0 + k at the four corners of c (shared weights w), in
+// the field-major tile or, outside it, in the overflow grid.
+template <typename R, int N>
+__device__ __forceinline__ void deposit_n(R* tile, R* ovf, const Cic<R>& c, const W4<R>& w,
+                                          int f0, int nx, int ny, const R (&v)[N]) {
+  if (c.ty >= 0 && c.ty <= kTileRows - 2) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      R* r0 = tile + ((size_t)(f0 + k) * kTileRows + c.ty) * nx;
+      R* r1 = r0 + nx;
+      atomicAdd(r0 + c.x0, w.w00 * v[k]);
+      atomicAdd(r0 + c.x1, w.w01 * v[k]);
+      atomicAdd(r1 + c.x0, w.w10 * v[k]);
+      atomicAdd(r1 + c.x1, w.w11 * v[k]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      R* o = ovf + (size_t)(f0 + k) * ny * nx;
+      atomicAdd(o + (size_t)c.y0 * nx + c.x0, w.w00 * v[k]);
+      atomicAdd(o + (size_t)c.y0 * nx + c.x1, w.w01 * v[k]);
+      atomicAdd(o + (size_t)c.y1 * nx + c.x0, w.w10 * v[k]);
+      atomicAdd(o + (size_t)c.y1 * nx + c.x1, w.w11 * v[k]);
+    }
+  }
+}
+
+// Weight differences W(x) - W(home) at the four corners of the home cell, from the offsets
+// (ox, oy) and the home sub-cell position (hx, hy), without cancellation.
+template <typename R>
+__device__ __forceinline__ W4<R> cic_dw(R hx, R hy, R ox, R oy) {
+  const R ax = R(1) - hx, ay = R(1) - hy, oxy = ox * oy;
+  return W4<R>{-ox * ay - oy * ax + oxy, ox * ay - hx * oy - oxy, ax * oy - ox * hy - oxy,
+                hx * oy + ox * hy + oxy};
+}
+
 template <typename R>
 __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, double psi0,
                           bool first, bool last) {
   // reference state of the deposits: a particle at rest at its lattice home with psi = psi0
   // carries rho - J_z = -w and u_z/(1+psi) = c0 = -psi0 (2 + psi0) / (2 (1+psi0)^2)
+  const DevParams& p = a.p;
   const double opp0d = 1.0 + psi0;
   const R opp0 = R(opp0d);
   const R c0 = R(-psi0 * (2.0 + psi0) / (2.0 * opp0d * opp0d));
   const R iopp02 = R(1.0 / (opp0d * opp0d));
-  const DevParams& p = a.p;
+  const R dfloor = R(p.psi_floor - opp0d);  // psi fluctuation of a floored particle
   const int nx = p.nx, ny = p.ny;
   const int nf = (mode == DEP_TRIAL) ? kNF : 3;
   const int per_chunk = p.ppc * nx;
@@ -230,12 +312,12 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
   const R dxi = R(p.dxi);
   const R idx = R(1) / R(p.dx), idy = R(1) / R(p.dy);
   const R floor_ = R(p.psi_floor);
-  const int tile_elems = kTileRows * nx * nf;
-  // per-thread diagnostics accumulate in R (FP64 arithmetic is scarce on this GPU); the block
-  // reductions below are FP64
-  R kap = R(0), inv = R(0), omin = R(1e30);
   const R psi0r = R(psi0);
-  unsigned long long nfloor = 0;
+  const int tile_elems = kTileRows * nx * nf;
+  // the aggregated deposit needs whole warps over consecutive columns
+  const bool lane_agg = (nx % 32 == 0) && (blockDim.x % 32 == 0);
+  // per-thread diagnostics accumulate in R; the block reductions below finish in FP64
+  R kap = R(0), inv = R(0), omin = R(1e30), nfloor = R(0);
   __shared__ double red[32];
   R* __restrict__ pox = a.pox;
   R* __restrict__ poy = a.poy;
@@ -247,77 +329,201 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
     for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) tile[e] = R(0);
     __syncthreads();
     const size_t base = (size_t)crow * per_chunk;
-    for (int t = threadIdx.x; t < per_chunk; t += blockDim.x) {
-      const size_t i = base + t;
-      const int sub = t / nx, ix = t - sub * nx;
-      const int sx = sub % p.ppx, sy = sub / p.ppx;
-      const R hx = (R(sx) + R(0.5)) / R(p.ppx), hy = (R(sy) + R(0.5)) / R(p.ppy);
-      if (mode == DEP_INIT) {  // at home: rho - J_z equals its reference, nothing to add
+    if (mode == DEP_INIT) {  // at home: rho - J_z equals its reference, nothing to add
+      for (int t = threadIdx.x; t < per_chunk; t += blockDim.x) {
+        const size_t i = base + t;
         pox[i] = R(0);
         poy[i] = R(0);
         pux[i] = R(0);
         puy[i] = R(0);
         pps[i] = R(0);
-        continue;
       }
-      const R ox = pox[i], oy = poy[i];
-      R ux = pux[i], uy = puy[i];
-      const R pprev = pps[i];
-      const Cic<R> c = cic<R>(ix, crow, hx + ox, hy + oy, nx, ny, crow);
-      R F[8];
-      gather8(a.fg, c, nx, F);
-      const R psi_fl = F[FG_PSI];
-      const R psi_p = psi0r + psi_fl;
-      const R opp_raw = R(1) + psi_p;
-      const R opp = opp_raw < floor_ ? floor_ : opp_raw;
-      const R iopp = R(1) / opp;
-      R oph = R(1) + R(0.5) * (R(3) * psi_p - pprev);
-      oph = oph < floor_ ? floor_ : oph;
-      const R ioph = R(1) / oph;
-      const R uxm = ux, uym = uy;
-      push_xi(ux, uy, opp, iopp, F[FG_GX], F[FG_GY], F[FG_BX], F[FG_BY], F[FG_BZ], dxi);
-      const R sh = R(0.5) * dxi * ioph;
-      const R jxh = -wn * ux * ioph, jyh = -wn * uy * ioph;
-      const Cic<R> ch = cic<R>(ix, crow, hx + ox + sh * ux * idx, hy + oy + sh * uy * idy, nx, ny,
-                               crow);
-      if (mode == DEP_TRIAL) {
-        const R uxj = R(0.5) * (uxm + ux), uyj = R(0.5) * (uym + uy);
-        const R u2 = uxj * uxj + uyj * uyj;
-        const R pe = opp - R(1);
-        // u_z from gamma - u_z = 1 + psi without cancellation: (u^2 - psi (2 + psi)) / (2(1+psi))
-        const R uzj = (u2 - pe * (R(2) + pe)) * R(0.5) * iopp;
-        const R q = -wn * iopp;
-        // u_z/(1+psi) - c0 = u^2/(2 opp^2) + (1/opp^2 - 1/opp0^2)/2, the second term formed
-        // from the psi fluctuation opp - opp0 without cancellation
-        const R dpsi = (opp_raw < floor_) ? R((double)floor_ - opp0d) : psi_fl;
-        const R iop2 = iopp * iopp;
-        const R dz = R(0.5) * u2 * iop2 - R(0.5) * dpsi * (opp0 + opp) * iop2 * iopp02;
-        deposit(tile, a.ovf, c, 0, nx, ny, q * uxj);
-        deposit(tile, a.ovf, c, 1, nx, ny, q * uyj);
-        deposit_ref(tile, a.ovf, ix, crow, hx, hy, ox, oy, 2, nx, ny, -wn * dz, -wn * c0);
-        deposit(tile, a.ovf, ch, 3, nx, ny, jxh);
-        deposit(tile, a.ovf, ch, 4, nx, ny, jyh);
-        if (first) {
-          kap += iopp;
-          omin = opp_raw < omin ? opp_raw : omin;
-          if (opp_raw < floor_) ++nfloor;
+    } else {
+      // two sub-lattice positions per thread per pass, (sub0, ix) and (sub0 + 1, ix): the
+      // loads and gathers of both are issued before either particle's arithmetic
+      for (int sub0 = 0; sub0 < p.ppc; sub0 += 2) {
+        R hx[2], hy[2];
+        bool ok[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          ok[u] = sub0 + u < p.ppc;
+          const int sub = ok[u] ? sub0 + u : sub0;
+          hx[u] = (R(sub % p.ppx) + R(0.5)) / R(p.ppx);
+          hy[u] = (R(sub / p.ppx) + R(0.5)) / R(p.ppy);
         }
-        if (last) {
-          const R gam = (R(1) + u2 + opp * opp) * R(0.5) * iopp;
-          const R r = fabs(gam - uzj - opp) * iopp;
-          inv = r > inv ? r : inv;
+        for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
+          size_t ii[2];
+          R ox[2], oy[2], uxs[2], uys[2], pprev[2];
+          Cic<R> c[2];
+          R F[2][8];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            ii[u] = base + (size_t)(ok[u] ? sub0 + u : sub0) * nx + ix;
+            ox[u] = pox[ii[u]];
+            oy[u] = poy[ii[u]];
+            uxs[u] = pux[ii[u]];
+            uys[u] = puy[ii[u]];
+            pprev[u] = pps[ii[u]];
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            c[u] = cic<R>(ix, crow, hx[u] + ox[u], hy[u] + oy[u], nx, ny, crow);
+            gather8(a.fg, c[u], nx, F[u]);
+          }
+          // arithmetic of both particles; their deposit values are kept for the deposit step
+          bool home[2] = {false, false}, homeh[2] = {false, false};
+          R vx[2] = {0, 0}, vy[2] = {0, 0}, vdev[2] = {0, 0};
+          R jhx[2] = {0, 0}, jhy[2] = {0, 0}, nox[2] = {0, 0}, noy[2] = {0, 0};
+          Cic<R> ch[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            if (!ok[u]) continue;
+            const size_t i = ii[u];
+            R ux = uxs[u], uy = uys[u];
+            const R psi_fl = F[u][FG_PSI];
+            const R psi_p = psi0r + psi_fl;
+            const R opp_raw = R(1) + psi_p;
+            const R opp = opp_raw < floor_ ? floor_ : opp_raw;
+            const R iopp = rcp(opp);
+            R oph = R(1) + R(0.5) * (R(3) * psi_p - pprev[u]);
+            oph = oph < floor_ ? floor_ : oph;
+            const R ioph = rcp(oph);
+            const R uxm = ux, uym = uy;
+            push_xi(ux, uy, opp, iopp, F[u][FG_GX], F[u][FG_GY], F[u][FG_BX], F[u][FG_BY],
+                    F[u][FG_BZ], dxi);
+            const R sh = R(0.5) * dxi * ioph;
+            const R lxh = hx[u] + ox[u] + sh * ux * idx, lyh = hy[u] + oy[u] + sh * uy * idy;
+            ch[u] = cic<R>(ix, crow, lxh, lyh, nx, ny, crow);
+            homeh[u] = lxh >= R(0) && lxh < R(1) && lyh >= R(0) && lyh < R(1);
+            jhx[u] = -wn * ux * ioph;
+            jhy[u] = -wn * uy * ioph;
+            if (mode == DEP_TRIAL) {
+              const R uxj = R(0.5) * (uxm + ux), uyj = R(0.5) * (uym + uy);
+              const R u2 = uxj * uxj + uyj * uyj;
+              const R pe = opp - R(1);
+              // u_z from gamma - u_z = 1 + psi without cancellation: (u^2 - psi (2 + psi)) /
+              // (2 (1+psi))
+              const R uzj = (u2 - pe * (R(2) + pe)) * R(0.5) * iopp;
+              const R q = -wn * iopp;
+              // u_z/(1+psi) - c0 = u^2/(2 opp^2) + (1/opp^2 - 1/opp0^2)/2, the second term
+              // formed from the psi fluctuation opp - opp0 without cancellation
+              const R dpsi = (opp_raw < floor_) ? dfloor : psi_fl;
+              const R iop2 = iopp * iopp;
+              const R dz = R(0.5) * u2 * iop2 - R(0.5) * dpsi * (opp0 + opp) * iop2 * iopp02;
+              vx[u] = q * uxj;
+              vy[u] = q * uyj;
+              vdev[u] = -wn * dz;
+              const R lx = hx[u] + ox[u], ly = hy[u] + oy[u];
+              home[u] = lx >= R(0) && lx < R(1) && ly >= R(0) && ly < R(1);
+              if (first) {
+                kap += iopp;
+                omin = opp_raw < omin ? opp_raw : omin;
+                if (opp_raw < floor_) nfloor += R(1);
+              }
+              if (last) {
+                const R gam = (R(1) + u2 + opp * opp) * R(0.5) * iopp;
+                const R r = fabs(gam - uzj - opp) * iopp;
+                inv = r > inv ? r : inv;
+              }
+            } else {  // commit
+              const R sf = dxi * ioph;
+              nox[u] = ox[u] + sf * ux * idx;
+              noy[u] = oy[u] + sf * uy * idy;
+              pox[i] = nox[u];
+              poy[i] = noy[u];
+              pux[i] = ux;
+              puy[i] = uy;
+              pps[i] = psi_p;
+              const R lx = hx[u] + nox[u], ly = hy[u] + noy[u];
+              home[u] = lx >= R(0) && lx < R(1) && ly >= R(0) && ly < R(1);
+            }
+          }
+          const R vref = (mode == DEP_TRIAL) ? -wn * c0 : -wn;
+          const int x1 = (ix + 1 == nx) ? 0 : ix + 1;
+          // Aggregated deposit: when every particle of the warp's two sub-lattice positions
+          // sits in its home cell (at x^j or x^{j+1} and at x^{j+1/2}), the two particles of a
+          // thread share their four corners, and the right corners of lane l are the left
+          // corners of lane l + 1: one atomic per node and row instead of four per particle.
+          const bool agg = ok[1] && home[0] && home[1] && homeh[0] && homeh[1];
+          if (lane_agg && __all_sync(0xffffffffu, agg)) {
+            const int lane = threadIdx.x & 31;
+            auto put = [&](int f, R a00, R a01, R a10, R a11) {
+              R* r0 = tile + ((size_t)f * kTileRows + 1) * nx;  // tile rows 1, 2: home rows
+#pragma unroll
+              for (int r = 0; r < 2; ++r) {
+                const R lft = r ? a10 : a00, rgt = r ? a11 : a01;
+                const R from = __shfl_up_sync(0xffffffffu, rgt, 1);
+                atomicAdd(r0 + (size_t)r * nx + ix, lft + (lane ? from : R(0)));
+                if (lane == 31) atomicAdd(r0 + (size_t)r * nx + x1, rgt);
+              }
+            };
+            W4<R> w[2], d[2], wh[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              w[u] = cic_w(Cic<R>{0, 0, 0, 0, 0, hx[u] + (mode == DEP_TRIAL ? ox[u] : nox[u]),
+                                  hy[u] + (mode == DEP_TRIAL ? oy[u] : noy[u])});
+              d[u] = (mode == DEP_TRIAL) ? cic_dw(hx[u], hy[u], ox[u], oy[u])
+                                         : cic_dw(hx[u], hy[u], nox[u], noy[u]);
+              wh[u] = cic_w(ch[u]);
+            }
+            const int fh = (mode == DEP_TRIAL) ? 3 : 1;
+            if (mode == DEP_TRIAL) {
+              put(0, w[0].w00 * vx[0] + w[1].w00 * vx[1], w[0].w01 * vx[0] + w[1].w01 * vx[1],
+                  w[0].w10 * vx[0] + w[1].w10 * vx[1], w[0].w11 * vx[0] + w[1].w11 * vx[1]);
+              put(1, w[0].w00 * vy[0] + w[1].w00 * vy[1], w[0].w01 * vy[0] + w[1].w01 * vy[1],
+                  w[0].w10 * vy[0] + w[1].w10 * vy[1], w[0].w11 * vy[0] + w[1].w11 * vy[1]);
+              put(2, w[0].w00 * vdev[0] + w[1].w00 * vdev[1] + (d[0].w00 + d[1].w00) * vref,
+                  w[0].w01 * vdev[0] + w[1].w01 * vdev[1] + (d[0].w01 + d[1].w01) * vref,
+                  w[0].w10 * vdev[0] + w[1].w10 * vdev[1] + (d[0].w10 + d[1].w10) * vref,
+                  w[0].w11 * vdev[0] + w[1].w11 * vdev[1] + (d[0].w11 + d[1].w11) * vref);
+            } else {
+              put(0, (d[0].w00 + d[1].w00) * vref, (d[0].w01 + d[1].w01) * vref,
+                  (d[0].w10 + d[1].w10) * vref, (d[0].w11 + d[1].w11) * vref);
+            }
+            put(fh, wh[0].w00 * jhx[0] + wh[1].w00 * jhx[1], wh[0].w01 * jhx[0] + wh[1].w01 * jhx[1],
+                wh[0].w10 * jhx[0] + wh[1].w10 * jhx[1], wh[0].w11 * jhx[0] + wh[1].w11 * jhx[1]);
+            put(fh + 1, wh[0].w00 * jhy[0] + wh[1].w00 * jhy[1],
+                wh[0].w01 * jhy[0] + wh[1].w01 * jhy[1], wh[0].w10 * jhy[0] + wh[1].w10 * jhy[1],
+                wh[0].w11 * jhy[0] + wh[1].w11 * jhy[1]);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              if (!ok[u]) continue;
+              const R jh[2] = {jhx[u], jhy[u]};
+              if (mode == DEP_TRIAL) {
+                const W4<R> w = cic_w(c[u]);
+                if (home[u]) {
+                  // home cell: J_x, J_y, and J_z minus its reference share the four corners
+                  const W4<R> d = cic_dw(hx[u], hy[u], ox[u], oy[u]);
+                  R* t0 = tile + (size_t)1 * nx;  // field 0, tile row 1 (home row)
+                  const size_t fs = (size_t)kTileRows * nx;
+                  atomicAdd(t0 + ix, w.w00 * vx[u]);
+                  atomicAdd(t0 + x1, w.w01 * vx[u]);
+                  atomicAdd(t0 + nx + ix, w.w10 * vx[u]);
+                  atomicAdd(t0 + nx + x1, w.w11 * vx[u]);
+                  atomicAdd(t0 + fs + ix, w.w00 * vy[u]);
+                  atomicAdd(t0 + fs + x1, w.w01 * vy[u]);
+                  atomicAdd(t0 + fs + nx + ix, w.w10 * vy[u]);
+                  atomicAdd(t0 + fs + nx + x1, w.w11 * vy[u]);
+                  atomicAdd(t0 + 2 * fs + ix, w.w00 * vdev[u] + d.w00 * vref);
+                  atomicAdd(t0 + 2 * fs + x1, w.w01 * vdev[u] + d.w01 * vref);
+                  atomicAdd(t0 + 2 * fs + nx + ix, w.w10 * vdev[u] + d.w10 * vref);
+                  atomicAdd(t0 + 2 * fs + nx + x1, w.w11 * vdev[u] + d.w11 * vref);
+                } else {
+                  const R v3[3] = {vx[u], vy[u], vdev[u] + vref};
+                  deposit_n(tile, a.ovf, c[u], w, 0, nx, ny, v3);
+                  const Cic<R> hc = cic<R>(ix, crow, hx[u], hy[u], nx, ny, crow);
+                  deposit(tile, a.ovf, hc, 2, nx, ny, -vref);
+                }
+                deposit_n(tile, a.ovf, ch[u], cic_w(ch[u]), 3, nx, ny, jh);
+              } else {
+                deposit_ref(tile, a.ovf, ix, crow, hx[u], hy[u], nox[u], noy[u], 0, nx, ny, R(0),
+                            vref);
+                deposit_n(tile, a.ovf, ch[u], cic_w(ch[u]), 1, nx, ny, jh);
+              }
+            }
+          }
         }
-      } else {  // commit
-        const R sf = dxi * ioph;
-        pox[i] = ox + sf * ux * idx;
-        poy[i] = oy + sf * uy * idy;
-        pux[i] = ux;
-        puy[i] = uy;
-        pps[i] = psi_p;
-        deposit_ref(tile, a.ovf, ix, crow, hx, hy, ox + sf * ux * idx, oy + sf * uy * idy, 0, nx,
-                    ny, R(0), -wn);
-        deposit(tile, a.ovf, ch, 1, nx, ny, jxh);
-        deposit(tile, a.ovf, ch, 2, nx, ny, jyh);
       }
     }
     __syncthreads();
@@ -326,21 +532,19 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
     __syncthreads();
   }
   if (mode == DEP_TRIAL && first) {
-    double s = block_sum((double)kap, red);
+    double s = block_sum_lo(kap, red);
     if (threadIdx.x == 0 && s != 0.0) atomicAdd(&a.diag[D_KAPPA * p.nk + j], s);
-    double m = block_min((double)omin, red);
-    if (threadIdx.x == 0 && m < 1e29) {
-      atomicMin((unsigned long long*)&a.diag[D_OPPMIN * p.nk + j], dkey(m));
-    }
-    double nfl = block_sum((double)nfloor, red);
-    if (threadIdx.x == 0 && nfl > 0) {
-      atomicAdd(&a.diag[D_NFLOOR * p.nk + j], nfl);
-      atomicOr(a.bar.status, ST_FLOOR);
+    double m = block_min_lo(omin, red);
+    double nfl = block_sum_lo(nfloor, red);
+    if (threadIdx.x == 0) {
+      *pslot(a.dpart, j, P_OPPMIN) = m;
+      *pslot(a.dpart, j, P_NFLOOR) = nfl;
+      if (nfl > 0) atomicOr(a.bar.status, ST_FLOOR);
     }
   }
   if (mode == DEP_TRIAL && last) {
-    double m = block_max((double)inv, red);
-    if (threadIdx.x == 0 && m > 0) atomic_max_nonneg(&a.diag[D_INV * p.nk + j], m);
+    double m = block_max_lo(inv, red);
+    if (threadIdx.x == 0) *pslot(a.dpart, j, P_INV) = m;
   }
 }
 
@@ -366,7 +570,7 @@ __device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, 
   R* __restrict__ ovf = a.ovf;
   const R* __restrict__ src = a.src;
   __shared__ double red[32];
-  double charge = 0.0;
+  R charge = R(0);
   load_tw(tw, a.twx, nx);
   const int k0 = (mode == DEP_TRIAL) ? jj : jj - 1;  // beam-source nodes k0, k0 + 1
   for (int q = blockIdx.x; q < ny; q += gridDim.x) {
@@ -408,7 +612,7 @@ __device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, 
         v[3] += R(0.5) * (s0[2] + s1[2]);
         v[4] += R(0.5) * (s0[3] + s1[3]);
       } else {
-        charge += (double)v[0];
+        charge += v[0];
         v[0] += s1[0];
         v[1] += R(0.5) * (s0[2] + s1[2]);
         v[2] += R(0.5) * (s0[3] + s1[3]);
@@ -432,9 +636,8 @@ __device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, 
     __syncthreads();
   }
   if (mode != DEP_TRIAL) {
-    double s = block_sum(charge, red);
-    if (threadIdx.x == 0 && s != 0.0)
-      atomicAdd(&a.diag[D_CHARGE * p.nk + jj], s * p.dx * p.dy);
+    double s = block_sum_lo(charge, red);
+    if (threadIdx.x == 0) *pslot(a.dpart, jj, P_CHARGE) = s * p.dx * p.dy;
   }
 }
 
@@ -532,10 +735,10 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
     __syncthreads();
   }
   if (last) {
-    double s = block_sum((double)num, red);
-    if (threadIdx.x == 0 && s != 0.0) atomicAdd(&a.diag[D_PCNUM * p.nk + j], s);
-    s = block_sum((double)den, red);
-    if (threadIdx.x == 0 && s != 0.0) atomicAdd(&a.diag[D_PCDEN * p.nk + j], s);
+    double s = block_sum_lo(num, red);
+    if (threadIdx.x == 0) *pslot(a.dpart, j, P_PCNUM) = s;
+    s = block_sum_lo(den, red);
+    if (threadIdx.x == 0) *pslot(a.dpart, j, P_PCDEN) = s;
   }
 }
 
@@ -595,7 +798,7 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
   const R scale = R(1.0 / ((double)nx * ny));
   const C<R>* __restrict__ cspec = a.cspec;
   R* __restrict__ fg = a.fg;
-  __shared__ double red[32];
+  __shared__ double red[64];
   R en[6] = {0, 0, 0, 0, 0, 0};
   bool bad = false;
   load_tw(tw, a.twx, nx);
@@ -641,15 +844,7 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
       if (!psi_mode && last) {
         const R wx = -node[FG_GX], wy = -node[FG_GY];
         const R ez = R(ez0j + (double)v[3]);
-        R* s = a.slab + (((size_t)j * ny + q) * nx + x) * 8;
-        s[0] = wx;
-        s[1] = wy;
-        s[2] = ez;
-        s[3] = v[0];
-        s[4] = v[1];
-        s[5] = v[2];
-        s[6] = R(0);
-        s[7] = R(0);
+        st8(a.slab + (((size_t)j * ny + q) * nx + x) * 8, wx, wy, ez, v[0], v[1], v[2]);
         const R Ex = wx + v[1], Ey = wy - v[0];
         en[0] += Ex * Ex;
         en[1] += Ey * Ey;
@@ -665,10 +860,10 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
   if (!psi_mode && last) {
     const double cell = 0.5 * p.dx * p.dy * p.dxi;
     double tot[6];
-    block_sum_n<6>(en, tot, red);
+    block_sum_lo_n<6>(en, tot, red);
     if (threadIdx.x == 0)
       for (int f = 0; f < 6; ++f)
-        if (tot[f] != 0.0) atomicAdd(&a.diag[(D_E0 + f) * p.nk + j], tot[f] * cell);
+        *pslot(a.dpart, j, P_E0 + f) = tot[f] * cell;
     if (bad) atomicOr(a.bar.status, ST_NONFINITE);
   }
 }
