@@ -166,6 +166,39 @@ int qsa_field_solve(qsa_handle* h, const double* S, const double* Jx, const doub
                     const double* Jz, const double* Dx, const double* Dy, double kappa2,
                     double* out);
 
+/* ---------------------------------------------------------------------------------------
+ * Transverse field solve that allocates nothing.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc (or any allocating routine) when they
+ * need a solve, for instance a code whose own memory manager has already reserved the GPU's
+ * memory in a fixed pool, or a process running under a hard device-memory budget, where a new
+ * allocation would fail or fragment that pool.  Such callers still own their inputs and
+ * outputs; only the solve's scratch memory comes from the library.
+ *
+ * It computes exactly what qsa_field_solve computes (same device kernels), for one grid:
+ *   psi = S/k^2, d_x psi, d_y psi;  E_z = -(i k.J)/k^2;  B_z = (i k_x J_y - i k_y J_x)/k^2;
+ *   (k^2 + kappa2) B_x = i k_y J_z + D_y,  (k^2 + kappa2) B_y = -i k_x J_z - D_x  (k = 0 dropped).
+ * Arguments: nx, ny in {1, 2^a 3^b} and <= QSA_STATIC_MAX_N; periodic box Lx, Ly > 0;
+ * kappa2 >= 0; precision QSA_FP64 (arrays of double) or QSA_MIXED (arrays of float); S, Jx,
+ * Jy, Jz, Dx, Dy: DEVICE pointers to [ny][nx] arrays; out: DEVICE pointer to [7][ny][nx]
+ * (psi, d_x psi, d_y psi, E_z, B_z, B_x, B_y); stream: cudaStream_t or NULL.  The call
+ * enqueues its work on the stream and returns after synchronising it.
+ * Memory: the scratch lives in one file-scope device array of QSA_STATIC_SCRATCH_BYTES that
+ * every GPU loading this library holds until the process exits.  The first call on a device
+ * takes that array's device address (cudaGetSymbolAddress, with that device current); make
+ * that first call before any stream capture.  The call itself calls no cudaMalloc, cudaFree or
+ * other allocating routine.  Every call shares the one array and leaves its contents behind
+ * (the call clears what must start at zero), so calls that overlap on the GPU - from two
+ * streams or two host threads - race and must be serialised by the caller.
+ * Errors: QSA_ERR_ARG for a size above QSA_STATIC_MAX_N, an invalid size or argument, or a
+ * grid whose scratch would not fit (qsa_last_error(NULL) says which); QSA_ERR_CUDA if a CUDA
+ * call fails; QSA_ERR_TIMEOUT if a device-side wait gave up. */
+#define QSA_STATIC_MAX_N 128
+#define QSA_STATIC_SCRATCH_BYTES (6u * 1024u * 1024u + 512u * 1024u)
+int qsa_field_solve_static(int32_t nx, int32_t ny, double Lx, double Ly, double kappa2,
+                           int32_t precision, const void* S, const void* Jx, const void* Jy,
+                           const void* Jz, const void* Dx, const void* Dy, void* out,
+                           void* stream);
+
 /* Phase timing of the last sweep (tracing): out[(j * 32 + ph) * 2 + 0] is the device
  * globaltimer (ns) when the last block arrived at the barrier closing phase ph of slice j,
  * out[... + 1] when block 0 left it, for slices j < 8 and phases ph < 32 (trial iteration it,

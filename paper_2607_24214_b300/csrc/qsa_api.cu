@@ -78,6 +78,15 @@ struct qsa_handle {
 
 namespace {
 
+}  // namespace
+
+namespace qsa {
+// Message for qsa_last_error(NULL) from entry points that have no handle.
+void set_global_error(const std::string& msg) { g_init_error = msg; }
+}  // namespace qsa
+
+namespace {
+
 int fail(qsa_handle* h, int code, const std::string& msg) {
   if (h) h->err = msg;
   else g_init_error = msg;

@@ -31,7 +31,7 @@ SOURCES = ("Sb", "Jz", "Jx", "Jy")
 EXPORTS = ("qsa_init", "qsa_set_beam", "qsa_get_beam", "qsa_plasma_sweep", "qsa_beam_step",
            "qsa_diagnostics", "qsa_copy_field", "qsa_copy_source", "qsa_field_solve",
            "qsa_phase_times", "qsa_launch_count", "qsa_device_bytes", "qsa_last_error",
-           "qsa_destroy")
+           "qsa_destroy", "qsa_field_solve_static")
 
 
 class QsaError(RuntimeError):
@@ -106,6 +106,9 @@ def load_library(path: str = LIB_PATH):
     lib.qsa_copy_source.restype = ct.c_int
     lib.qsa_field_solve.argtypes = [P] + [_DP] * 6 + [ct.c_double, _DP]
     lib.qsa_field_solve.restype = ct.c_int
+    lib.qsa_field_solve_static.argtypes = ([ct.c_int32, ct.c_int32, ct.c_double, ct.c_double,
+                                            ct.c_double, ct.c_int32] + [P] * 8)
+    lib.qsa_field_solve_static.restype = ct.c_int
     lib.qsa_phase_times.argtypes = [P, ct.POINTER(ct.c_int64), ct.c_int]
     lib.qsa_phase_times.restype = ct.c_int
     lib.qsa_launch_count.argtypes = [P]
