@@ -128,6 +128,7 @@ struct State {
   SweepArgs<R> sa{};
   std::vector<BeamArrays<BR>> beams;
   std::vector<SpeciesDev> species;
+  std::vector<BeamConst<R>> bconst;
   ModesDev modes{};
   R* src = nullptr;
   R* slab = nullptr;
@@ -167,6 +168,7 @@ int setup(qsa_handle* h) {
   const size_t spec = (size_t)dp.nxh * dp.ny;
   SweepArgs<R>& a = s->sa;
   a.p = dp;
+  a.k = sweep_consts<R>(dp);
   auto A = [&](size_t bytes) { return dalloc(h, bytes); };
   const size_t np = (size_t)dp.np;
   R** pl[5] = {&a.pox, &a.poy, &a.pux, &a.puy, &a.ppsi};
@@ -289,9 +291,10 @@ int setup(qsa_handle* h) {
     if (!(b.ox = (R*)A(n * sizeof(R))) || !(b.oy = (R*)A(n * sizeof(R))) ||
         !(b.oxi = (R*)A(n * sizeof(R))) || !(b.ux = (R*)A(n * sizeof(R))) ||
         !(b.uy = (R*)A(n * sizeof(R))) || !(b.dw = (R*)A(n * sizeof(R))) ||
-        !(b.uz = (double*)A(n * sizeof(double))))
+        !(b.uz = (typename UzT<R>::T*)A(n * sizeof(typename UzT<R>::T))))
       return fail(h, QSA_ERR_OOM, "beam arrays");
     s->species.push_back(sp);
+    s->bconst.push_back(beam_consts<R>(dp, sp));
     s->beams.push_back(b);
     if (b.n > 0) {
       const unsigned blocks = (unsigned)((b.n + kThreads - 1) / kThreads);
@@ -332,7 +335,7 @@ int deposit_sources(qsa_handle* h) {
     if (b.n == 0) continue;
     const unsigned groups = (unsigned)(s->species[si].nkb * dp.ny);
     beam_kernel<R, false><<<groups, kThreads, beam_smem_bytes<R>(dp.nx), h->stream>>>(
-        b, dp, s->species[si], s->slab, s->src, nullptr);
+        b, dp, s->species[si], s->bconst[si], s->slab, s->src, nullptr);
     ++h->launches;
     CK(cudaGetLastError());
   }
@@ -418,7 +421,7 @@ int beam_step(qsa_handle* h) {
     if (b.n == 0) continue;
     const unsigned groups = (unsigned)(s->species[si].nkb * dp.ny);
     beam_kernel<R, true><<<groups, kThreads, beam_smem_bytes<R>(dp.nx), h->stream>>>(
-        b, dp, s->species[si], s->slab, s->src, s->lost);
+        b, dp, s->species[si], s->bconst[si], s->slab, s->src, s->lost);
     ++h->launches;
     CK(cudaGetLastError());
   }
@@ -544,6 +547,7 @@ int field_solve(qsa_handle* h, const double* const* in, double kappa2, double* o
   const size_t g = (size_t)dp.nx * dp.ny;
   SweepArgs<R> a = s->sa;
   a.src = nullptr;
+  a.bref = nullptr;
   std::vector<R> ov(g * kNF);
   std::vector<double> dg((size_t)D_COUNT * dp.nk, 0.0);
   dg[(size_t)D_KAPPA * dp.nk] = kappa2 * dp.ppc * (double)dp.nx * dp.ny;

@@ -5,7 +5,10 @@
 // Storage per species, index s = ((k_xi * ny + iy) * ppc + sub) * nx + ix (a warp holds 32
 // neighbouring cells of one sub-lattice position).  Positions are offsets, in cells, from
 // the particle's lattice home; this keeps the slow transverse and longitudinal drifts of an
-// ultrarelativistic beam (1e-6 cells per step) exact in FP32.  u_z is FP64 in both paths.
+// ultrarelativistic beam (1e-6 cells per step) exact in FP32.  u_z is FP64 in the FP64 path
+// and a double-float pair (leading float + trailing float, about 48 significant bits) in the
+// mixed path: the per-step increments of u_z are 1e-6 of it, too small for one float, and the
+// pair keeps them with FP32 instructions only.
 // The weight is stored as its relative deviation dw = w / wbar - 1 from the species' nominal
 // weight wbar = alpha dx dy dxi / ppc (dw = -1 marks a lost particle), and the beam sources
 // are deposited as deviations from the reference beam (nominal weight, at home, u = (0, 0,
@@ -16,10 +19,30 @@
 
 namespace qsa {
 
+// Storage type of u_z: FP64, or a (leading, trailing) float pair in the mixed path.
+template <typename BR>
+struct UzT {
+  using T = double;
+};
+template <>
+struct UzT<float> {
+  using T = float2;
+};
+__host__ __device__ __forceinline__ double uz_value(double v) { return v; }
+__host__ __device__ __forceinline__ double uz_value(float2 v) { return (double)v.x + (double)v.y; }
+__host__ __device__ __forceinline__ void uz_store(double& d, double v) { d = v; }
+__host__ __device__ __forceinline__ void uz_store(float2& d, double v) {
+  const float hi = (float)v;
+  d = make_float2(hi, (float)(v - (double)hi));
+}
+// Leading part (the value for the derived quantities gamma, 1 - v_z).
+__device__ __forceinline__ double uz_lead(double v) { return v; }
+__device__ __forceinline__ float uz_lead(float2 v) { return v.x; }
+
 template <typename BR>
 struct BeamArrays {
   BR *ox, *oy, *oxi, *ux, *uy, *dw;
-  double* uz;
+  typename UzT<BR>::T* uz;
   long long n;
 };
 
@@ -32,6 +55,29 @@ struct SpeciesDev {
   int k0, nkb;  // first xi cell and number of xi cells
   int seeded, index;
 };
+
+// Per-species constants of the push and deposit in the working precision, formed on the host
+// in FP64 (no FP64 division in device code).
+template <typename BR>
+struct BeamConst {
+  BR hdt;            // 0.5 Z dt / M
+  BR cdx, cdy, cdk;  // dt/dx, dt/dy, dt/dxi
+  BR refS, refJz;    // reference source weights qbar omvbar, qbar (1 - omvbar)
+  BR qb, omvbar;     // qbar, 1 - v_z of the reference momentum
+};
+template <typename BR>
+inline BeamConst<BR> beam_consts(const DevParams& p, const SpeciesDev& sp) {
+  BeamConst<BR> c;
+  c.hdt = BR(0.5 * sp.Z * p.dt / sp.M);
+  c.cdx = BR(p.dt / p.dx);
+  c.cdy = BR(p.dt / p.dy);
+  c.cdk = BR(p.dt / p.dxi);
+  c.refS = BR(sp.qbar * sp.omvbar);
+  c.refJz = BR(sp.qbar * (1.0 - sp.omvbar));
+  c.qb = BR(sp.qbar);
+  c.omvbar = BR(sp.omvbar);
+  return c;
+}
 
 struct ModesDev {
   int n;
@@ -93,15 +139,16 @@ __global__ void beam_init_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp, M
   b.oxi[s] = BR(0);
   b.ux[s] = BR(ux);
   b.uy[s] = BR(uy);
-  b.uz[s] = sqrt(gam * gam - 1.0 - ux * ux - uy * uy);
+  uz_store(b.uz[s], sqrt(gam * gam - 1.0 - ux * ux - uy * uy));
   b.dw[s] = BR(dw);
 }
 
 // ------------------------------------------------------------------ deposit and push
 // A block handles one group of a species: the ppc * nx particles whose home is xi cell k and
 // row iy.  Their deposits land in a shared-memory tile of the nodes (k, k+1) x rows
-// (iy-1 .. iy+2) x every x, which is flushed to the source slab with one vector atomic per
-// touched node; a deposit outside the tile goes straight to global memory.
+// (iy-1 .. iy+2) x every x, field-major ([node][row][quantity][x]: the lanes of a warp, on
+// consecutive columns, hit consecutive banks), which is flushed to the source slab with one
+// vector atomic per touched node; a deposit outside the tile goes straight to global memory.
 
 __device__ __forceinline__ void red4(float* a, float s, float z, float x, float y) {
   atomicAdd(reinterpret_cast<float4*>(a), make_float4(s, z, x, y));
@@ -116,7 +163,7 @@ __device__ __forceinline__ void red4(double* a, double s, double z, double x, do
 template <typename BR>
 struct Group {
   int kabs, iy;  // home xi node and row of the group
-  BR* tile;      // [2][4][nx][4]: S_b, J_z, J_x, J_y deviations
+  BR* tile;      // [2][4][4][nx]: S_b, J_z, J_x, J_y deviations
 };
 
 // Add weight * (s, z, jx, jy) at node k, unwrapped row gy, wrapped column x.
@@ -125,11 +172,12 @@ __device__ __forceinline__ void put(const Group<BR>& g, BR* src, const DevParams
                                     int x, BR wt, BR s, BR z, BR jx, BR jy) {
   const int dk = k - g.kabs, r = gy - (g.iy - 1);
   if (dk >= 0 && dk < 2 && r >= 0 && r < 4) {
-    BR* t = g.tile + ((size_t)(dk * 4 + r) * p.nx + x) * 4;
+    const int nx = p.nx;
+    BR* t = g.tile + (size_t)(dk * 4 + r) * 4 * nx + x;
     atomicAdd(t, wt * s);
-    atomicAdd(t + 1, wt * z);
-    atomicAdd(t + 2, wt * jx);
-    atomicAdd(t + 3, wt * jy);
+    atomicAdd(t + nx, wt * z);
+    atomicAdd(t + 2 * nx, wt * jx);
+    atomicAdd(t + 3 * nx, wt * jy);
   } else if (k >= 0 && k < p.nk) {
     red4(src + (((size_t)k * p.ny + wrap(gy, p.ny)) * p.nx + x) * 4, wt * s, wt * z, wt * jx,
          wt * jy);
@@ -156,18 +204,18 @@ __device__ __forceinline__ void deposit_particle(const Group<BR>& g, BR* src, co
 #pragma unroll
       for (int cy = 0; cy < 2; ++cy) {
         const BR a2 = cy ? hy : BR(1) - hy, d2 = cy ? oy : -oy;
-        BR* row = g.tile + (size_t)(ck * 4 + 1 + cy) * nx * 4;
+        BR* row = g.tile + (size_t)(ck * 4 + 1 + cy) * 4 * nx;
 #pragma unroll
         for (int cx = 0; cx < 2; ++cx) {
           const BR a1 = cx ? hx : BR(1) - hx, d1 = cx ? ox : -ox;
           const BR w = (a1 + d1) * (a2 + d2) * (a3 + d3);
           const BR dW = d1 * a2 * a3 + a1 * d2 * a3 + a1 * a2 * d3 + d1 * d2 * a3 +
                         d1 * a2 * d3 + a1 * d2 * d3 + d1 * d2 * d3;
-          BR* t = row + (size_t)(cx ? x1 : ix) * 4;
+          BR* t = row + (cx ? x1 : ix);
           atomicAdd(t, dS * w + refS * dW);
-          atomicAdd(t + 1, dJz * w + refJz * dW);
-          atomicAdd(t + 2, jx * w);
-          atomicAdd(t + 3, jy * w);
+          atomicAdd(t + nx, dJz * w + refJz * dW);
+          atomicAdd(t + 2 * nx, jx * w);
+          atomicAdd(t + 3 * nx, jy * w);
         }
       }
     }
@@ -201,32 +249,46 @@ __device__ __forceinline__ void deposit_particle(const Group<BR>& g, BR* src, co
 // Source deviations of one particle with q = qbar (1 + dw): dS = q(1 - v_z) - qbar omvbar,
 // dJz = q v_z - qbar (1 - omvbar); J_perp = q u_perp/gamma (reference zero).
 __device__ __forceinline__ void beam_sources(double ux, double uy, double uz, double dw,
-                                             const SpeciesDev& sp, double& dS, double& dJz,
-                                             double& jx, double& jy) {
+                                             const BeamConst<double>& c, double& dS,
+                                             double& dJz, double& jx, double& jy) {
   const double up2 = ux * ux + uy * uy;
   const double g = sqrt(1.0 + up2 + uz * uz);
   const double omv = (1.0 + up2) / (g * (g + uz));
-  const double q = sp.qbar * (1.0 + dw);
-  dS = sp.qbar * (dw * omv + (omv - sp.omvbar));
-  dJz = sp.qbar * (dw * (1.0 - omv) - (omv - sp.omvbar));
+  const double q = c.qb * (1.0 + dw);
+  dS = c.qb * (dw * omv + (omv - c.omvbar));
+  dJz = c.qb * (dw * (1.0 - omv) - (omv - c.omvbar));
   jx = q * ux / g;
   jy = q * uy / g;
 }
-__device__ __forceinline__ void beam_sources(float ux, float uy, double uz, float dw,
-                                             const SpeciesDev& sp, float& dS, float& dJz,
+__device__ __forceinline__ void beam_sources(float ux, float uy, float uzf, float dw,
+                                             const BeamConst<float>& c, float& dS, float& dJz,
                                              float& jx, float& jy) {
   const float up2 = ux * ux + uy * uy;
-  const float uzf = (float)uz;
   const float d = (1.0f + up2) / (sqrtf(1.0f + up2 + uzf * uzf) + uzf);  // gamma - u_z
   const float g = uzf + d;
   const float omv = d / g;                                               // 1 - v_z
-  const float qb = (float)sp.qbar;
-  const float domv = omv - (float)sp.omvbar;
-  dS = qb * (dw * omv + domv);
-  dJz = qb * (dw * (1.0f - omv) - domv);
-  const float q = qb * (1.0f + dw);
+  const float domv = omv - c.omvbar;
+  dS = c.qb * (dw * omv + domv);
+  dJz = c.qb * (dw * (1.0f - omv) - domv);
+  const float q = c.qb * (1.0f + dw);
   jx = q * ux / g;
   jy = q * uy / g;
+}
+
+// 1/gamma and 1 - v_z = (1 + u_perp^2)/(gamma (gamma + u_z)) of the pushed momentum.
+__device__ __forceinline__ void drift_rates(double ux, double uy, double uz, double& ig,
+                                            double& omv) {
+  const double up2 = ux * ux + uy * uy;
+  const double gg = sqrt(1.0 + up2 + uz * uz);
+  ig = 1.0 / gg;
+  omv = (1.0 + up2) / (gg * (gg + uz));
+}
+__device__ __forceinline__ void drift_rates(float ux, float uy, float uzf, float& ig,
+                                            float& omv) {
+  const float up2 = ux * ux + uy * uy;
+  const float d = (1.0f + up2) / (sqrtf(1.0f + up2 + uzf * uzf) + uzf);  // gamma - u_z
+  ig = 1.0f / (uzf + d);
+  omv = d * ig;
 }
 
 // Trilinear gather of the six slab fields (CIC in x, y, linear in xi) at unwrapped node
@@ -287,15 +349,15 @@ __device__ __forceinline__ void boris(double& ux, double& uy, double& uz, const 
   uz = mz + (px * sy - py * sx) + h * Ez;
 }
 
-// The same Boris step with FP32 transverse arithmetic and FP64 u_z accumulation, written so
-// that no step subtracts nearly equal terms: with W = E_perp - z x B (the slab's first two
-// fields), E_x - v_z B_y = W_x + (1 - v_z) B_y, and 1 - v_z is formed from gamma - u_z =
+// The same Boris step with FP32 arithmetic and double-float u_z accumulation, written so that
+// no step subtracts nearly equal terms: with W = E_perp - z x B (the slab's first two fields),
+// E_x - v_z B_y = W_x + (1 - v_z) B_y, and 1 - v_z is formed from gamma - u_z =
 // (1 + u_perp^2)/(gamma + u_z).
-__device__ __forceinline__ void boris(float& ux, float& uy, double& uz, const float F[6],
+__device__ __forceinline__ void boris(float& ux, float& uy, float2& uz, const float F[6],
                                       float h) {
   const float Wx = F[0], Wy = F[1], Ez = F[2], Bx = F[3], By = F[4], Bz = F[5];
   const float mx = ux + h * (Wx + By), my = uy + h * (Wy - Bx);
-  const float mzf = (float)uz + h * Ez;
+  const float mzf = uz.x + h * Ez;
   const float mp2 = mx * mx + my * my;
   const float gm = sqrtf(1.0f + mp2 + mzf * mzf);
   const float dm = (1.0f + mp2) / (gm + mzf);  // gamma^- - m_z
@@ -311,7 +373,15 @@ __device__ __forceinline__ void boris(float& ux, float& uy, double& uz, const fl
   const float eps = (dm + gm * t2 - (mx * ty - my * tx)) * ig / (1.0f + t2);
   ux = ux + 2.0f * h * Wx + 2.0f * h * By * eps + pyp * sz;
   uy = uy + 2.0f * h * Wy - 2.0f * h * Bx * eps - pxp * sz;
-  uz = uz + (double)(2.0f * h * Ez + pxp * sy - pyp * sx);
+  // u_z += du in double-float: Knuth's two-sum of the leading part and du, its rounding error
+  // carried into the trailing part, then renormalised (|trailing| <= ulp(leading) / 2)
+  const float du = 2.0f * h * Ez + pxp * sy - pyp * sx;
+  const float sum = uz.x + du;
+  const float bv = sum - uz.x;
+  const float err = (uz.x - (sum - bv)) + (du - bv);
+  const float lo = uz.y + err;
+  const float hi = sum + lo;
+  uz = make_float2(hi, lo - (hi - sum));
 }
 
 // PUSH = false: deposit the current beam (sources of the first sweep).  PUSH = true: push
@@ -319,8 +389,9 @@ __device__ __forceinline__ void boris(float& ux, float& uy, double& uz, const fl
 // sources of the next sweep.  Grid: one block per (xi cell, row) group of the species.
 template <typename BR, bool PUSH>
 __global__ void __launch_bounds__(256, 2) beam_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp,
-                                                   const BR* __restrict__ slab, BR* src,
-                                                   unsigned long long* lost) {
+                                                   BeamConst<BR> bc, const BR* __restrict__ slab,
+                                                   BR* src, unsigned long long* lost) {
+  using UZ = typename UzT<BR>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   Group<BR> g;
   g.tile = reinterpret_cast<BR*>(smem);
@@ -332,9 +403,9 @@ __global__ void __launch_bounds__(256, 2) beam_kernel(BeamArrays<BR> b, DevParam
   for (int e = threadIdx.x; e < tn; e += blockDim.x) g.tile[e] = BR(0);
   __syncthreads();
   const size_t base = (size_t)grp * sp.ppc * nx;
-  const BR refS = BR(sp.qbar * sp.omvbar), refJz = BR(sp.qbar * (1.0 - sp.omvbar));
-  const BR hdt = BR(0.5 * sp.Z * p.dt / sp.M);
-  const BR cdx = BR(p.dt / p.dx), cdy = BR(p.dt / p.dy), cdk = BR(p.dt / p.dxi);
+  const BR refS = bc.refS, refJz = bc.refJz;
+  const BR hdt = bc.hdt;
+  const BR cdx = bc.cdx, cdy = bc.cdy, cdk = bc.cdk;
   const int kleft = p.nxi - g.kabs;  // lost when the local xi position reaches this
   int my_lost = 0;
   // two sub-lattice positions per thread per pass: particles (sub0, ix) and (sub0 + 1, ix);
@@ -354,7 +425,7 @@ __global__ void __launch_bounds__(256, 2) beam_kernel(BeamArrays<BR> b, DevParam
     for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
       size_t si[2];
       BR dw[2], ox[2], oy[2], oxi[2], ux[2], uy[2];
-      double uz[2];
+      UZ uz[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         si[u] = base + (size_t)(ok[u] ? sub0 + u : sub0) * nx + ix;
@@ -388,19 +459,7 @@ __global__ void __launch_bounds__(256, 2) beam_kernel(BeamArrays<BR> b, DevParam
           boris(ux[u], uy[u], uz[u], F[u], hdt);
           // dx/dt = u/gamma, dxi/dt = 1 - v_z = (1 + u_perp^2)/(gamma (gamma + u_z))
           BR ig, omv;
-          {
-            const BR up2 = ux[u] * ux[u] + uy[u] * uy[u];
-            if (sizeof(BR) == 8) {
-              const double gg = sqrt(1.0 + (double)up2 + uz[u] * uz[u]);
-              ig = BR(1.0 / gg);
-              omv = BR((1.0 + (double)up2) / (gg * (gg + uz[u])));
-            } else {
-              const float uzf = (float)uz[u];
-              const float d = (1.0f + (float)up2) / (sqrtf(1.0f + (float)up2 + uzf * uzf) + uzf);
-              ig = BR(1.0f / (uzf + d));
-              omv = BR(d) * ig;
-            }
-          }
+          drift_rates(ux[u], uy[u], uz_lead(uz[u]), ig, omv);
           ox[u] += cdx * ux[u] * ig;
           oy[u] += cdy * uy[u] * ig;
           oxi[u] += cdk * omv;
@@ -420,7 +479,7 @@ __global__ void __launch_bounds__(256, 2) beam_kernel(BeamArrays<BR> b, DevParam
           }
         }
         BR dS, dJz, JX, JY;
-        beam_sources(ux[u], uy[u], uz[u], dw[u], sp, dS, dJz, JX, JY);
+        beam_sources(ux[u], uy[u], uz_lead(uz[u]), dw[u], bc, dS, dJz, JX, JY);
         deposit_particle(g, src, p, ix, hx[u], hy[u], hk[u], ox[u], oy[u], oxi[u], dS, dJz, JX,
                          JY, refS, refJz);
       }
@@ -430,10 +489,10 @@ __global__ void __launch_bounds__(256, 2) beam_kernel(BeamArrays<BR> b, DevParam
   for (int e = threadIdx.x; e < 2 * 4 * nx; e += blockDim.x) {
     const int dk = e / (4 * nx), r = (e / nx) % 4, x = e % nx;
     const int k = g.kabs + dk;
-    const BR* t = g.tile + (size_t)e * 4;
-    if (k < p.nk && (t[0] != BR(0) || t[1] != BR(0) || t[2] != BR(0) || t[3] != BR(0)))
-      red4(src + (((size_t)k * p.ny + wrap(g.iy - 1 + r, p.ny)) * nx + x) * 4, t[0], t[1], t[2],
-           t[3]);
+    const BR* t = g.tile + (size_t)(e / nx) * 4 * nx + x;
+    const BR t0 = t[0], t1 = t[nx], t2 = t[2 * nx], t3 = t[3 * nx];
+    if (k < p.nk && (t0 != BR(0) || t1 != BR(0) || t2 != BR(0) || t3 != BR(0)))
+      red4(src + (((size_t)k * p.ny + wrap(g.iy - 1 + r, p.ny)) * nx + x) * 4, t0, t1, t2, t3);
   }
   if (my_lost && lost) atomicAdd(lost, (unsigned long long)my_lost);
 }
@@ -465,7 +524,7 @@ __global__ void beam_from_host_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev 
   b.oxi[s] = BR(xi[id] / p.dxi - hk);
   b.ux[s] = BR(ux[id]);
   b.uy[s] = BR(uy[id]);
-  b.uz[s] = uz[id];
+  uz_store(b.uz[s], uz[id]);
   b.dw[s] = (w[id] == 0.0) ? BR(-1) : BR(w[id] / sp.wbar - 1.0);
 }
 
@@ -487,7 +546,7 @@ __global__ void beam_to_host_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp
   xi[id] = (hk + (double)b.oxi[s]) * p.dxi;
   ux[id] = (double)b.ux[s];
   uy[id] = (double)b.uy[s];
-  uz[id] = b.uz[s];
+  uz[id] = uz_value(b.uz[s]);
   w[id] = (b.dw[s] == BR(-1)) ? 0.0 : sp.wbar * (1.0 + (double)b.dw[s]);
 }
 

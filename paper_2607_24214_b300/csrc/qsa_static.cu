@@ -150,6 +150,7 @@ int solve_static(int nx, int ny, double Lx, double Ly, double kappa2, const R* S
   Carve cv{reinterpret_cast<unsigned char*>(base)};
   SweepArgs<R> a{};
   a.p = dp;
+  a.k = sweep_consts<R>(dp);
   a.fg = cv.take<R>(g * kFG);
   a.part = cv.take<R>((size_t)ny * kTileRows * nx * kNF);
   a.ovf = cv.take<R>(g * kNF);

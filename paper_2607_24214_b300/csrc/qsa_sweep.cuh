@@ -76,9 +76,36 @@ __device__ __forceinline__ unsigned long long dkey(double v) {
   return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
 }
 
+// Grid constants in the working precision, formed on the host in FP64 once: device code
+// needs no FP64 division per phase (every thread of every block would repeat it, and FP64
+// issue is scarce on this part).
+template <typename R>
+struct SweepConst {
+  R dxi, rdxi;     // slice step and its inverse
+  R idx, idy;      // inverse cell sizes
+  R wn;            // w / (dx dy) of a plasma macroparticle = 1 / ppc
+  R floor_;        // psi_floor
+  R inv_npc;       // 1 / (ppc nx ny): kappa^2 from the sum of 1/(1+psi)
+  R scale;         // 1 / (nx ny): inverse FFT normalisation
+};
+template <typename R>
+inline SweepConst<R> sweep_consts(const DevParams& p) {
+  SweepConst<R> k;
+  k.dxi = R(p.dxi);
+  k.rdxi = R(1.0 / p.dxi);
+  k.idx = R(1.0 / p.dx);
+  k.idy = R(1.0 / p.dy);
+  k.wn = R(1.0 / p.ppc);
+  k.floor_ = R(p.psi_floor);
+  k.inv_npc = R(1.0 / ((double)p.ppc * p.nx * p.ny));
+  k.scale = R(1.0 / ((double)p.nx * p.ny));
+  return k;
+}
+
 template <typename R>
 struct SweepArgs {
   DevParams p;
+  SweepConst<R> k;
   R *pox, *poy, *pux, *puy, *ppsi;          // plasma state (offsets in cells)
   R* fg;                                    // [ny][nx][8] real-space fields
   R* part;                                  // [ny chunks][nf][4][nx]
@@ -298,21 +325,21 @@ template <typename R>
 __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, double psi0,
                           bool first, bool last) {
   // reference state of the deposits: a particle at rest at its lattice home with psi = psi0
-  // carries rho - J_z = -w and u_z/(1+psi) = c0 = -psi0 (2 + psi0) / (2 (1+psi0)^2)
+  // carries rho - J_z = -w and u_z/(1+psi) = c0 = -psi0 (2 + psi0) / (2 (1+psi0)^2); formed
+  // in the working precision (psi0 is O(alpha), no cancellation)
   const DevParams& p = a.p;
-  const double opp0d = 1.0 + psi0;
-  const R opp0 = R(opp0d);
-  const R c0 = R(-psi0 * (2.0 + psi0) / (2.0 * opp0d * opp0d));
-  const R iopp02 = R(1.0 / (opp0d * opp0d));
-  const R dfloor = R(p.psi_floor - opp0d);  // psi fluctuation of a floored particle
+  const R psi0r = R(psi0);
+  const R opp0 = R(1) + psi0r;
+  const R iopp02 = R(1) / (opp0 * opp0);
+  const R c0 = R(-0.5) * psi0r * (R(2) + psi0r) * iopp02;
+  const R floor_ = a.k.floor_;
+  const R dfloor = floor_ - opp0;  // psi fluctuation of a floored particle
   const int nx = p.nx, ny = p.ny;
   const int nf = (mode == DEP_TRIAL) ? kNF : 3;
   const int per_chunk = p.ppc * nx;
-  const R wn = R(1) / R(p.ppc);  // w/(dx dy) of a plasma macroparticle
-  const R dxi = R(p.dxi);
-  const R idx = R(1) / R(p.dx), idy = R(1) / R(p.dy);
-  const R floor_ = R(p.psi_floor);
-  const R psi0r = R(psi0);
+  const R wn = a.k.wn;
+  const R dxi = a.k.dxi;
+  const R idx = a.k.idx, idy = a.k.idy;
   const int tile_elems = kTileRows * nx * nf;
   // the aggregated deposit needs whole warps over consecutive columns
   const bool lane_agg = (nx % 32 == 0) && (blockDim.x % 32 == 0);
@@ -660,18 +687,18 @@ __device__ __forceinline__ Kv<R> kvec(const R* __restrict__ ktab, int nxh, int n
 }
 
 // ------------------------------------------------------------------ column phase: B, E_z
-// jz_ref: the uniform parts of J_z left out of the grid deposits (plasma reference state and
-// beam reference density), added to <J_z> for the k = 0 mode.
+// psi0: the k = 0 potential of the slice, which fixes the plasma reference state of the
+// deposits (needed for <J_z>, the source of the k = 0 mode).
 template <typename R>
 __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, bool last,
-                            double jz_ref) {
+                            double psi0) {
   const DevParams& p = a.p;
   const int ny = p.ny, nxh = p.nxh;
   C<R>* A = buf;
   C<R>* B = buf + kNF * ny;
-  const double kappa2 = a.diag[D_KAPPA * p.nk + j] / ((double)p.ppc * p.nx * p.ny);
-  const R rdxi = R(1.0 / p.dxi);
-  const R kap = R(kappa2);
+  __shared__ R s_kap;
+  if (threadIdx.x == 0) s_kap = R(a.diag[D_KAPPA * p.nk + j]) * a.k.inv_npc;
+  const R rdxi = a.k.rdxi;
   const C<R>* __restrict__ rspec = a.rspec;
   C<R>* __restrict__ bold = a.bold;
   const C<R>* __restrict__ jprev = a.jprev;
@@ -687,6 +714,7 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
       for (int f = 0; f < kNF; ++f) A[f * ny + ky] = v[f];
     }
     __syncthreads();
+    const R kap = s_kap;
     C<R>* Z = block_fft(A, B, kNF, p.py, tw, -1);
     C<R>* O = (Z == A) ? B : A;
     const R pw = (kx == 0 || ((p.nx % 2 == 0) && 2 * kx == p.nx)) ? R(1) : R(2);
@@ -696,8 +724,14 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
       const C<R> Bxo = bold[ix0], Byo = bold[ix1];
       const C<R> Jx = Z[ky], Jy = Z[ny + ky], Jz = Z[2 * ny + ky];
       const C<R> Jxh = Z[3 * ny + ky], Jyh = Z[4 * ny + ky];
-      if (kx == 0 && ky == 0)
+      if (kx == 0 && ky == 0) {
+        // <J_z> for the k = 0 mode: the grid mean plus the uniform parts left out of the grid
+        // deposits (plasma reference state and beam reference density)
+        const double opp0 = 1.0 + psi0;
+        const double jz_ref =
+            psi0 * (2.0 + psi0) / (2.0 * opp0 * opp0) + (a.bref ? a.bref[j] : 0.0);
         a.diag[D_JZ * p.nk + j] = (double)Jz.x / ((double)p.nx * p.ny) + jz_ref;
+      }
       const Kv<R> k = kvec(a.ktab, nxh, ny, kx, ky);
       C<R> obx{0, 0}, oby{0, 0}, obz{0, 0}, oez{0, 0};
       if (k.k2 > R(0)) {
@@ -795,7 +829,8 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
   const int npair = 2;
   C<R>* A = buf;
   C<R>* B = buf + 3 * nx;
-  const R scale = R(1.0 / ((double)nx * ny));
+  const R scale = a.k.scale;
+  const R ez0r = R(ez0j);
   const C<R>* __restrict__ cspec = a.cspec;
   R* __restrict__ fg = a.fg;
   __shared__ double red[64];
@@ -843,7 +878,7 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
       }
       if (!psi_mode && last) {
         const R wx = -node[FG_GX], wy = -node[FG_GY];
-        const R ez = R(ez0j + (double)v[3]);
+        const R ez = ez0r + v[3];
         st8(a.slab + (((size_t)j * ny + q) * nx + x) * 8, wx, wy, ez, v[0], v[1], v[2]);
         const R Ex = wx + v[1], Ey = wy - v[0];
         en[0] += Ex * Ex;
@@ -914,15 +949,13 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<R> a) {
 
   for (int j = 0; j < p.nk; ++j) {
     double ez0n = ez0h, ez0j = ez0h;
-    const double opp0 = 1.0 + psi0;
-    const double jz_ref = psi0 * (2.0 + psi0) / (2.0 * opp0 * opp0) + (a.bref ? a.bref[j] : 0.0);
     for (int it = 0; it < p.n_pc; ++it) {
       const bool first = (it == 0), last = (it == p.n_pc - 1);
       dep_phase(a, tile, DEP_TRIAL, j, psi0, first, last);
       if (!sync(j, 4 * it + 0)) return;
       row_phase(a, buf, tw, DEP_TRIAL, j);
       if (!sync(j, 4 * it + 1)) return;
-      col_phase_b(a, buf, tw, j, last, jz_ref);
+      col_phase_b(a, buf, tw, j, last, psi0);
       if (!sync(j, 4 * it + 2)) return;
       if (last) {
         const double jz = *((volatile double*)&a.diag[D_JZ * p.nk + j]);
