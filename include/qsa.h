@@ -78,7 +78,8 @@ typedef struct {
   int32_t n_species, n_modes;
   int32_t precision;       /* qsa_precision */
   int32_t n_pc_iter;       /* predictor-corrector field solves per slice (>= 1) */
-  int32_t _reserved;
+  int32_t pipeline_depth;  /* beam steps one qsa_advance launch keeps in flight (0, 1: none;
+                              2..16: pipelined, see qsa_advance) */
   double Lx, Ly, Lxi;      /* periodic box (Lx, Ly) and window length, c/omega_p */
   double dt;               /* beam time step, 1/omega_p */
   double psi_floor;        /* lower bound applied to 1 + psi of plasma particles */
@@ -142,6 +143,19 @@ int qsa_plasma_sweep(qsa_handle* h);
  * relativistic Boris), drop particles with xi >= Lxi, and deposit the beam sources of the
  * next sweep.  QSA_ERR_STATE before the first sweep.  Asynchronous. */
 int qsa_beam_step(qsa_handle* h);
+
+/* n_steps beam steps, each a plasma sweep followed by a beam push: the same result as
+ * n_steps x (qsa_plasma_sweep; qsa_beam_step), up to the summation order of the deposits.
+ * With pipeline_depth S >= 2 the steps run in persistent launches of up to S steps each, as a
+ * wavefront in xi: the sweep of a step trails the previous step by a few slices, since its
+ * slice j needs only the beam sources of nodes <= j + 1, which are final once the previous
+ * step has pushed every particle that can land there (beam particles only move backwards in
+ * the window; the gates follow the particles' actual xi extent per layer, so the schedule is
+ * exact for any drift).  The work of the steps in flight is spread over every SM in each
+ * phase.  Memory: S sweep slots (each one field slab of (nxi+1) nx ny 8 values) and S + 1
+ * source buffers.  Afterwards the slab and the diagnostics are those of the last sweep and
+ * the sources those of the next.  n_steps = 0 is a no-op.  Asynchronous. */
+int qsa_advance(qsa_handle* h, int32_t n_steps);
 
 /* Copy the per-slice diagnostics of the last sweep into `out`; synchronises and returns the
  * latched device status (QSA_ERR_TIMEOUT, QSA_WARN_PSI_FLOOR, ...). */

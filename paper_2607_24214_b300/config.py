@@ -66,6 +66,7 @@ class Params:
     psi_floor: float = 0.05
     seed: int = 0
     spin_limit: int = 1 << 26
+    pipeline_depth: int = 1          # beam steps in flight per qsa_advance launch (1: none)
     steps: int = 1                   # beam steps of the named workload (not part of the C struct)
 
     @property

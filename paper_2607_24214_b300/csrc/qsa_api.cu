@@ -11,6 +11,7 @@
 #include "qsa_beam.cuh"
 #include "qsa_common.cuh"
 #include "qsa_fft.cuh"
+#include "qsa_pipe.cuh"
 #include "qsa_sweep.cuh"
 
 using namespace qsa;
@@ -69,6 +70,7 @@ struct qsa_handle {
   int64_t bytes = 0;
   int64_t launches = 0;
   int64_t sweeps = 0;
+  int64_t pushes = 0;  // beam pushes done: the source and extent rings are indexed by it
   bool src_valid = false;
   std::string err;
   // typed state lives behind these pointers (R = double for FP64, float for mixed)
@@ -125,14 +127,19 @@ void dfree_all(qsa_handle* h) {
 template <typename R>
 struct State {
   using BR = R;
-  SweepArgs<R> sa{};
+  // sweep slots: slot 0 serves the single sweep; a pipelined launch of m steps uses 0..m-1
+  std::vector<SweepArgs<R>> slots;
+  int last_slot = 0;                // slot of the last sweep (slab, diagnostics)
   std::vector<BeamArrays<BR>> beams;
   std::vector<SpeciesDev> species;
   std::vector<BeamConst<R>> bconst;
   ModesDev modes{};
-  R* src = nullptr;
-  R* slab = nullptr;
-  double* diag = nullptr;
+  std::vector<R*> srcs;             // source ring, S + 1 entries [nk][ny][nx][4]
+  std::vector<int*> cmaxs;          // extent ring, S + 1 entries [nxi]
+  int* dmin = nullptr;              // min over live particles of (xi cell - home layer)
+  PipeTable<R>* ptab = nullptr;     // device copy of the pipeline table
+  int pipe_grid = 0;
+  size_t pipe_smem = 0;
   unsigned long long* lost = nullptr;
   unsigned* bar = nullptr;  // [0] count, [1] generation
   int* status = nullptr;
@@ -147,6 +154,18 @@ struct State {
 
 template <typename R>
 State<R>* S(qsa_handle* h) { return reinterpret_cast<State<R>*>(h->st); }
+
+// Ring entries of the beam state after `pushes` pushes: its sources and its extents.
+template <typename R>
+R* ring_src(qsa_handle* h, int64_t pushes) {
+  State<R>* s = S<R>(h);
+  return s->srcs[(size_t)(pushes % (int64_t)s->srcs.size())];
+}
+template <typename R>
+int* ring_cmax(qsa_handle* h, int64_t pushes) {
+  State<R>* s = S<R>(h);
+  return s->cmaxs[(size_t)(pushes % (int64_t)s->cmaxs.size())];
+}
 
 #define CK(call)                                              \
   do {                                                        \
@@ -166,32 +185,18 @@ int setup(qsa_handle* h) {
   const DevParams& dp = h->dp;
   const size_t g = (size_t)dp.nx * dp.ny;
   const size_t spec = (size_t)dp.nxh * dp.ny;
-  SweepArgs<R>& a = s->sa;
-  a.p = dp;
-  a.k = sweep_consts<R>(dp);
   auto A = [&](size_t bytes) { return dalloc(h, bytes); };
-  const size_t np = (size_t)dp.np;
-  R** pl[5] = {&a.pox, &a.poy, &a.pux, &a.puy, &a.ppsi};
-  for (auto p : pl) if (!(*p = (R*)A(np * sizeof(R)))) return fail(h, QSA_ERR_OOM, "plasma");
-  if (!(a.fg = (R*)A(g * kFG * sizeof(R)))) return fail(h, QSA_ERR_OOM, "grids");
-  if (!(a.part = (R*)A((size_t)dp.ny * kTileRows * dp.nx * kNF * sizeof(R))) ||
-      !(a.ovf = (R*)A(g * kNF * sizeof(R))) ||
-      !(a.rspec = (C<R>*)A(kNF * spec * sizeof(C<R>))) ||
-      !(a.cspec = (C<R>*)A(4 * spec * sizeof(C<R>))) ||
-      !(a.jprev = (C<R>*)A(2 * spec * sizeof(C<R>))) ||
-      !(a.bold = (C<R>*)A(2 * spec * sizeof(C<R>))) ||
-      !(s->tw = (C<R>*)A((size_t)(dp.nx + dp.ny) * sizeof(C<R>))) ||
-      !(s->src = (R*)A((size_t)dp.nk * g * 4 * sizeof(R))) ||
-      !(s->slab = (R*)A((size_t)dp.nk * g * 8 * sizeof(R))) ||
-      !(s->diag = (double*)A((size_t)D_COUNT * dp.nk * sizeof(double))) ||
-      !(s->lost = (unsigned long long*)A(sizeof(unsigned long long))) ||
-      !(s->bar = (unsigned*)A(2 * sizeof(unsigned))) ||
-      !(s->status = (int*)A(sizeof(int))) ||
-      !(s->bref = (double*)A((size_t)dp.nk * sizeof(double))) ||
-      !(s->ptimes = (unsigned long long*)A(kTimedSlices * kTimedPhases * 2 * 8)) ||
-      !(s->ktab = (R*)A((size_t)(2 * dp.nxh + 2 * dp.ny) * sizeof(R))))
-    return fail(h, QSA_ERR_OOM, "sweep buffers");
-  a.ptimes = s->ptimes;
+  const int nslot = h->prm.pipeline_depth > 1 ? h->prm.pipeline_depth : 1;  // depth S
+  // tables shared by every slot
+  R* ktab = (R*)A((size_t)(2 * dp.nxh + 2 * dp.ny) * sizeof(R));
+  C<R>* twp = (C<R>*)A((size_t)(dp.nx + dp.ny) * sizeof(C<R>));
+  double* bref = (double*)A((size_t)dp.nk * sizeof(double));
+  unsigned* bar = (unsigned*)A(2 * sizeof(unsigned));
+  int* status = (int*)A(sizeof(int));
+  s->lost = (unsigned long long*)A(sizeof(unsigned long long));
+  s->dmin = (int*)A(sizeof(int));
+  if (!ktab || !twp || !bref || !bar || !status || !s->lost || !s->dmin)
+    return fail(h, QSA_ERR_OOM, "sweep tables");
   {
     // k_x = 2 pi m / Lx (m = 0..nx/2), k_y = 2 pi m / Ly (m in numpy.fft order), and the
     // first-derivative symbols, zero at the Nyquist index of an even grid
@@ -207,56 +212,103 @@ int setup(qsa_handle* h) {
       kt[2 * dp.nxh + m] = R(k);
       kt[2 * dp.nxh + dp.ny + m] = (dp.ny % 2 == 0 && 2 * m == dp.ny) ? R(0) : R(k);
     }
-    CK(cudaMemcpyAsync(s->ktab, kt.data(), kt.size() * sizeof(R), cudaMemcpyHostToDevice,
+    CK(cudaMemcpyAsync(ktab, kt.data(), kt.size() * sizeof(R), cudaMemcpyHostToDevice,
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    a.ktab = s->ktab;
   }
-  // twiddles exp(-2 pi i m/n), built in FP64 on the host
-  std::vector<C<R>> tw(dp.nx + dp.ny);
-  for (int m = 0; m < dp.nx; ++m) {
-    const double t = -2.0 * M_PI * m / dp.nx;
-    tw[m] = C<R>{R(std::cos(t)), R(std::sin(t))};
+  {
+    // twiddles exp(-2 pi i m/n), built in FP64 on the host
+    std::vector<C<R>> tw(dp.nx + dp.ny);
+    for (int m = 0; m < dp.nx; ++m) {
+      const double t = -2.0 * M_PI * m / dp.nx;
+      tw[m] = C<R>{R(std::cos(t)), R(std::sin(t))};
+    }
+    for (int m = 0; m < dp.ny; ++m) {
+      const double t = -2.0 * M_PI * m / dp.ny;
+      tw[dp.nx + m] = C<R>{R(std::cos(t)), R(std::sin(t))};
+    }
+    CK(cudaMemcpyAsync(twp, tw.data(), tw.size() * sizeof(C<R>), cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
   }
-  for (int m = 0; m < dp.ny; ++m) {
-    const double t = -2.0 * M_PI * m / dp.ny;
-    tw[dp.nx + m] = C<R>{R(std::cos(t)), R(std::sin(t))};
-  }
-  CK(cudaMemcpyAsync(s->tw, tw.data(), tw.size() * sizeof(C<R>), cudaMemcpyHostToDevice,
-                     h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  a.twx = s->tw;
-  a.twy = s->tw + dp.nx;
-  a.src = s->src;
-  a.slab = s->slab;
-  a.diag = s->diag;
-  a.bar = Barrier{s->bar, s->status, (long long)h->prm.spin_limit};
-  CK(cudaMemsetAsync(s->bar, 0, 2 * sizeof(unsigned), h->stream));
-  CK(cudaMemsetAsync(s->status, 0, sizeof(int), h->stream));
+  CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), h->stream));
+  CK(cudaMemsetAsync(status, 0, sizeof(int), h->stream));
   CK(cudaMemsetAsync(s->lost, 0, sizeof(unsigned long long), h->stream));
-  CK(cudaMemsetAsync(s->slab, 0, (size_t)dp.nk * g * 8 * sizeof(R), h->stream));
-  CK(cudaMemsetAsync(s->diag, 0, (size_t)D_COUNT * dp.nk * sizeof(double), h->stream));
-  // launch shape of the persistent kernels
-  s->smem = sweep_smem<R>(dp);
+  CK(cudaMemsetAsync(s->dmin, 0, sizeof(int), h->stream));
+  // launch shapes of the persistent kernels
+  const size_t smem = sweep_smem<R>(dp);
   CK(cudaFuncSetAttribute(sweep_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)s->smem));
+                          (int)smem));
   CK(cudaFuncSetAttribute(solve_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)s->smem));
+                          (int)smem));
   CK(cudaFuncSetAttribute(beam_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)beam_smem_bytes<R>(dp.nx)));
   CK(cudaFuncSetAttribute(beam_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)beam_smem_bytes<R>(dp.nx)));
   int per_sm = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<R>, kThreads, s->smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<R>, kThreads, smem));
   int per_sm2 = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, solve_kernel<R>, kThreads, s->smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, solve_kernel<R>, kThreads, smem));
   per_sm = per_sm < per_sm2 ? per_sm : per_sm2;
   if (per_sm < 1) return fail(h, QSA_ERR_ARG, "sweep kernel does not fit on an SM");
   const int work = dp.ny > dp.nxh ? dp.ny : dp.nxh;
-  s->grid = per_sm * h->num_sms;
-  if (s->grid > work) s->grid = work;
-  if (!(a.dpart = (double*)A((size_t)dp.nk * s->grid * P_COUNT * sizeof(double))))
-    return fail(h, QSA_ERR_OOM, "diagnostic partials");
+  int grid = per_sm * h->num_sms;
+  if (grid > work) grid = work;
+  int dgrid = grid;  // blocks whose diagnostic partials a slot holds
+  if (nslot > 1) {
+    s->pipe_smem = pipe_smem_bytes<R>(dp.nx, dp.ny);
+    CK(cudaFuncSetAttribute(pipe_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)s->pipe_smem));
+    int per_sm3 = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, pipe_kernel<R>, kThreads,
+                                                     s->pipe_smem));
+    if (per_sm3 < 1) return fail(h, QSA_ERR_ARG, "pipelined kernel does not fit on an SM");
+    s->pipe_grid = per_sm3 * h->num_sms;
+    if (s->pipe_grid > dgrid) dgrid = s->pipe_grid;
+  }
+  // sweep slots
+  s->slots.resize(nslot);
+  for (int i = 0; i < nslot; ++i) {
+    SweepArgs<R>& a = s->slots[i];
+    a = SweepArgs<R>{};
+    a.p = dp;
+    a.k = sweep_consts<R>(dp);
+    const size_t np = (size_t)dp.np;
+    R** pl[5] = {&a.pox, &a.poy, &a.pux, &a.puy, &a.ppsi};
+    for (auto q : pl) if (!(*q = (R*)A(np * sizeof(R)))) return fail(h, QSA_ERR_OOM, "plasma");
+    if (!(a.fg = (R*)A(g * kFG * sizeof(R))) ||
+        !(a.part = (R*)A((size_t)dp.ny * kTileRows * dp.nx * kNF * sizeof(R))) ||
+        !(a.ovf = (R*)A(g * kNF * sizeof(R))) ||
+        !(a.rspec = (C<R>*)A(kNF * spec * sizeof(C<R>))) ||
+        !(a.cspec = (C<R>*)A(4 * spec * sizeof(C<R>))) ||
+        !(a.jprev = (C<R>*)A(2 * spec * sizeof(C<R>))) ||
+        !(a.bold = (C<R>*)A(2 * spec * sizeof(C<R>))) ||
+        !(a.slab = (R*)A((size_t)dp.nk * g * 8 * sizeof(R))) ||
+        !(a.diag = (double*)A((size_t)D_COUNT * dp.nk * sizeof(double))) ||
+        !(a.dpart = (double*)A((size_t)dp.nk * dgrid * P_COUNT * sizeof(double))))
+      return fail(h, QSA_ERR_OOM, "sweep buffers");
+    if (i == 0 &&
+        !(a.ptimes = (unsigned long long*)A(kTimedSlices * kTimedPhases * 2 * 8)))
+      return fail(h, QSA_ERR_OOM, "sweep buffers");
+    a.twx = twp;
+    a.twy = twp + dp.nx;
+    a.ktab = ktab;
+    a.bref = bref;
+    a.src = nullptr;
+    a.bar = Barrier{bar, status, (long long)h->prm.spin_limit};
+    CK(cudaMemsetAsync(a.slab, 0, (size_t)dp.nk * g * 8 * sizeof(R), h->stream));
+    CK(cudaMemsetAsync(a.diag, 0, (size_t)D_COUNT * dp.nk * sizeof(double), h->stream));
+  }
+  s->grid = grid;
+  s->smem = smem;
+  // source and extent rings
+  for (int i = 0; i <= nslot; ++i) {
+    R* sb = (R*)A((size_t)dp.nk * g * 4 * sizeof(R));
+    int* cm = (int*)A((size_t)(dp.nxi > 0 ? dp.nxi : 1) * sizeof(int));
+    if (!sb || !cm) return fail(h, QSA_ERR_OOM, "source ring");
+    s->srcs.push_back(sb);
+    s->cmaxs.push_back(cm);
+  }
   // beam species
   const qsa_params& P = h->prm;
   s->modes.n = P.n_modes;
@@ -318,9 +370,30 @@ int setup(qsa_handle* h) {
       s->bref_jz[k] += rho * (1.0 - sp.omvbar);
     }
   }
-  CK(cudaMemcpyAsync(s->bref, s->bref_jz.data(), dp.nk * sizeof(double), cudaMemcpyHostToDevice,
+  CK(cudaMemcpyAsync(bref, s->bref_jz.data(), dp.nk * sizeof(double), cudaMemcpyHostToDevice,
                      h->stream));
-  a.bref = s->bref;
+  // the pipeline table, on the device once
+  if (nslot > 1) {
+    PipeTable<R> t{};
+    for (int i = 0; i < nslot; ++i) t.st[i] = s->slots[i];
+    for (int i = 0; i <= nslot; ++i) {
+      t.srcbuf[i] = s->srcs[i];
+      t.cmaxbuf[i] = s->cmaxs[i];
+    }
+    t.nslot = nslot;
+    t.nspecies = (int)s->species.size();
+    t.max_push = 2;
+    for (int si = 0; si < t.nspecies; ++si) {
+      t.beam[si] = s->beams[si];
+      t.sp[si] = s->species[si];
+      t.bc[si] = s->bconst[si];
+    }
+    t.dmin = s->dmin;
+    t.lost = s->lost;
+    if (!(s->ptab = (PipeTable<R>*)A(sizeof(PipeTable<R>))))
+      return fail(h, QSA_ERR_OOM, "pipeline table");
+    CK(cudaMemcpyAsync(s->ptab, &t, sizeof(t), cudaMemcpyHostToDevice, h->stream));
+  }
   CK(cudaStreamSynchronize(h->stream));
   return QSA_OK;
 }
@@ -329,13 +402,17 @@ template <typename R>
 int deposit_sources(qsa_handle* h) {
   State<R>* s = S<R>(h);
   const DevParams& dp = h->dp;
-  CK(cudaMemsetAsync(s->src, 0, (size_t)dp.nk * dp.nx * dp.ny * 4 * sizeof(R), h->stream));
+  R* src = ring_src<R>(h, h->pushes);
+  int* cmax = ring_cmax<R>(h, h->pushes);
+  CK(cudaMemsetAsync(src, 0, (size_t)dp.nk * dp.nx * dp.ny * 4 * sizeof(R), h->stream));
+  CK(cudaMemsetAsync(cmax, 0xFF, (size_t)(dp.nxi > 0 ? dp.nxi : 1) * sizeof(int), h->stream));
+  CK(cudaMemsetAsync(s->dmin, 0, sizeof(int), h->stream));
   for (size_t si = 0; si < s->beams.size(); ++si) {
     const auto& b = s->beams[si];
     if (b.n == 0) continue;
     const unsigned groups = (unsigned)(s->species[si].nkb * dp.ny);
     beam_kernel<R, false><<<groups, kThreads, beam_smem_bytes<R>(dp.nx), h->stream>>>(
-        b, dp, s->species[si], s->bconst[si], s->slab, s->src, nullptr);
+        b, dp, s->species[si], s->bconst[si], nullptr, src, nullptr, Extent{cmax, s->dmin});
     ++h->launches;
     CK(cudaGetLastError());
   }
@@ -391,23 +468,76 @@ int sweep(qsa_handle* h) {
   }
   const size_t g = (size_t)dp.nx * dp.ny;
   const size_t spec = (size_t)dp.nxh * dp.ny;
-  SweepArgs<R>& a = s->sa;
+  SweepArgs<R>& a = s->slots[0];
   CK(cudaMemsetAsync(a.ovf, 0, g * kNF * sizeof(R), h->stream));
   CK(cudaMemsetAsync(a.bold, 0, 2 * spec * sizeof(C<R>), h->stream));
   CK(cudaMemsetAsync(a.fg, 0, g * kFG * sizeof(R), h->stream));
-  CK(cudaMemsetAsync(s->bar, 0, sizeof(unsigned), h->stream));
-  CK(cudaMemsetAsync(s->ptimes, 0, kTimedSlices * kTimedPhases * 2 * 8, h->stream));
+  CK(cudaMemsetAsync(a.bar.count, 0, sizeof(unsigned), h->stream));
+  CK(cudaMemsetAsync(a.ptimes, 0, kTimedSlices * kTimedPhases * 2 * 8, h->stream));
   const int nd = D_COUNT * dp.nk;
-  diag_init_kernel<<<(nd + 255) / 256, 256, 0, h->stream>>>(s->diag, dp.nk);
+  diag_init_kernel<<<(nd + 255) / 256, 256, 0, h->stream>>>(a.diag, dp.nk);
   ++h->launches;
-  a.src = s->src;
+  a.src = ring_src<R>(h, h->pushes);
   void* args[] = {&a};
   CK(cudaLaunchCooperativeKernel((void*)sweep_kernel<R>, dim3(s->grid), dim3(kThreads), args,
                                  s->smem, h->stream));
   ++h->launches;
-  diag_reduce_kernel<<<dp.nk, 256, 0, h->stream>>>(a.dpart, s->grid, s->diag, dp.nk);
+  diag_reduce_kernel<<<dp.nk, 256, 0, h->stream>>>(a.dpart, s->grid, a.diag, dp.nk);
   ++h->launches;
   ++h->sweeps;
+  s->last_slot = 0;
+  return QSA_OK;
+}
+
+// n beam steps (sweep + push each) as wavefronts of up to S steps per persistent launch.
+template <typename R>
+int advance_pipelined(qsa_handle* h, int n) {
+  State<R>* s = S<R>(h);
+  const DevParams& dp = h->dp;
+  const int nslot = (int)s->slots.size();
+  if (!h->src_valid) {
+    int rc = deposit_sources<R>(h);
+    if (rc) return rc;
+  }
+  const size_t g = (size_t)dp.nx * dp.ny;
+  const size_t spec = (size_t)dp.nxh * dp.ny;
+  const int nd = D_COUNT * dp.nk;
+  while (n > 0) {
+    const int m = n < nslot ? n : nslot;
+    for (int i = 1; i <= m; ++i) {
+      CK(cudaMemsetAsync(ring_src<R>(h, h->pushes + i), 0, (size_t)dp.nk * g * 4 * sizeof(R),
+                         h->stream));
+      CK(cudaMemsetAsync(ring_cmax<R>(h, h->pushes + i), 0xFF,
+                         (size_t)(dp.nxi > 0 ? dp.nxi : 1) * sizeof(int), h->stream));
+    }
+    for (int i = 0; i < m; ++i) {
+      SweepArgs<R>& a = s->slots[i];
+      CK(cudaMemsetAsync(a.ovf, 0, g * kNF * sizeof(R), h->stream));
+      CK(cudaMemsetAsync(a.bold, 0, 2 * spec * sizeof(C<R>), h->stream));
+      CK(cudaMemsetAsync(a.fg, 0, g * kFG * sizeof(R), h->stream));
+      diag_init_kernel<<<(nd + 255) / 256, 256, 0, h->stream>>>(a.diag, dp.nk);
+      ++h->launches;
+    }
+    Barrier bar = s->slots[0].bar;
+    CK(cudaMemsetAsync(bar.count, 0, sizeof(unsigned), h->stream));
+    const PipeTable<R>* tab = s->ptab;
+    int r0 = (int)(h->pushes % (int64_t)(nslot + 1));
+    int steps = m;
+    void* args[] = {&tab, &r0, &steps, &bar};
+    CK(cudaLaunchCooperativeKernel((void*)pipe_kernel<R>, dim3(s->pipe_grid), dim3(kThreads),
+                                   args, s->pipe_smem, h->stream));
+    ++h->launches;
+    for (int i = 0; i < m; ++i) {
+      SweepArgs<R>& a = s->slots[i];
+      diag_reduce_kernel<<<dp.nk, 256, 0, h->stream>>>(a.dpart, s->pipe_grid, a.diag, dp.nk);
+      ++h->launches;
+    }
+    h->pushes += m;
+    h->sweeps += m;
+    s->last_slot = m - 1;
+    n -= m;
+  }
+  h->src_valid = true;
   return QSA_OK;
 }
 
@@ -415,16 +545,21 @@ template <typename R>
 int beam_step(qsa_handle* h) {
   State<R>* s = S<R>(h);
   const DevParams& dp = h->dp;
-  CK(cudaMemsetAsync(s->src, 0, (size_t)dp.nk * dp.nx * dp.ny * 4 * sizeof(R), h->stream));
+  R* src = ring_src<R>(h, h->pushes + 1);
+  int* cmax = ring_cmax<R>(h, h->pushes + 1);
+  const R* slab = s->slots[s->last_slot].slab;
+  CK(cudaMemsetAsync(src, 0, (size_t)dp.nk * dp.nx * dp.ny * 4 * sizeof(R), h->stream));
+  CK(cudaMemsetAsync(cmax, 0xFF, (size_t)(dp.nxi > 0 ? dp.nxi : 1) * sizeof(int), h->stream));
   for (size_t si = 0; si < s->beams.size(); ++si) {
     const auto& b = s->beams[si];
     if (b.n == 0) continue;
     const unsigned groups = (unsigned)(s->species[si].nkb * dp.ny);
     beam_kernel<R, true><<<groups, kThreads, beam_smem_bytes<R>(dp.nx), h->stream>>>(
-        b, dp, s->species[si], s->bconst[si], s->slab, s->src, s->lost);
+        b, dp, s->species[si], s->bconst[si], slab, src, s->lost, Extent{cmax, nullptr});
     ++h->launches;
     CK(cudaGetLastError());
   }
+  ++h->pushes;
   h->src_valid = true;
   return QSA_OK;
 }
@@ -444,9 +579,10 @@ int diagnostics(qsa_handle* h, qsa_diag* out) {
   std::vector<double> d((size_t)D_COUNT * nk);
   int st = 0;
   unsigned long long lost = 0;
-  CK(cudaMemcpyAsync(d.data(), s->diag, d.size() * sizeof(double), cudaMemcpyDeviceToHost,
+  const SweepArgs<R>& a = s->slots[s->last_slot];
+  CK(cudaMemcpyAsync(d.data(), a.diag, d.size() * sizeof(double), cudaMemcpyDeviceToHost,
                      h->stream));
-  CK(cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&st, a.bar.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(&lost, s->lost, sizeof(lost), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   auto row = [&](int r) { return d.data() + (size_t)r * nk; };
@@ -482,7 +618,8 @@ int copy_field(qsa_handle* h, int field, int j0, int j1, double* out, bool sourc
   const int stride = source ? 4 : 8;
   const size_t g = (size_t)dp.nx * dp.ny;
   std::vector<R> tmp((size_t)(j1 - j0) * g * stride);
-  const R* base = (source ? s->src : s->slab) + (size_t)j0 * g * stride;
+  const R* base = (source ? ring_src<R>(h, h->pushes) : s->slots[s->last_slot].slab) +
+                  (size_t)j0 * g * stride;
   CK(cudaMemcpyAsync(tmp.data(), base, tmp.size() * sizeof(R), cudaMemcpyDeviceToHost,
                      h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -545,13 +682,13 @@ int field_solve(qsa_handle* h, const double* const* in, double kappa2, double* o
   State<R>* s = S<R>(h);
   const DevParams& dp = h->dp;
   const size_t g = (size_t)dp.nx * dp.ny;
-  SweepArgs<R> a = s->sa;
+  SweepArgs<R> a = s->slots[0];
   a.src = nullptr;
   a.bref = nullptr;
   std::vector<R> ov(g * kNF);
   std::vector<double> dg((size_t)D_COUNT * dp.nk, 0.0);
   dg[(size_t)D_KAPPA * dp.nk] = kappa2 * dp.ppc * (double)dp.nx * dp.ny;
-  CK(cudaMemcpyAsync(s->diag, dg.data(), dg.size() * sizeof(double), cudaMemcpyHostToDevice,
+  CK(cudaMemcpyAsync(a.diag, dg.data(), dg.size() * sizeof(double), cudaMemcpyHostToDevice,
                      h->stream));
   CK(cudaMemsetAsync(a.part, 0, (size_t)dp.ny * kTileRows * dp.nx * kNF * sizeof(R), h->stream));
   CK(cudaMemsetAsync(a.jprev, 0, 2 * (size_t)dp.nxh * dp.ny * sizeof(C<R>), h->stream));
@@ -567,7 +704,7 @@ int field_solve(qsa_handle* h, const double* const* in, double kappa2, double* o
   }
   CK(cudaMemcpyAsync(a.ovf, ov.data(), ov.size() * sizeof(R), cudaMemcpyHostToDevice,
                      h->stream));
-  CK(cudaMemsetAsync(s->bar, 0, sizeof(unsigned), h->stream));
+  CK(cudaMemsetAsync(a.bar.count, 0, sizeof(unsigned), h->stream));
   int which = 0;
   void* args[] = {&a, &which};
   CK(cudaLaunchCooperativeKernel((void*)solve_kernel<R>, dim3(s->grid), dim3(kThreads), args,
@@ -593,7 +730,7 @@ int field_solve(qsa_handle* h, const double* const* in, double kappa2, double* o
   for (size_t i = 0; i < g; ++i) ov[i] = R(in[0][i]);
   CK(cudaMemcpyAsync(a.ovf, ov.data(), g * 3 * sizeof(R), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemsetAsync(a.part, 0, (size_t)dp.ny * kTileRows * dp.nx * kNF * sizeof(R), h->stream));
-  CK(cudaMemsetAsync(s->bar, 0, sizeof(unsigned), h->stream));
+  CK(cudaMemsetAsync(a.bar.count, 0, sizeof(unsigned), h->stream));
   which = 1;
   CK(cudaLaunchCooperativeKernel((void*)solve_kernel<R>, dim3(s->grid), dim3(kThreads), args,
                                  s->smem, h->stream));
@@ -604,7 +741,7 @@ int field_solve(qsa_handle* h, const double* const* in, double kappa2, double* o
     if ((rc = get(comps, o, 3))) return rc;
   }
   int st = 0;
-  CK(cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&st, a.bar.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   rc = status_code(st);
   return rc < 0 ? fail(h, rc, "device wait exceeded spin_limit") : QSA_OK;
@@ -624,6 +761,8 @@ int validate(const qsa_params* p, std::string& why) {
   if (p->n_pc_iter < 1 || p->n_pc_iter > 64) return bad("n_pc_iter must be in 1..64");
   if (!(p->psi_floor > 0 && p->psi_floor < 1)) return bad("psi_floor must be in (0, 1)");
   if (p->spin_limit < 0) return bad("spin_limit must be >= 0");
+  if (p->pipeline_depth < 0 || p->pipeline_depth > kMaxPipe)
+    return bad("pipeline_depth must be in 0..16");
   const double dxi = p->Lxi / p->nxi;
   for (int s = 0; s < p->n_species; ++s) {
     const qsa_species& q = p->species[s];
@@ -745,6 +884,20 @@ int qsa_beam_step(qsa_handle* h) {
   return h->fp64 ? beam_step<double>(h) : beam_step<float>(h);
 }
 
+int qsa_advance(qsa_handle* h, int32_t n_steps) {
+  if (!h) return QSA_ERR_ARG;
+  if (n_steps < 0) return fail(h, QSA_ERR_ARG, "n_steps must be >= 0");
+  if (h->prm.pipeline_depth > 1)
+    return h->fp64 ? advance_pipelined<double>(h, n_steps) : advance_pipelined<float>(h, n_steps);
+  for (int32_t i = 0; i < n_steps; ++i) {
+    int rc = h->fp64 ? sweep<double>(h) : sweep<float>(h);
+    if (rc) return rc;
+    rc = h->fp64 ? beam_step<double>(h) : beam_step<float>(h);
+    if (rc) return rc;
+  }
+  return QSA_OK;
+}
+
 int qsa_diagnostics(qsa_handle* h, qsa_diag* out) {
   if (!h || !out) return QSA_ERR_ARG;
   return h->fp64 ? diagnostics<double>(h, out) : diagnostics<float>(h, out);
@@ -783,7 +936,8 @@ int qsa_phase_times(qsa_handle* h, int64_t* out, int cap) {
   if (!h || !out) return QSA_ERR_ARG;
   const int n = kTimedSlices * kTimedPhases * 2;
   if (cap < n) return fail(h, QSA_ERR_ARG, "capacity below 512");
-  unsigned long long* dev = h->fp64 ? S<double>(h)->ptimes : S<float>(h)->ptimes;
+  unsigned long long* dev =
+      h->fp64 ? S<double>(h)->slots[0].ptimes : S<float>(h)->slots[0].ptimes;
   CK(cudaMemcpyAsync(out, dev, n * 8, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return QSA_OK;

@@ -384,24 +384,40 @@ __device__ __forceinline__ void boris(float& ux, float& uy, float2& uz, const fl
   uz = make_float2(hi, lo - (hi - sum));
 }
 
+// Where the live particles of a group sit after its push (or now, without a push): the
+// largest xi cell, max-reduced per home layer into cmax[layer] (a later push of the layer
+// gathers slab nodes up to that cell + 1), and the smallest cell minus the home layer,
+// min-reduced into dmin (a particle deposits at nodes >= its home layer + dmin).  Either
+// pointer may be null.
+struct Extent {
+  int* cmax;
+  int* dmin;
+};
+
+// One group of a species: the ppc * nx particles whose home is xi cell (layer) k and row iy.
 // PUSH = false: deposit the current beam (sources of the first sweep).  PUSH = true: push
 // every live particle by dt through the slab, drop those with xi >= Lxi, and deposit the
-// sources of the next sweep.  Grid: one block per (xi cell, row) group of the species.
+// sources of the next sweep.  Called by every thread of the block; tile holds
+// beam_smem_bytes(nx).
 template <typename BR, bool PUSH>
-__global__ void __launch_bounds__(256, 2) beam_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp,
-                                                   BeamConst<BR> bc, const BR* __restrict__ slab,
-                                                   BR* src, unsigned long long* lost) {
+__device__ void beam_group(const BeamArrays<BR>& b, const DevParams& p, const SpeciesDev& sp,
+                           const BeamConst<BR>& bc, const BR* __restrict__ slab, BR* src,
+                           unsigned long long* lost, Extent ext, int grp, BR* tile) {
   using UZ = typename UzT<BR>::T;
-  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_ext[2];
   Group<BR> g;
-  g.tile = reinterpret_cast<BR*>(smem);
-  const int grp = blockIdx.x;
+  g.tile = tile;
   g.iy = grp % p.ny;
   g.kabs = sp.k0 + grp / p.ny;
   const int nx = p.nx;
   const int tn = 2 * 4 * nx * 4;
   for (int e = threadIdx.x; e < tn; e += blockDim.x) g.tile[e] = BR(0);
+  if (threadIdx.x == 0) {
+    s_ext[0] = -1;
+    s_ext[1] = 0;
+  }
   __syncthreads();
+  int cmax_t = -1, dmin_t = 0;
   const size_t base = (size_t)grp * sp.ppc * nx;
   const BR refS = bc.refS, refJz = bc.refJz;
   const BR hdt = bc.hdt;
@@ -478,6 +494,11 @@ __global__ void __launch_bounds__(256, 2) beam_kernel(BeamArrays<BR> b, DevParam
             continue;
           }
         }
+        {
+          const int cell = (int)floor(hk[u] + oxi[u]);  // xi cell relative to the home layer
+          cmax_t = max(cmax_t, g.kabs + cell);
+          dmin_t = min(dmin_t, cell);
+        }
         BR dS, dJz, JX, JY;
         beam_sources(ux[u], uy[u], uz_lead(uz[u]), dw[u], bc, dS, dJz, JX, JY);
         deposit_particle(g, src, p, ix, hx[u], hy[u], hk[u], ox[u], oy[u], oxi[u], dS, dJz, JX,
@@ -485,7 +506,17 @@ __global__ void __launch_bounds__(256, 2) beam_kernel(BeamArrays<BR> b, DevParam
       }
     }
   }
+  cmax_t = warp_max(cmax_t);
+  dmin_t = warp_min(dmin_t);
+  if ((threadIdx.x & 31) == 0) {
+    if (cmax_t > s_ext[0]) atomicMax(&s_ext[0], cmax_t);
+    if (dmin_t < 0) atomicMin(&s_ext[1], dmin_t);
+  }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    if (ext.cmax && s_ext[0] >= 0) atomicMax(ext.cmax + g.kabs, s_ext[0]);
+    if (ext.dmin && s_ext[1] < 0) atomicMin(ext.dmin, s_ext[1]);
+  }
   for (int e = threadIdx.x; e < 2 * 4 * nx; e += blockDim.x) {
     const int dk = e / (4 * nx), r = (e / nx) % 4, x = e % nx;
     const int k = g.kabs + dk;
@@ -495,6 +526,17 @@ __global__ void __launch_bounds__(256, 2) beam_kernel(BeamArrays<BR> b, DevParam
       red4(src + (((size_t)k * p.ny + wrap(g.iy - 1 + r, p.ny)) * nx + x) * 4, t0, t1, t2, t3);
   }
   if (my_lost && lost) atomicAdd(lost, (unsigned long long)my_lost);
+  __syncthreads();  // the tile and s_ext are reused by the block's next group
+}
+
+// Grid: one block per (xi cell, row) group of the species.
+template <typename BR, bool PUSH>
+__global__ void __launch_bounds__(256, 2) beam_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp,
+                                                   BeamConst<BR> bc, const BR* __restrict__ slab,
+                                                   BR* src, unsigned long long* lost, Extent ext) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  beam_group<BR, PUSH>(b, p, sp, bc, slab, src, lost, ext, blockIdx.x,
+                       reinterpret_cast<BR*>(smem));
 }
 
 template <typename BR>

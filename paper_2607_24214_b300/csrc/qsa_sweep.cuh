@@ -321,9 +321,13 @@ __device__ __forceinline__ W4<R> cic_dw(R hx, R hy, R ox, R oy) {
                 hx * oy + ox * hy + oxy};
 }
 
+// Every phase takes its work units (grid rows, or half-spectrum columns) u0, u0 + G, ... so
+// that one launch can spread the units of several sweeps over its blocks; a single sweep
+// passes (blockIdx.x, gridDim.x).  The per-block diagnostic partials are written by every
+// block that calls the phase, with or without units.
 template <typename R>
 __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, double psi0,
-                          bool first, bool last) {
+                          bool first, bool last, int u0, int G) {
   // reference state of the deposits: a particle at rest at its lattice home with psi = psi0
   // carries rho - J_z = -w and u_z/(1+psi) = c0 = -psi0 (2 + psi0) / (2 (1+psi0)^2); formed
   // in the working precision (psi0 is O(alpha), no cancellation)
@@ -352,7 +356,7 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
   R* __restrict__ puy = a.puy;
   R* __restrict__ pps = a.ppsi;
 
-  for (int crow = blockIdx.x; crow < ny; crow += gridDim.x) {
+  for (int crow = u0; crow < ny; crow += G) {
     for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) tile[e] = R(0);
     __syncthreads();
     const size_t base = (size_t)crow * per_chunk;
@@ -585,7 +589,8 @@ __device__ __forceinline__ void load_tw(C<R>* dst, const C<R>* src, int n) {
 // mode DEP_TRIAL: fields Jx^j, Jy^j, Jz^j, Jx^{j+1/2}, Jy^{j+1/2} of slice j = jj.
 // else: fields S, Jx^{jn-1/2}, Jy^{jn-1/2} of the new slice jn = jj.
 template <typename R>
-__device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, int jj) {
+__device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, int jj, int u0,
+                          int G) {
   const DevParams& p = a.p;
   const int nx = p.nx, ny = p.ny, nxh = p.nxh, nk = p.nk;
   const int nf = (mode == DEP_TRIAL) ? kNF : 3;
@@ -600,7 +605,7 @@ __device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, 
   R charge = R(0);
   load_tw(tw, a.twx, nx);
   const int k0 = (mode == DEP_TRIAL) ? jj : jj - 1;  // beam-source nodes k0, k0 + 1
-  for (int q = blockIdx.x; q < ny; q += gridDim.x) {
+  for (int q = u0; q < ny; q += G) {
     for (int x = threadIdx.x; x < nx; x += blockDim.x) {
       R v[kNF];
 #pragma unroll
@@ -691,7 +696,7 @@ __device__ __forceinline__ Kv<R> kvec(const R* __restrict__ ktab, int nxh, int n
 // deposits (needed for <J_z>, the source of the k = 0 mode).
 template <typename R>
 __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, bool last,
-                            double psi0) {
+                            double psi0, int u0, int G) {
   const DevParams& p = a.p;
   const int ny = p.ny, nxh = p.nxh;
   C<R>* A = buf;
@@ -705,7 +710,7 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
   __shared__ double red[32];
   R num = R(0), den = R(0);
   load_tw(tw, a.twy, ny);
-  for (int kx = blockIdx.x; kx < nxh; kx += gridDim.x) {
+  for (int kx = u0; kx < nxh; kx += G) {
     for (int ky = threadIdx.x; ky < ny; ky += blockDim.x) {
       C<R> v[kNF];
 #pragma unroll
@@ -778,14 +783,14 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
 
 // ------------------------------------------------------------------ column phase: psi
 template <typename R>
-__device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf, C<R>* tw) {
+__device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int u0, int G) {
   const DevParams& p = a.p;
   const int ny = p.ny, nxh = p.nxh;
   C<R>* A = buf;
   C<R>* B = buf + kNF * ny;
   const C<R>* __restrict__ rspec = a.rspec;
   load_tw(tw, a.twy, ny);
-  for (int kx = blockIdx.x; kx < nxh; kx += gridDim.x) {
+  for (int kx = u0; kx < nxh; kx += G) {
     for (int ky = threadIdx.x; ky < ny; ky += blockDim.x) {
       C<R> v[3];
 #pragma unroll
@@ -822,7 +827,7 @@ __device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf, C<R>* tw) {
 // iteration also the slab of slice j and the field energies.
 template <typename R>
 __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_mode, int j,
-                           bool last, double ez0j) {
+                           bool last, double ez0j, int u0, int G) {
   const DevParams& p = a.p;
   const int nx = p.nx, ny = p.ny, nxh = p.nxh;
   const int nout = psi_mode ? 3 : 4;
@@ -837,7 +842,7 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
   R en[6] = {0, 0, 0, 0, 0, 0};
   bool bad = false;
   load_tw(tw, a.twx, nx);
-  for (int q = blockIdx.x; q < ny; q += gridDim.x) {
+  for (int q = u0; q < ny; q += G) {
     for (int e = threadIdx.x; e < npair * nx; e += blockDim.x) {
       const int pr = e / nx, k = e - pr * nx;
       const int f0 = 2 * pr, f1 = 2 * pr + 1;
@@ -938,31 +943,32 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<R> a) {
   };
   double psi0 = 0.0, ez0h = 0.0;
 
-  dep_phase(a, tile, DEP_INIT, 0, 0.0, false, false);
+  const int u0 = blockIdx.x, G = gridDim.x;
+  dep_phase(a, tile, DEP_INIT, 0, 0.0, false, false, u0, G);
   if (!sync(-1, 0)) return;
-  row_phase(a, buf, tw, DEP_INIT, 0);
+  row_phase(a, buf, tw, DEP_INIT, 0, u0, G);
   if (!sync(-1, 1)) return;
-  col_phase_psi(a, buf, tw);
+  col_phase_psi(a, buf, tw, u0, G);
   if (!sync(-1, 2)) return;
-  irow_phase(a, buf, tw, true, 0, false, 0.0);
+  irow_phase(a, buf, tw, true, 0, false, 0.0, u0, G);
   if (!sync(-1, 3)) return;
 
   for (int j = 0; j < p.nk; ++j) {
     double ez0n = ez0h, ez0j = ez0h;
     for (int it = 0; it < p.n_pc; ++it) {
       const bool first = (it == 0), last = (it == p.n_pc - 1);
-      dep_phase(a, tile, DEP_TRIAL, j, psi0, first, last);
+      dep_phase(a, tile, DEP_TRIAL, j, psi0, first, last, u0, G);
       if (!sync(j, 4 * it + 0)) return;
-      row_phase(a, buf, tw, DEP_TRIAL, j);
+      row_phase(a, buf, tw, DEP_TRIAL, j, u0, G);
       if (!sync(j, 4 * it + 1)) return;
-      col_phase_b(a, buf, tw, j, last, psi0);
+      col_phase_b(a, buf, tw, j, last, psi0, u0, G);
       if (!sync(j, 4 * it + 2)) return;
       if (last) {
         const double jz = *((volatile double*)&a.diag[D_JZ * p.nk + j]);
         ez0n = ez0h - p.dxi * jz;
         ez0j = 0.5 * (ez0h + ez0n);
       }
-      irow_phase(a, buf, tw, false, j, last, ez0j);
+      irow_phase(a, buf, tw, false, j, last, ez0j, u0, G);
       if (!sync(j, 4 * it + 3)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -971,13 +977,13 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<R> a) {
     }
     if (j + 1 < p.nk) {
       const int pc = 4 * p.n_pc;
-      dep_phase(a, tile, DEP_COMMIT, j, psi0, false, false);
+      dep_phase(a, tile, DEP_COMMIT, j, psi0, false, false, u0, G);
       if (!sync(j, pc + 0)) return;
-      row_phase(a, buf, tw, DEP_COMMIT, j + 1);
+      row_phase(a, buf, tw, DEP_COMMIT, j + 1, u0, G);
       if (!sync(j, pc + 1)) return;
-      col_phase_psi(a, buf, tw);
+      col_phase_psi(a, buf, tw, u0, G);
       if (!sync(j, pc + 2)) return;
-      irow_phase(a, buf, tw, true, j + 1, false, 0.0);
+      irow_phase(a, buf, tw, true, j + 1, false, 0.0, u0, G);
       if (!sync(j, pc + 3)) return;
     }
     psi0 += p.dxi * ez0n;
@@ -995,18 +1001,19 @@ __global__ void __launch_bounds__(256) solve_kernel(SweepArgs<R> a, int which) {
   C<R>* buf = reinterpret_cast<C<R>*>(smem);
   C<R>* tw = reinterpret_cast<C<R>*>(smem + phase_smem_bytes<R>(p.nx, p.ny));
   unsigned epoch = 0;
+  const int u0 = blockIdx.x, G = gridDim.x;
   if (which == 0) {
-    row_phase(a, buf, tw, DEP_TRIAL, 0);
+    row_phase(a, buf, tw, DEP_TRIAL, 0, u0, G);
     if (!grid_sync(a.bar, epoch)) return;
-    col_phase_b(a, buf, tw, 0, false, 0.0);
+    col_phase_b(a, buf, tw, 0, false, 0.0, u0, G);
     if (!grid_sync(a.bar, epoch)) return;
-    irow_phase(a, buf, tw, false, 0, false, 0.0);
+    irow_phase(a, buf, tw, false, 0, false, 0.0, u0, G);
   } else {
-    row_phase(a, buf, tw, DEP_COMMIT, 0);
+    row_phase(a, buf, tw, DEP_COMMIT, 0, u0, G);
     if (!grid_sync(a.bar, epoch)) return;
-    col_phase_psi(a, buf, tw);
+    col_phase_psi(a, buf, tw, u0, G);
     if (!grid_sync(a.bar, epoch)) return;
-    irow_phase(a, buf, tw, true, 0, false, 0.0);
+    irow_phase(a, buf, tw, true, 0, false, 0.0, u0, G);
   }
 }
 

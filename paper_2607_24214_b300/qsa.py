@@ -31,7 +31,7 @@ SOURCES = ("Sb", "Jz", "Jx", "Jy")
 EXPORTS = ("qsa_init", "qsa_set_beam", "qsa_get_beam", "qsa_plasma_sweep", "qsa_beam_step",
            "qsa_diagnostics", "qsa_copy_field", "qsa_copy_source", "qsa_field_solve",
            "qsa_phase_times", "qsa_launch_count", "qsa_device_bytes", "qsa_last_error",
-           "qsa_destroy", "qsa_field_solve_static")
+           "qsa_destroy", "qsa_field_solve_static", "qsa_advance")
 
 
 class QsaError(RuntimeError):
@@ -57,7 +57,7 @@ class ParamsC(ct.Structure):
     _fields_ = [("nx", ct.c_int32), ("ny", ct.c_int32), ("nxi", ct.c_int32),
                 ("ppc_plasma_x", ct.c_int32), ("ppc_plasma_y", ct.c_int32),
                 ("n_species", ct.c_int32), ("n_modes", ct.c_int32), ("precision", ct.c_int32),
-                ("n_pc_iter", ct.c_int32), ("_reserved", ct.c_int32),
+                ("n_pc_iter", ct.c_int32), ("pipeline_depth", ct.c_int32),
                 ("Lx", ct.c_double), ("Ly", ct.c_double), ("Lxi", ct.c_double),
                 ("dt", ct.c_double), ("psi_floor", ct.c_double), ("seed", ct.c_uint64),
                 ("spin_limit", ct.c_int64), ("species", Species * 4), ("modes", Mode * 16)]
@@ -98,6 +98,8 @@ def load_library(path: str = LIB_PATH):
     for name in ("qsa_plasma_sweep", "qsa_beam_step"):
         getattr(lib, name).argtypes = [P]
         getattr(lib, name).restype = ct.c_int
+    lib.qsa_advance.argtypes = [P, ct.c_int32]
+    lib.qsa_advance.restype = ct.c_int
     lib.qsa_diagnostics.argtypes = [P, ct.POINTER(Diag)]
     lib.qsa_diagnostics.restype = ct.c_int
     lib.qsa_copy_field.argtypes = [P, ct.c_int, ct.c_int, ct.c_int, _DP]
@@ -131,6 +133,7 @@ def to_c_params(p: config.Params) -> ParamsC:
     c.n_modes = len(p.modes)
     c.precision = 0 if p.precision == "fp64" else 1
     c.n_pc_iter = p.n_pc_iter
+    c.pipeline_depth = p.pipeline_depth
     c.Lx, c.Ly, c.Lxi, c.dt = p.Lx, p.Ly, p.Lxi, p.dt
     c.psi_floor = p.psi_floor
     c.seed = p.seed
@@ -214,6 +217,10 @@ class QSA:
 
     def beam_step(self):
         return self._check(self.lib.qsa_beam_step(self.h))
+
+    def advance(self, n_steps: int):
+        """n_steps x (sweep, beam step); pipelined launches when p.pipeline_depth >= 2."""
+        return self._check(self.lib.qsa_advance(self.h, int(n_steps)))
 
     # -- data in / out
     def set_beam(self, si: int, b: dict):
