@@ -279,6 +279,8 @@ int setup(qsa_handle* h) {
     if (!(a.fg = (R*)A(g * kFG * sizeof(R))) ||
         !(a.part = (R*)A((size_t)dp.ny * kTileRows * dp.nx * kNF * sizeof(R))) ||
         !(a.ovf = (R*)A(g * kNF * sizeof(R))) ||
+        !(a.cflag = (int*)A((size_t)dp.ny * sizeof(int))) ||
+        !(a.odirty = (int*)A((size_t)dp.ny * sizeof(int))) ||
         !(a.rspec = (C<R>*)A(kNF * spec * sizeof(C<R>))) ||
         !(a.cspec = (C<R>*)A(4 * spec * sizeof(C<R>))) ||
         !(a.jprev = (C<R>*)A(2 * spec * sizeof(C<R>))) ||
@@ -298,6 +300,8 @@ int setup(qsa_handle* h) {
     a.bar = Barrier{bar, status, (long long)h->prm.spin_limit};
     CK(cudaMemsetAsync(a.slab, 0, (size_t)dp.nk * g * 8 * sizeof(R), h->stream));
     CK(cudaMemsetAsync(a.diag, 0, (size_t)D_COUNT * dp.nk * sizeof(double), h->stream));
+    CK(cudaMemsetAsync(a.cflag, 0, (size_t)dp.ny * sizeof(int), h->stream));
+    CK(cudaMemsetAsync(a.odirty, 0, (size_t)dp.ny * sizeof(int), h->stream));
   }
   s->grid = grid;
   s->smem = smem;
@@ -470,6 +474,7 @@ int sweep(qsa_handle* h) {
   const size_t spec = (size_t)dp.nxh * dp.ny;
   SweepArgs<R>& a = s->slots[0];
   CK(cudaMemsetAsync(a.ovf, 0, g * kNF * sizeof(R), h->stream));
+  CK(cudaMemsetAsync(a.odirty, 0, (size_t)dp.ny * sizeof(int), h->stream));
   CK(cudaMemsetAsync(a.bold, 0, 2 * spec * sizeof(C<R>), h->stream));
   CK(cudaMemsetAsync(a.fg, 0, g * kFG * sizeof(R), h->stream));
   CK(cudaMemsetAsync(a.bar.count, 0, sizeof(unsigned), h->stream));
@@ -513,6 +518,7 @@ int advance_pipelined(qsa_handle* h, int n) {
     for (int i = 0; i < m; ++i) {
       SweepArgs<R>& a = s->slots[i];
       CK(cudaMemsetAsync(a.ovf, 0, g * kNF * sizeof(R), h->stream));
+      CK(cudaMemsetAsync(a.odirty, 0, (size_t)dp.ny * sizeof(int), h->stream));
       CK(cudaMemsetAsync(a.bold, 0, 2 * spec * sizeof(C<R>), h->stream));
       CK(cudaMemsetAsync(a.fg, 0, g * kFG * sizeof(R), h->stream));
       diag_init_kernel<<<(nd + 255) / 256, 256, 0, h->stream>>>(a.diag, dp.nk);
@@ -704,6 +710,9 @@ int field_solve(qsa_handle* h, const double* const* in, double kappa2, double* o
   }
   CK(cudaMemcpyAsync(a.ovf, ov.data(), ov.size() * sizeof(R), cudaMemcpyHostToDevice,
                      h->stream));
+  // the inputs sit in the overflow grid: every overflow row is read, no outer tile row
+  CK(cudaMemsetAsync(a.odirty, 1, (size_t)dp.ny * sizeof(int), h->stream));
+  CK(cudaMemsetAsync(a.cflag, 0, (size_t)dp.ny * sizeof(int), h->stream));
   CK(cudaMemsetAsync(a.bar.count, 0, sizeof(unsigned), h->stream));
   int which = 0;
   void* args[] = {&a, &which};
@@ -729,6 +738,7 @@ int field_solve(qsa_handle* h, const double* const* in, double kappa2, double* o
   std::fill(ov.begin(), ov.end(), R(0));
   for (size_t i = 0; i < g; ++i) ov[i] = R(in[0][i]);
   CK(cudaMemcpyAsync(a.ovf, ov.data(), g * 3 * sizeof(R), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemsetAsync(a.odirty, 1, (size_t)dp.ny * sizeof(int), h->stream));
   CK(cudaMemsetAsync(a.part, 0, (size_t)dp.ny * kTileRows * dp.nx * kNF * sizeof(R), h->stream));
   CK(cudaMemsetAsync(a.bar.count, 0, sizeof(unsigned), h->stream));
   which = 1;

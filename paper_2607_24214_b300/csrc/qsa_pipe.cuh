@@ -36,6 +36,10 @@ namespace qsa {
 
 constexpr int kMaxPipe = 16;
 constexpr int kMaxSpecies = 4;
+// rows (half-spectrum columns) per unit of the FFT phases, and resident blocks per SM
+constexpr int kPipeRowBatch = 2;
+constexpr int kPipeColBatch = 1;
+constexpr int kPipeBlocksPerSM = 4;
 
 template <typename R>
 struct PipeTable {
@@ -60,8 +64,8 @@ __device__ __forceinline__ int unit0(int k, int U, int G) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) pipe_kernel(const PipeTable<R>* __restrict__ T, int r0,
-                                                   int nsteps, Barrier bar) {
+__global__ void __launch_bounds__(256, kPipeBlocksPerSM)
+    pipe_kernel(const PipeTable<R>* __restrict__ T, int r0, int nsteps, Barrier bar) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SweepArgs<R> sa[kMaxPipe];
   __shared__ BeamArrays<R> sb[kMaxSpecies];
@@ -102,8 +106,9 @@ __global__ void __launch_bounds__(256) pipe_kernel(const PipeTable<R>* __restric
   const int nspec = T->nspecies, max_push = T->max_push;
   R* tile = reinterpret_cast<R*>(smem);
   C<R>* buf = reinterpret_cast<C<R>*>(smem);
-  C<R>* tw = reinterpret_cast<C<R>*>(smem + phase_smem_bytes<R>(nx, ny));
-  (void)nx;
+  constexpr int nbr = kPipeRowBatch, nbc = kPipeColBatch;
+  const int ur = (ny + nbr - 1) / nbr, uc = (nxh + nbc - 1) / nbc;  // FFT units per step
+  C<R>* tw = reinterpret_cast<C<R>*>(smem + phase_smem_bytes<R>(nx, ny, nbr, nbc));
   unsigned epoch = 0;
   // every tick processes at least one slice or one layer, so this bound is never reached by
   // a correct schedule; it keeps a scheduling fault from spinning forever
@@ -160,12 +165,12 @@ __global__ void __launch_bounds__(256) pipe_kernel(const PipeTable<R>* __restric
         if (!grid_sync(bar, epoch)) return;
         for (int k = 0; k < nt; ++k) {
           const int s = act_t[k];
-          row_phase(sa[s], buf, tw, DEP_TRIAL, js[s], unit0(k, ny, G), G);
+          row_phase(sa[s], buf, tw, DEP_TRIAL, js[s], unit0(k, ur, G), G, nbr);
         }
         if (!grid_sync(bar, epoch)) return;
         for (int k = 0; k < nt; ++k) {
           const int s = act_t[k];
-          col_phase_b(sa[s], buf, tw, js[s], last, psi0[s], unit0(k, nxh, G), G);
+          col_phase_b(sa[s], buf, tw, js[s], last, psi0[s], unit0(k, uc, G), G, nbc);
         }
         if (!grid_sync(bar, epoch)) return;
         if (last) {
@@ -185,7 +190,7 @@ __global__ void __launch_bounds__(256) pipe_kernel(const PipeTable<R>* __restric
         }
         for (int k = 0; k < nt; ++k) {
           const int s = act_t[k];
-          irow_phase(sa[s], buf, tw, false, js[s], last, ez0j[s], unit0(k, ny, G), G);
+          irow_phase(sa[s], buf, tw, false, js[s], last, ez0j[s], unit0(k, ur, G), G, nbr);
         }
         if (!grid_sync(bar, epoch)) return;
       }
@@ -227,17 +232,17 @@ __global__ void __launch_bounds__(256) pipe_kernel(const PipeTable<R>* __restric
       for (int k = 0; k < nc; ++k) {
         const int s = act_c[k];
         row_phase(sa[s], buf, tw, js[s] < 0 ? DEP_INIT : DEP_COMMIT, js[s] + 1,
-                  unit0(k, ny, G), G);
+                  unit0(k, ur, G), G, nbr);
       }
       if (!grid_sync(bar, epoch)) return;
       for (int k = 0; k < nc; ++k) {
         const int s = act_c[k];
-        col_phase_psi(sa[s], buf, tw, unit0(k, nxh, G), G);
+        col_phase_psi(sa[s], buf, tw, unit0(k, uc, G), G, nbc);
       }
       if (!grid_sync(bar, epoch)) return;
       for (int k = 0; k < nc; ++k) {
         const int s = act_c[k];
-        irow_phase(sa[s], buf, tw, true, js[s] + 1, false, 0.0, unit0(k, ny, G), G);
+        irow_phase(sa[s], buf, tw, true, js[s] + 1, false, 0.0, unit0(k, ur, G), G, nbr);
       }
       if (!grid_sync(bar, epoch)) return;
     }
@@ -260,7 +265,8 @@ __global__ void __launch_bounds__(256) pipe_kernel(const PipeTable<R>* __restric
 
 template <typename R>
 __host__ __device__ inline size_t pipe_smem_bytes(int nx, int ny) {
-  const size_t a = sweep_smem_bytes<R>(nx, ny), b = beam_smem_bytes<R>(nx);
+  const size_t a = sweep_smem_bytes<R>(nx, ny, kPipeRowBatch, kPipeColBatch),
+               b = beam_smem_bytes<R>(nx);
   return a > b ? a : b;
 }
 

@@ -154,6 +154,8 @@ int solve_static(int nx, int ny, double Lx, double Ly, double kappa2, const R* S
   a.fg = cv.take<R>(g * kFG);
   a.part = cv.take<R>((size_t)ny * kTileRows * nx * kNF);
   a.ovf = cv.take<R>(g * kNF);
+  a.cflag = cv.take<int>((size_t)ny);
+  a.odirty = cv.take<int>((size_t)ny);
   a.rspec = cv.take<C<R>>(kNF * spec);
   a.cspec = cv.take<C<R>>(4 * spec);
   a.jprev = cv.take<C<R>>(2 * spec);
@@ -211,6 +213,9 @@ int solve_static(int nx, int ny, double Lx, double Ly, double kappa2, const R* S
   QSA_TRY(cudaMemsetAsync(a.jprev, 0, 2 * spec * sizeof(C<R>), st));
   QSA_TRY(cudaMemsetAsync(a.bold, 0, 2 * spec * sizeof(C<R>), st));
   QSA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+  // the inputs sit in the overflow grid: every overflow row is read, no outer tile row
+  QSA_TRY(cudaMemsetAsync(a.cflag, 0, (size_t)ny * sizeof(int), st));
+  QSA_TRY(cudaMemsetAsync(a.odirty, 1, (size_t)ny * sizeof(int), st));
   // B pass: the five trial fields J_x, J_y, J_z, J_x^{+1/2}, J_y^{+1/2}, field-major
   const R* ins[5] = {Jx, Jy, Jz, Dx, Dy};
   for (int f = 0; f < 5; ++f)
@@ -228,6 +233,7 @@ int solve_static(int nx, int ny, double Lx, double Ly, double kappa2, const R* S
   // psi pass: S in field 0 of three
   QSA_TRY(cudaMemsetAsync(a.ovf, 0, 3 * g * sizeof(R), st));
   QSA_TRY(cudaMemcpyAsync(a.ovf, S, g * sizeof(R), cudaMemcpyDeviceToDevice, st));
+  QSA_TRY(cudaMemsetAsync(a.odirty, 1, (size_t)ny * sizeof(int), st));
   QSA_TRY(cudaMemsetAsync(a.part, 0, (size_t)ny * kTileRows * nx * kNF * sizeof(R), st));
   QSA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned), st));
   which = 1;

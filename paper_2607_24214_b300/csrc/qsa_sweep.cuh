@@ -110,6 +110,8 @@ struct SweepArgs {
   R* fg;                                    // [ny][nx][8] real-space fields
   R* part;                                  // [ny chunks][nf][4][nx]
   R* ovf;                                   // [kNF][ny][nx]
+  int* cflag;                               // [ny chunks] outer tile rows used (bits 0, 1)
+  int* odirty;                              // [ny] overflow row holds deposits
   C<R>* rspec;                              // [kNF][nxh][ny]
   C<R>* cspec;                              // [4][ny][nxh]
   C<R>* jprev;                              // [2][nxh][ny]  J_perp^{j-1/2} spectra
@@ -194,12 +196,29 @@ __device__ __forceinline__ void gather8(const R* __restrict__ fg, const Cic<R>& 
 
 // Deposit v (already a density) at the four corners into the field-major tile [nf][4][nx],
 // or into the overflow grid [kNF][ny][nx] when the rows fall outside the tile.
+// Deposits outside the two home rows of the tile are rare (a particle that left its home
+// row); they are flagged so that the row phase reads the outer tile rows (cflag bit 0: tile
+// row 0, bit 1: tile row 3) and the overflow rows (odirty) only where something landed.
+struct DepFlags {
+  int* tile;    // shared flag word of the chunk
+  int* odirty;  // [ny] overflow rows
+};
+__device__ __forceinline__ void flag_rows(const DepFlags& fl, int ty) {
+  if (ty == 0) atomicOr(fl.tile, 1);
+  else if (ty == kTileRows - 2) atomicOr(fl.tile, 2);
+}
+__device__ __forceinline__ void flag_ovf(const DepFlags& fl, int y0, int y1) {
+  atomicOr(fl.odirty + y0, 1);
+  atomicOr(fl.odirty + y1, 1);
+}
+
 template <typename R>
-__device__ __forceinline__ void deposit(R* tile, R* ovf, const Cic<R>& c, int f, int nx, int ny,
-                                        R v) {
+__device__ __forceinline__ void deposit(R* tile, R* ovf, const DepFlags& fl, const Cic<R>& c,
+                                        int f, int nx, int ny, R v) {
   const R gx = R(1) - c.fx, gy = R(1) - c.fy;
   const R w00 = gx * gy * v, w01 = c.fx * gy * v, w10 = gx * c.fy * v, w11 = c.fx * c.fy * v;
   if (c.ty >= 0 && c.ty <= kTileRows - 2) {
+    if (c.ty != 1) flag_rows(fl, c.ty);
     R* r0 = tile + ((size_t)f * kTileRows + c.ty) * nx;
     R* r1 = r0 + nx;
     atomicAdd(r0 + c.x0, w00);
@@ -207,6 +226,7 @@ __device__ __forceinline__ void deposit(R* tile, R* ovf, const Cic<R>& c, int f,
     atomicAdd(r1 + c.x0, w10);
     atomicAdd(r1 + c.x1, w11);
   } else {
+    flag_ovf(fl, c.y0, c.y1);
     R* o = ovf + (size_t)f * ny * nx;
     atomicAdd(o + (size_t)c.y0 * nx + c.x0, w00);
     atomicAdd(o + (size_t)c.y0 * nx + c.x1, w01);
@@ -222,8 +242,9 @@ __device__ __forceinline__ void deposit(R* tile, R* ovf, const Cic<R>& c, int f,
 // particle is in its home cell the weight differences are formed from the offsets without
 // cancellation.
 template <typename R>
-__device__ __forceinline__ void deposit_ref(R* tile, R* ovf, int ix, int crow, R hx, R hy, R ox,
-                                            R oy, int f, int nx, int ny, R v_dev, R v_ref) {
+__device__ __forceinline__ void deposit_ref(R* tile, R* ovf, const DepFlags& fl, int ix, int crow,
+                                            R hx, R hy, R ox, R oy, int f, int nx, int ny,
+                                            R v_dev, R v_ref) {
   const R lx = hx + ox, ly = hy + oy;
   if (lx >= R(0) && lx < R(1) && ly >= R(0) && ly < R(1)) {
     const R ax = R(1) - hx, ay = R(1) - hy;
@@ -241,9 +262,9 @@ __device__ __forceinline__ void deposit_ref(R* tile, R* ovf, int ix, int crow, R
     atomicAdd(r1 + x1, v_dev * w11 + v_ref * d11);
   } else {
     const Cic<R> c = cic<R>(ix, crow, lx, ly, nx, ny, crow);
-    deposit(tile, ovf, c, f, nx, ny, v_dev + v_ref);
+    deposit(tile, ovf, fl, c, f, nx, ny, v_dev + v_ref);
     const Cic<R> h = cic<R>(ix, crow, hx, hy, nx, ny, crow);
-    deposit(tile, ovf, h, f, nx, ny, -v_ref);
+    deposit(tile, ovf, fl, h, f, nx, ny, -v_ref);
   }
 }
 
@@ -288,9 +309,11 @@ __device__ __forceinline__ W4<R> cic_w(const Cic<R>& c) {
 // Deposit N values v[k] into fields f0 + k at the four corners of c (shared weights w), in
 // the field-major tile or, outside it, in the overflow grid.
 template <typename R, int N>
-__device__ __forceinline__ void deposit_n(R* tile, R* ovf, const Cic<R>& c, const W4<R>& w,
-                                          int f0, int nx, int ny, const R (&v)[N]) {
+__device__ __forceinline__ void deposit_n(R* tile, R* ovf, const DepFlags& fl, const Cic<R>& c,
+                                          const W4<R>& w, int f0, int nx, int ny,
+                                          const R (&v)[N]) {
   if (c.ty >= 0 && c.ty <= kTileRows - 2) {
+    if (c.ty != 1) flag_rows(fl, c.ty);
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       R* r0 = tile + ((size_t)(f0 + k) * kTileRows + c.ty) * nx;
@@ -301,6 +324,7 @@ __device__ __forceinline__ void deposit_n(R* tile, R* ovf, const Cic<R>& c, cons
       atomicAdd(r1 + c.x1, w.w11 * v[k]);
     }
   } else {
+    flag_ovf(fl, c.y0, c.y1);
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       R* o = ovf + (size_t)(f0 + k) * ny * nx;
@@ -350,6 +374,8 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
   // per-thread diagnostics accumulate in R; the block reductions below finish in FP64
   R kap = R(0), inv = R(0), omin = R(1e30), nfloor = R(0);
   __shared__ double red[32];
+  __shared__ int s_flag;
+  const DepFlags fl{&s_flag, a.odirty};
   R* __restrict__ pox = a.pox;
   R* __restrict__ poy = a.poy;
   R* __restrict__ pux = a.pux;
@@ -358,6 +384,7 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
 
   for (int crow = u0; crow < ny; crow += G) {
     for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) tile[e] = R(0);
+    if (threadIdx.x == 0) s_flag = 0;
     __syncthreads();
     const size_t base = (size_t)crow * per_chunk;
     if (mode == DEP_INIT) {  // at home: rho - J_z equals its reference, nothing to add
@@ -542,15 +569,15 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
                   atomicAdd(t0 + 2 * fs + nx + x1, w.w11 * vdev[u] + d.w11 * vref);
                 } else {
                   const R v3[3] = {vx[u], vy[u], vdev[u] + vref};
-                  deposit_n(tile, a.ovf, c[u], w, 0, nx, ny, v3);
+                  deposit_n(tile, a.ovf, fl, c[u], w, 0, nx, ny, v3);
                   const Cic<R> hc = cic<R>(ix, crow, hx[u], hy[u], nx, ny, crow);
-                  deposit(tile, a.ovf, hc, 2, nx, ny, -vref);
+                  deposit(tile, a.ovf, fl, hc, 2, nx, ny, -vref);
                 }
-                deposit_n(tile, a.ovf, ch[u], cic_w(ch[u]), 3, nx, ny, jh);
+                deposit_n(tile, a.ovf, fl, ch[u], cic_w(ch[u]), 3, nx, ny, jh);
               } else {
-                deposit_ref(tile, a.ovf, ix, crow, hx[u], hy[u], nox[u], noy[u], 0, nx, ny, R(0),
-                            vref);
-                deposit_n(tile, a.ovf, ch[u], cic_w(ch[u]), 1, nx, ny, jh);
+                deposit_ref(tile, a.ovf, fl, ix, crow, hx[u], hy[u], nox[u], noy[u], 0, nx, ny,
+                            R(0), vref);
+                deposit_n(tile, a.ovf, fl, ch[u], cic_w(ch[u]), 1, nx, ny, jh);
               }
             }
           }
@@ -560,6 +587,7 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
     __syncthreads();
     R* dst = a.part + (size_t)crow * tile_elems;
     for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) dst[e] = tile[e];
+    if (threadIdx.x == 0) a.cflag[crow] = s_flag;
     __syncthreads();
   }
   if (mode == DEP_TRIAL && first) {
@@ -588,15 +616,18 @@ __device__ __forceinline__ void load_tw(C<R>* dst, const C<R>* src, int n) {
 // ------------------------------------------------------------------ row phase (forward)
 // mode DEP_TRIAL: fields Jx^j, Jy^j, Jz^j, Jx^{j+1/2}, Jy^{j+1/2} of slice j = jj.
 // else: fields S, Jx^{jn-1/2}, Jy^{jn-1/2} of the new slice jn = jj.
+// A unit of the FFT phases is nb consecutive rows (or half-spectrum columns): their
+// transforms run in one block_fft call (more butterflies per thread between the stage
+// barriers) and the transposed writes of neighbouring rows (columns) land next to each other.
 template <typename R>
 __device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, int jj, int u0,
-                          int G) {
+                          int G, int nb) {
   const DevParams& p = a.p;
   const int nx = p.nx, ny = p.ny, nxh = p.nxh, nk = p.nk;
   const int nf = (mode == DEP_TRIAL) ? kNF : 3;
   const int npair = (nf + 1) / 2;
   C<R>* A = buf;
-  C<R>* B = buf + 3 * nx;
+  C<R>* B = buf + 3 * nx * nb;
   const int tile_elems = kTileRows * nx * nf;
   const R* __restrict__ part = a.part;
   R* __restrict__ ovf = a.ovf;
@@ -605,18 +636,28 @@ __device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, 
   R charge = R(0);
   load_tw(tw, a.twx, nx);
   const int k0 = (mode == DEP_TRIAL) ? jj : jj - 1;  // beam-source nodes k0, k0 + 1
-  for (int q = u0; q < ny; q += G) {
+  for (int u = u0; u * nb < ny; u += G) {
+    const int qb = u * nb, nr = min(nb, ny - qb);
+    for (int r = 0; r < nr; ++r) {
+    const int q = qb + r;
+    // grid row q collects tile row t of chunk q + 1 - t; rows 1, 2 always, rows 0, 3 and the
+    // overflow row only where a deposit landed
+    const bool use0 = a.cflag[wrap(q + 1, ny)] & 1, use3 = a.cflag[wrap(q - 2, ny)] & 2;
+    const bool od = a.odirty[q] != 0;
+    const R* p0 = part + (size_t)wrap(q + 1, ny) * tile_elems;
+    const R* p1 = part + (size_t)q * tile_elems + nx;
+    const R* p2 = part + (size_t)wrap(q - 1, ny) * tile_elems + 2 * nx;
+    const R* p3 = part + (size_t)wrap(q - 2, ny) * tile_elems + 3 * nx;
     for (int x = threadIdx.x; x < nx; x += blockDim.x) {
       R v[kNF];
 #pragma unroll
       for (int f = 0; f < kNF; ++f) {
         if (f < nf) {
-          R s = ovf[((size_t)f * ny + q) * nx + x];
-#pragma unroll
-          for (int t = 0; t < kTileRows; ++t) {
-            const int c = wrap(q + 1 - t, ny);
-            s += part[(size_t)c * tile_elems + ((size_t)f * kTileRows + t) * nx + x];
-          }
+          const size_t fo = (size_t)f * kTileRows * nx + x;
+          R s = p1[fo] + p2[fo];
+          if (use0) s += p0[fo];
+          if (use3) s += p3[fo];
+          if (od) s += ovf[((size_t)f * ny + q) * nx + x];
           v[f] = s;
         } else {
           v[f] = R(0);
@@ -636,7 +677,8 @@ __device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, 
           for (int k = 0; k < 4; ++k) s1[k] = e[k];
         }
       }
-      for (int f = 0; f < nf; ++f) ovf[((size_t)f * ny + q) * nx + x] = R(0);
+      if (od)
+        for (int f = 0; f < nf; ++f) ovf[((size_t)f * ny + q) * nx + x] = R(0);
       if (mode == DEP_TRIAL) {
         v[0] += s0[2];
         v[1] += s0[3];
@@ -651,15 +693,21 @@ __device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, 
       }
 #pragma unroll
       for (int pr = 0; pr < 3; ++pr)
-        if (pr < npair) A[pr * nx + x] = C<R>{v[2 * pr], (2 * pr + 1 < kNF) ? v[2 * pr + 1] : R(0)};
+        if (pr < npair)
+          A[(r * npair + pr) * nx + x] =
+              C<R>{v[2 * pr], (2 * pr + 1 < kNF) ? v[2 * pr + 1] : R(0)};
+    }
     }
     __syncthreads();
-    C<R>* Z = block_fft(A, B, npair, p.px, tw, -1);
+    if (threadIdx.x == 0)
+      for (int r = 0; r < nr; ++r) a.odirty[qb + r] = 0;  // consumed (read before the barrier)
+    C<R>* Z = block_fft(A, B, nr * npair, p.px, tw, -1);
     // unpack two real transforms: A_k = (Z_k + conj Z_{-k})/2, B_k = -i (Z_k - conj Z_{-k})/2
-    for (int e = threadIdx.x; e < npair * nxh; e += blockDim.x) {
-      const int pr = e / nxh, k = e - pr * nxh;
-      const C<R> zk = Z[pr * nx + k];
-      const C<R> zm = cconj(Z[pr * nx + (k == 0 ? 0 : nx - k)]);
+    for (int e = threadIdx.x; e < npair * nxh * nr; e += blockDim.x) {
+      const int t = e / nr, r = e - t * nr, pr = t / nxh, k = t - pr * nxh, q = qb + r;
+      const C<R>* zr = Z + (r * npair + pr) * nx;
+      const C<R> zk = zr[k];
+      const C<R> zm = cconj(zr[k == 0 ? 0 : nx - k]);
       const C<R> fa = C<R>{R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y + zm.y)};
       const C<R> fb = C<R>{R(0.5) * (zk.y - zm.y), R(-0.5) * (zk.x - zm.x)};
       a.rspec[((size_t)(2 * pr) * nxh + k) * ny + q] = fa;
@@ -696,11 +744,11 @@ __device__ __forceinline__ Kv<R> kvec(const R* __restrict__ ktab, int nxh, int n
 // deposits (needed for <J_z>, the source of the k = 0 mode).
 template <typename R>
 __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, bool last,
-                            double psi0, int u0, int G) {
+                            double psi0, int u0, int G, int nb) {
   const DevParams& p = a.p;
   const int ny = p.ny, nxh = p.nxh;
   C<R>* A = buf;
-  C<R>* B = buf + kNF * ny;
+  C<R>* B = buf + kNF * ny * nb;
   __shared__ R s_kap;
   if (threadIdx.x == 0) s_kap = R(a.diag[D_KAPPA * p.nk + j]) * a.k.inv_npc;
   const R rdxi = a.k.rdxi;
@@ -710,25 +758,30 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
   __shared__ double red[32];
   R num = R(0), den = R(0);
   load_tw(tw, a.twy, ny);
-  for (int kx = u0; kx < nxh; kx += G) {
-    for (int ky = threadIdx.x; ky < ny; ky += blockDim.x) {
+  for (int u = u0; u * nb < nxh; u += G) {
+    const int kb = u * nb, nc = min(nb, nxh - kb);
+    for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
+      const int c = e / ny, ky = e - c * ny, kx = kb + c;
       C<R> v[kNF];
 #pragma unroll
       for (int f = 0; f < kNF; ++f) v[f] = rspec[((size_t)f * nxh + kx) * ny + ky];
 #pragma unroll
-      for (int f = 0; f < kNF; ++f) A[f * ny + ky] = v[f];
+      for (int f = 0; f < kNF; ++f) A[(c * kNF + f) * ny + ky] = v[f];
     }
     __syncthreads();
     const R kap = s_kap;
-    C<R>* Z = block_fft(A, B, kNF, p.py, tw, -1);
+    C<R>* Z = block_fft(A, B, nc * kNF, p.py, tw, -1);
     C<R>* O = (Z == A) ? B : A;
-    const R pw = (kx == 0 || ((p.nx % 2 == 0) && 2 * kx == p.nx)) ? R(1) : R(2);
-    for (int ky = threadIdx.x; ky < ny; ky += blockDim.x) {
+    for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
+      const int c = e / ny, ky = e - c * ny, kx = kb + c;
+      const R pw = (kx == 0 || ((p.nx % 2 == 0) && 2 * kx == p.nx)) ? R(1) : R(2);
+      const C<R>* Zc = Z + c * kNF * ny;
+      C<R>* Oc = O + c * 4 * ny;
       const size_t ix0 = (size_t)kx * ny + ky, ix1 = ((size_t)nxh + kx) * ny + ky;
       const C<R> Jxp = jprev[ix0], Jyp = jprev[ix1];
       const C<R> Bxo = bold[ix0], Byo = bold[ix1];
-      const C<R> Jx = Z[ky], Jy = Z[ny + ky], Jz = Z[2 * ny + ky];
-      const C<R> Jxh = Z[3 * ny + ky], Jyh = Z[4 * ny + ky];
+      const C<R> Jx = Zc[ky], Jy = Zc[ny + ky], Jz = Zc[2 * ny + ky];
+      const C<R> Jxh = Zc[3 * ny + ky], Jyh = Zc[4 * ny + ky];
       if (kx == 0 && ky == 0) {
         // <J_z> for the k = 0 mode: the grid mean plus the uniform parts left out of the grid
         // deposits (plasma reference state and beam reference density)
@@ -760,16 +813,16 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
       }
       bold[ix0] = obx;
       bold[ix1] = oby;
-      O[ky] = obx;
-      O[ny + ky] = oby;
-      O[2 * ny + ky] = obz;
-      O[3 * ny + ky] = oez;
+      Oc[ky] = obx;
+      Oc[ny + ky] = oby;
+      Oc[2 * ny + ky] = obz;
+      Oc[3 * ny + ky] = oez;
     }
     __syncthreads();
-    C<R>* W = block_fft(O, Z, 4, p.py, tw, +1);
-    for (int e = threadIdx.x; e < 4 * ny; e += blockDim.x) {
-      const int f = e / ny, ky = e - f * ny;
-      a.cspec[((size_t)f * ny + ky) * nxh + kx] = W[e];
+    C<R>* W = block_fft(O, Z, nc * 4, p.py, tw, +1);
+    for (int e = threadIdx.x; e < 4 * ny * nc; e += blockDim.x) {
+      const int t = e / nc, c = e - t * nc, f = t / ny, ky = t - f * ny;
+      a.cspec[((size_t)f * ny + ky) * nxh + kb + c] = W[(c * 4 + f) * ny + ky];
     }
     __syncthreads();
   }
@@ -783,40 +836,46 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
 
 // ------------------------------------------------------------------ column phase: psi
 template <typename R>
-__device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int u0, int G) {
+__device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int u0, int G,
+                              int nb) {
   const DevParams& p = a.p;
   const int ny = p.ny, nxh = p.nxh;
   C<R>* A = buf;
-  C<R>* B = buf + kNF * ny;
+  C<R>* B = buf + kNF * ny * nb;
   const C<R>* __restrict__ rspec = a.rspec;
   load_tw(tw, a.twy, ny);
-  for (int kx = u0; kx < nxh; kx += G) {
-    for (int ky = threadIdx.x; ky < ny; ky += blockDim.x) {
+  for (int u = u0; u * nb < nxh; u += G) {
+    const int kb = u * nb, nc = min(nb, nxh - kb);
+    for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
+      const int c = e / ny, ky = e - c * ny, kx = kb + c;
       C<R> v[3];
 #pragma unroll
       for (int f = 0; f < 3; ++f) v[f] = rspec[((size_t)f * nxh + kx) * ny + ky];
 #pragma unroll
-      for (int f = 0; f < 3; ++f) A[f * ny + ky] = v[f];
+      for (int f = 0; f < 3; ++f) A[(c * 3 + f) * ny + ky] = v[f];
     }
     __syncthreads();
-    C<R>* Z = block_fft(A, B, 3, p.py, tw, -1);
+    C<R>* Z = block_fft(A, B, nc * 3, p.py, tw, -1);
     C<R>* O = (Z == A) ? B : A;
-    for (int ky = threadIdx.x; ky < ny; ky += blockDim.x) {
+    for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
+      const int c = e / ny, ky = e - c * ny, kx = kb + c;
+      const C<R>* Zc = Z + c * 3 * ny;
+      C<R>* Oc = O + c * 3 * ny;
       const size_t ix0 = (size_t)kx * ny + ky, ix1 = ((size_t)nxh + kx) * ny + ky;
-      a.jprev[ix0] = Z[ny + ky];
-      a.jprev[ix1] = Z[2 * ny + ky];
+      a.jprev[ix0] = Zc[ny + ky];
+      a.jprev[ix1] = Zc[2 * ny + ky];
       const Kv<R> k = kvec(a.ktab, nxh, ny, kx, ky);
       C<R> ps{0, 0};
-      if (k.k2 > R(0)) ps = cscale(Z[ky], R(1) / k.k2);
-      O[ky] = ps;
-      O[ny + ky] = cmuli(cscale(ps, k.kxd));
-      O[2 * ny + ky] = cmuli(cscale(ps, k.kyd));
+      if (k.k2 > R(0)) ps = cscale(Zc[ky], R(1) / k.k2);
+      Oc[ky] = ps;
+      Oc[ny + ky] = cmuli(cscale(ps, k.kxd));
+      Oc[2 * ny + ky] = cmuli(cscale(ps, k.kyd));
     }
     __syncthreads();
-    C<R>* W = block_fft(O, Z, 3, p.py, tw, +1);
-    for (int e = threadIdx.x; e < 3 * ny; e += blockDim.x) {
-      const int f = e / ny, ky = e - f * ny;
-      a.cspec[((size_t)f * ny + ky) * nxh + kx] = W[e];
+    C<R>* W = block_fft(O, Z, nc * 3, p.py, tw, +1);
+    for (int e = threadIdx.x; e < 3 * ny * nc; e += blockDim.x) {
+      const int t = e / nc, c = e - t * nc, f = t / ny, ky = t - f * ny;
+      a.cspec[((size_t)f * ny + ky) * nxh + kb + c] = W[(c * 3 + f) * ny + ky];
     }
     __syncthreads();
   }
@@ -827,13 +886,13 @@ __device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int u0
 // iteration also the slab of slice j and the field energies.
 template <typename R>
 __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_mode, int j,
-                           bool last, double ez0j, int u0, int G) {
+                           bool last, double ez0j, int u0, int G, int nb) {
   const DevParams& p = a.p;
   const int nx = p.nx, ny = p.ny, nxh = p.nxh;
   const int nout = psi_mode ? 3 : 4;
   const int npair = 2;
   C<R>* A = buf;
-  C<R>* B = buf + 3 * nx;
+  C<R>* B = buf + 3 * nx * nb;
   const R scale = a.k.scale;
   const R ez0r = R(ez0j);
   const C<R>* __restrict__ cspec = a.cspec;
@@ -842,9 +901,10 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
   R en[6] = {0, 0, 0, 0, 0, 0};
   bool bad = false;
   load_tw(tw, a.twx, nx);
-  for (int q = u0; q < ny; q += G) {
-    for (int e = threadIdx.x; e < npair * nx; e += blockDim.x) {
-      const int pr = e / nx, k = e - pr * nx;
+  for (int u = u0; u * nb < ny; u += G) {
+    const int qb = u * nb, nr = min(nb, ny - qb);
+    for (int e = threadIdx.x; e < nr * npair * nx; e += blockDim.x) {
+      const int rp = e / nx, k = e - rp * nx, r = rp / npair, pr = rp - r * npair, q = qb + r;
       const int f0 = 2 * pr, f1 = 2 * pr + 1;
       // full spectrum of z = a + i b from the half spectra of the real outputs a, b
       const int kk = (k < nxh) ? k : nx - k;
@@ -859,16 +919,18 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
         fa = cconj(fa);
         fb = cconj(fb);
       }
-      A[pr * nx + k] = cadd(fa, cmuli(fb));
+      A[rp * nx + k] = cadd(fa, cmuli(fb));
     }
     __syncthreads();
-    C<R>* Z = block_fft(A, B, npair, p.px, tw, +1);
-    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+    C<R>* Z = block_fft(A, B, nr * npair, p.px, tw, +1);
+    for (int e = threadIdx.x; e < nr * nx; e += blockDim.x) {
+      const int r = e / nx, x = e - r * nx, q = qb + r;
+      const C<R>* Zr = Z + r * npair * nx;
       R v[4];
-      v[0] = Z[x].x * scale;
-      v[1] = Z[x].y * scale;
-      v[2] = Z[nx + x].x * scale;
-      v[3] = Z[nx + x].y * scale;
+      v[0] = Zr[x].x * scale;
+      v[1] = Zr[x].y * scale;
+      v[2] = Zr[nx + x].x * scale;
+      v[3] = Zr[nx + x].y * scale;
       const size_t g = (size_t)q * nx + x;
       R* node = fg + g * kFG;
       if (psi_mode) {
@@ -911,22 +973,22 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
 // Shared-memory layout of the persistent kernels: the phase buffer (deposit tile or FFT
 // buffers) followed by a twiddle table.
 template <typename R>
-__host__ __device__ inline size_t phase_smem_bytes(int nx, int ny) {
+__host__ __device__ inline size_t phase_smem_bytes(int nx, int ny, int nbr = 1, int nbc = 1) {
   size_t tile = (size_t)kTileRows * nx * kNF * sizeof(R);
-  size_t row = (size_t)2 * 3 * nx * sizeof(C<R>);
-  size_t col = (size_t)2 * kNF * ny * sizeof(C<R>);
+  size_t row = (size_t)2 * 3 * nx * nbr * sizeof(C<R>);
+  size_t col = (size_t)2 * kNF * ny * nbc * sizeof(C<R>);
   size_t m = tile > row ? tile : row;
   m = m > col ? m : col;
   return (m + 15) & ~size_t(15);
 }
 template <typename R>
-__host__ __device__ inline size_t sweep_smem_bytes(int nx, int ny) {
-  return phase_smem_bytes<R>(nx, ny) + (size_t)(nx > ny ? nx : ny) * sizeof(C<R>);
+__host__ __device__ inline size_t sweep_smem_bytes(int nx, int ny, int nbr = 1, int nbc = 1) {
+  return phase_smem_bytes<R>(nx, ny, nbr, nbc) + (size_t)(nx > ny ? nx : ny) * sizeof(C<R>);
 }
 
 // ------------------------------------------------------------------ the kernel
 template <typename R>
-__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<R> a) {
+__global__ void __launch_bounds__(256, 2) sweep_kernel(SweepArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const DevParams& p = a.p;
   R* tile = reinterpret_cast<R*>(smem);
@@ -946,11 +1008,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<R> a) {
   const int u0 = blockIdx.x, G = gridDim.x;
   dep_phase(a, tile, DEP_INIT, 0, 0.0, false, false, u0, G);
   if (!sync(-1, 0)) return;
-  row_phase(a, buf, tw, DEP_INIT, 0, u0, G);
+  row_phase(a, buf, tw, DEP_INIT, 0, u0, G, 1);
   if (!sync(-1, 1)) return;
-  col_phase_psi(a, buf, tw, u0, G);
+  col_phase_psi(a, buf, tw, u0, G, 1);
   if (!sync(-1, 2)) return;
-  irow_phase(a, buf, tw, true, 0, false, 0.0, u0, G);
+  irow_phase(a, buf, tw, true, 0, false, 0.0, u0, G, 1);
   if (!sync(-1, 3)) return;
 
   for (int j = 0; j < p.nk; ++j) {
@@ -959,16 +1021,16 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<R> a) {
       const bool first = (it == 0), last = (it == p.n_pc - 1);
       dep_phase(a, tile, DEP_TRIAL, j, psi0, first, last, u0, G);
       if (!sync(j, 4 * it + 0)) return;
-      row_phase(a, buf, tw, DEP_TRIAL, j, u0, G);
+      row_phase(a, buf, tw, DEP_TRIAL, j, u0, G, 1);
       if (!sync(j, 4 * it + 1)) return;
-      col_phase_b(a, buf, tw, j, last, psi0, u0, G);
+      col_phase_b(a, buf, tw, j, last, psi0, u0, G, 1);
       if (!sync(j, 4 * it + 2)) return;
       if (last) {
         const double jz = *((volatile double*)&a.diag[D_JZ * p.nk + j]);
         ez0n = ez0h - p.dxi * jz;
         ez0j = 0.5 * (ez0h + ez0n);
       }
-      irow_phase(a, buf, tw, false, j, last, ez0j, u0, G);
+      irow_phase(a, buf, tw, false, j, last, ez0j, u0, G, 1);
       if (!sync(j, 4 * it + 3)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -979,11 +1041,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<R> a) {
       const int pc = 4 * p.n_pc;
       dep_phase(a, tile, DEP_COMMIT, j, psi0, false, false, u0, G);
       if (!sync(j, pc + 0)) return;
-      row_phase(a, buf, tw, DEP_COMMIT, j + 1, u0, G);
+      row_phase(a, buf, tw, DEP_COMMIT, j + 1, u0, G, 1);
       if (!sync(j, pc + 1)) return;
-      col_phase_psi(a, buf, tw, u0, G);
+      col_phase_psi(a, buf, tw, u0, G, 1);
       if (!sync(j, pc + 2)) return;
-      irow_phase(a, buf, tw, true, j + 1, false, 0.0, u0, G);
+      irow_phase(a, buf, tw, true, j + 1, false, 0.0, u0, G, 1);
       if (!sync(j, pc + 3)) return;
     }
     psi0 += p.dxi * ez0n;
@@ -995,7 +1057,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<R> a) {
 // from the five trial fields placed in the overflow grid; which = 1 solves psi and its
 // gradient from S placed in the overflow grid (field 0 of three).
 template <typename R>
-__global__ void __launch_bounds__(256) solve_kernel(SweepArgs<R> a, int which) {
+__global__ void __launch_bounds__(256, 2) solve_kernel(SweepArgs<R> a, int which) {
   extern __shared__ __align__(16) unsigned char smem[];
   const DevParams& p = a.p;
   C<R>* buf = reinterpret_cast<C<R>*>(smem);
@@ -1003,17 +1065,17 @@ __global__ void __launch_bounds__(256) solve_kernel(SweepArgs<R> a, int which) {
   unsigned epoch = 0;
   const int u0 = blockIdx.x, G = gridDim.x;
   if (which == 0) {
-    row_phase(a, buf, tw, DEP_TRIAL, 0, u0, G);
+    row_phase(a, buf, tw, DEP_TRIAL, 0, u0, G, 1);
     if (!grid_sync(a.bar, epoch)) return;
-    col_phase_b(a, buf, tw, 0, false, 0.0, u0, G);
+    col_phase_b(a, buf, tw, 0, false, 0.0, u0, G, 1);
     if (!grid_sync(a.bar, epoch)) return;
-    irow_phase(a, buf, tw, false, 0, false, 0.0, u0, G);
+    irow_phase(a, buf, tw, false, 0, false, 0.0, u0, G, 1);
   } else {
-    row_phase(a, buf, tw, DEP_COMMIT, 0, u0, G);
+    row_phase(a, buf, tw, DEP_COMMIT, 0, u0, G, 1);
     if (!grid_sync(a.bar, epoch)) return;
-    col_phase_psi(a, buf, tw, u0, G);
+    col_phase_psi(a, buf, tw, u0, G, 1);
     if (!grid_sync(a.bar, epoch)) return;
-    irow_phase(a, buf, tw, true, 0, false, 0.0, u0, G);
+    irow_phase(a, buf, tw, true, 0, false, 0.0, u0, G, 1);
   }
 }
 
