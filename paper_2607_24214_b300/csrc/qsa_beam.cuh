@@ -384,6 +384,49 @@ __device__ __forceinline__ void boris(float& ux, float& uy, float2& uz, const fl
   uz = make_float2(hi, lo - (hi - sum));
 }
 
+template <typename BR>
+__device__ __forceinline__ bool in_cell(BR lx, BR ly, BR lk) {
+  return lx >= BR(0) && lx < BR(1) && ly >= BR(0) && ly < BR(1) && lk >= BR(0) && lk < BR(1);
+}
+
+// Trilinear gather for the two particles of a thread, both inside their home cell (layer k,
+// row iy, column ix; x1 the next column): the eight corner nodes are loaded once.
+template <typename BR>
+__device__ __forceinline__ void gather_cell(const BR* __restrict__ slab, const DevParams& p,
+                                            int k, int iy, int ix, int x1, const BR hx[2],
+                                            const BR hy[2], const BR hk[2], const BR ox[2],
+                                            const BR oy[2], const BR oxi[2], BR F[2][6]) {
+  const int y1 = (iy + 1 == p.ny) ? 0 : iy + 1;
+  BR lx[2], ly[2], lk[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    lx[u] = hx[u] + ox[u];
+    ly[u] = hy[u] + oy[u];
+    lk[u] = hk[u] + oxi[u];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) F[u][f] = BR(0);
+  }
+#pragma unroll
+  for (int ck = 0; ck < 2; ++ck) {
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy) {
+      const BR* row = slab + ((size_t)(k + ck) * p.ny + (cy ? y1 : iy)) * p.nx * 8;
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) {
+        BR v[6];
+        ldslab(row + (size_t)(cx ? x1 : ix) * 8, v);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const BR wt = (ck ? lk[u] : BR(1) - lk[u]) * (cy ? ly[u] : BR(1) - ly[u]) *
+                        (cx ? lx[u] : BR(1) - lx[u]);
+#pragma unroll
+          for (int f = 0; f < 6; ++f) F[u][f] += wt * v[f];
+        }
+      }
+    }
+  }
+}
+
 // Where the live particles of a group sit after its push (or now, without a push): the
 // largest xi cell, max-reduced per home layer into cmax[layer] (a later push of the layer
 // gathers slab nodes up to that cell + 1), and the smallest cell minus the home layer,
@@ -418,6 +461,8 @@ __device__ void beam_group(const BeamArrays<BR>& b, const DevParams& p, const Sp
   }
   __syncthreads();
   int cmax_t = -1, dmin_t = 0;
+  // the aggregated deposit needs whole warps over consecutive columns
+  const bool lane_agg = (nx % 32 == 0) && (blockDim.x % 32 == 0);
   const size_t base = (size_t)grp * sp.ppc * nx;
   const BR refS = bc.refS, refJz = bc.refJz;
   const BR hdt = bc.hdt;
@@ -453,22 +498,39 @@ __device__ void beam_group(const BeamArrays<BR>& b, const DevParams& p, const Sp
         uy[u] = b.uy[si[u]];
         uz[u] = b.uz[si[u]];
       }
+      const int x1 = (ix + 1 == nx) ? 0 : ix + 1;
+      // pre-push positions in cells from the home cell's lower corner
+      bool pre_home = true;
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (ok[u]) pre_home = pre_home && in_cell(hx[u] + ox[u], hy[u] + oy[u], hk[u] + oxi[u]);
       BR F[2][6];
       if (PUSH) {
+        if (pre_home) {
+          // both particles in the home cell: one gather of the cell's eight slab nodes
+          gather_cell(slab, p, g.kabs, g.iy, ix, x1, hx, hy, hk, ox, oy, oxi, F);
+        } else {
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const BR lx = hx[u] + ox[u], ly = hy[u] + oy[u], lk = hk[u] + oxi[u];
-          const BR fx = floor(lx), fy = floor(ly), fk = floor(lk);
-          gather_slab(slab, p, g.kabs + (int)fk, g.iy + (int)fy, ix + (int)fx, lk - fk, ly - fy,
-                      lx - fx, F[u]);
+          for (int u = 0; u < 2; ++u) {
+            const BR lx = hx[u] + ox[u], ly = hy[u] + oy[u], lk = hk[u] + oxi[u];
+            const BR fx = floor(lx), fy = floor(ly), fk = floor(lk);
+            gather_slab(slab, p, g.kabs + (int)fk, g.iy + (int)fy, ix + (int)fx, lk - fk,
+                        ly - fy, lx - fx, F[u]);
+          }
         }
       }
+      // push and loss; the deposit of each particle: values (dS, dJz, J_x, J_y) at offsets
+      // (ox, oy, oxi) from home (a lost particle removes its reference: offsets 0)
+      BR dv[2][4], dox[2], doy[2], doxi[2];
+      bool post_home = true;
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
+        dv[u][0] = dv[u][1] = dv[u][2] = dv[u][3] = BR(0);
+        dox[u] = doy[u] = doxi[u] = BR(0);
         if (!ok[u]) continue;
         if (dw[u] == BR(-1)) {  // lost: only its reference, at home, is removed
-          deposit_particle(g, src, p, ix, hx[u], hy[u], hk[u], BR(0), BR(0), BR(0), -refS,
-                           -refJz, BR(0), BR(0), refS, refJz);
+          dv[u][0] = -refS;
+          dv[u][1] = -refJz;
           continue;
         }
         if (PUSH) {
@@ -489,8 +551,8 @@ __device__ void beam_group(const BeamArrays<BR>& b, const DevParams& p, const Sp
           if (hk[u] + oxi[u] >= BR(kleft)) {
             b.dw[s] = BR(-1);
             ++my_lost;
-            deposit_particle(g, src, p, ix, hx[u], hy[u], hk[u], BR(0), BR(0), BR(0), -refS,
-                             -refJz, BR(0), BR(0), refS, refJz);
+            dv[u][0] = -refS;
+            dv[u][1] = -refJz;
             continue;
           }
         }
@@ -499,10 +561,58 @@ __device__ void beam_group(const BeamArrays<BR>& b, const DevParams& p, const Sp
           cmax_t = max(cmax_t, g.kabs + cell);
           dmin_t = min(dmin_t, cell);
         }
-        BR dS, dJz, JX, JY;
-        beam_sources(ux[u], uy[u], uz_lead(uz[u]), dw[u], bc, dS, dJz, JX, JY);
-        deposit_particle(g, src, p, ix, hx[u], hy[u], hk[u], ox[u], oy[u], oxi[u], dS, dJz, JX,
-                         JY, refS, refJz);
+        beam_sources(ux[u], uy[u], uz_lead(uz[u]), dw[u], bc, dv[u][0], dv[u][1], dv[u][2],
+                     dv[u][3]);
+        dox[u] = ox[u];
+        doy[u] = oy[u];
+        doxi[u] = oxi[u];
+        post_home = post_home && in_cell(hx[u] + ox[u], hy[u] + oy[u], hk[u] + oxi[u]);
+      }
+      if (lane_agg && __all_sync(0xffffffffu, post_home)) {
+        // every particle of the warp's two sub-lattice positions is in its home cell: the two
+        // particles of a thread share their eight corners, and the right corners of lane l
+        // are the left corners of lane l + 1
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int ck = 0; ck < 2; ++ck) {
+#pragma unroll
+          for (int cy = 0; cy < 2; ++cy) {
+            BR acc[2][4];
+#pragma unroll
+            for (int cx = 0; cx < 2; ++cx)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) acc[cx][q] = BR(0);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const BR a3 = ck ? hk[u] : BR(1) - hk[u], d3 = ck ? doxi[u] : -doxi[u];
+              const BR a2 = cy ? hy[u] : BR(1) - hy[u], d2 = cy ? doy[u] : -doy[u];
+#pragma unroll
+              for (int cx = 0; cx < 2; ++cx) {
+                const BR a1 = cx ? hx[u] : BR(1) - hx[u], d1 = cx ? dox[u] : -dox[u];
+                const BR w = (a1 + d1) * (a2 + d2) * (a3 + d3);
+                const BR dW = d1 * a2 * a3 + a1 * d2 * a3 + a1 * a2 * d3 + d1 * d2 * a3 +
+                              d1 * a2 * d3 + a1 * d2 * d3 + d1 * d2 * d3;
+                acc[cx][0] += dv[u][0] * w + refS * dW;
+                acc[cx][1] += dv[u][1] * w + refJz * dW;
+                acc[cx][2] += dv[u][2] * w;
+                acc[cx][3] += dv[u][3] * w;
+              }
+            }
+            BR* row = g.tile + (size_t)(ck * 4 + 1 + cy) * 4 * nx;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const BR from = __shfl_up_sync(0xffffffffu, acc[1][q], 1);
+              atomicAdd(row + (size_t)q * nx + ix, acc[0][q] + (lane ? from : BR(0)));
+              if (lane == 31) atomicAdd(row + (size_t)q * nx + x1, acc[1][q]);
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          if (ok[u])
+            deposit_particle(g, src, p, ix, hx[u], hy[u], hk[u], dox[u], doy[u], doxi[u],
+                             dv[u][0], dv[u][1], dv[u][2], dv[u][3], refS, refJz);
       }
     }
   }
