@@ -1,12 +1,14 @@
 """Benchmark of the QS-PIC hot path: plasma particle-slice updates per second.
 
 One step = one beam step of the method: a full plasma sweep (every xi slice: push, deposit,
-FFT field solves, predictor-corrector for B_perp) followed by the beam push with the fused
-deposit of the next sweep's beam sources.  Workload: the 256x256, 1024-slice, 4-ppc mixed
-precision electron-beam run (5.4e8 beam macroparticles), synthetic seeded inputs, state
-resident in HBM.  Also measured: the same workload on the FP64 path (speedup denominator),
-an end-to-end figure through host buffers, the roofline of the dominant kernel, and the FP64
-oracle on a bounded sample (CPU baseline).
+FFT field solves, predictor-corrector for B_perp) followed by the beam push with the deposit
+of the next sweep's beam sources.  Workload: the 256x256, 1024-slice, 4-ppc mixed precision
+electron-beam run (5.4e8 beam macroparticles), synthetic seeded inputs, state resident in
+HBM.  The steps run through qsa_advance with pipeline_depth steps in flight per persistent
+launch (a wavefront in xi; the same arithmetic as the steps one after the other).  Also
+measured: the same workload on the FP64 path, an end-to-end job through host buffers, the
+roofline of the dominant kernel (the pipelined launch), and the FP64 oracle on a bounded
+sample (CPU baseline).
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Under torchrun each rank runs an independent replica (the method does not shard; weak
@@ -54,6 +56,12 @@ def sweep_bytes(p):
     ppc = p.ppc_plasma_x * p.ppc_plasma_y
     cells = p.nx * p.ny
     return 40.0 * ppc * cells * p.nxi + (16.0 + 24.0) * cells * (p.nxi + 1)
+
+
+def pipe_bytes(p, depth):
+    """Algorithmic HBM bytes of one pipelined launch of `depth` steps: each step's sweep and
+    beam push (sweep_bytes + push_bytes)."""
+    return depth * (sweep_bytes(p) + push_bytes(p))
 
 
 def push_bytes(p):
@@ -140,6 +148,23 @@ def updates_per_step(p):
     return p.plasma_per_slice() * p.nxi
 
 
+def time_advance(q, steps, warmup, depth, torch, stream):
+    """Warm up, then time `steps` beam steps through qsa_advance (launches of `depth` steps)
+    with CUDA events on the library's stream.  Returns (total ms, per-launch ms of the
+    persistent kernel, launches of the library's kernels)."""
+    q.advance(warmup)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    l0 = q.launch_count()
+    t0.record(stream)
+    q.advance(steps)
+    t1.record(stream)
+    t1.synchronize()
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1), q.launch_times(), q.launch_count() - l0
+
+
 def time_steps(q, p, steps, warmup, torch, stream, extra=None):
     """Warm up, then time `steps` beam steps with CUDA events on the library's stream; also
     the sweep and push launches separately.  Returns (total ms, sweep ms list, push ms list,
@@ -213,11 +238,12 @@ def run_reference(args, p):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--depth", type=int, default=16, help="beam steps in flight per launch")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -226,7 +252,7 @@ def main():
     ap.add_argument("--nxi", type=int, default=0,
                     help="override the number of slices (small profiling cases only)")
     args = ap.parse_args()
-    p = config.c2_mixed_electron_beam()
+    p = config.c2_mixed_electron_beam().with_(pipeline_depth=args.depth)
     if args.nxi:
         p = p.with_(nxi=args.nxi, Lxi=p.dxi * args.nxi)
     rank, world, local = dist_info()
@@ -250,26 +276,44 @@ def main():
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
     q = QSA(p)
-    barrier(world)
-    with Clocks(local) as clk:
-        ms, sw, pu, launches = time_steps(q, p, args.steps, args.warmup, torch, stream)
-    barrier(world)
-    ms = max_over_ranks(ms, world)
-    d = q.diagnostics()
     ups = updates_per_step(p)
-    value = ups * args.steps * world / (ms * 1e-3)
-    sw_ms, pu_ms = float(np.mean(sw)), float(np.mean(pu))
-    # dominant kernel: the larger of the sweep launch and the beam push
-    if sw_ms >= pu_ms:
-        dom, dom_ms, dom_bytes = "sweep_kernel", sw_ms, sweep_bytes(p)
+    barrier(world)
+    if args.depth > 1:
+        with Clocks(local) as clk:
+            ms, lt, launches = time_advance(q, args.steps, args.warmup, args.depth, torch,
+                                            stream)
+        barrier(world)
+        ms = max_over_ranks(ms, world)
+        value = ups * args.steps * world / (ms * 1e-3)
+        # dominant kernel: the persistent pipelined launch (all but a few memsets of the
+        # step); its full launches (depth steps each) give the per-launch duration
+        full = [t for i, t in enumerate(lt) if (i + 1) * args.depth <= args.steps]
+        dom_ms = float(np.mean(full if full else lt))
+        dom_steps = args.depth if full else args.steps
+        achieved = pipe_bytes(p, dom_steps) / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "pipe_kernel", "achieved": achieved,
+                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": None, "peak_source": peak_src, "launch_ms": dom_ms,
+                "steps_per_launch": dom_steps, "kernel_share": float(np.sum(lt)) / ms,
+                "step_frac": bytes_per_update(p) * value / world / 1e9 / hbm_peak}
     else:
-        dom, dom_ms, dom_bytes = "beam_push_kernel", pu_ms, push_bytes(p)
-    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
-            "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
-            "peak_source": peak_src,
-            "step_frac": bytes_per_update(p) * value / world / 1e9 / hbm_peak,
-            "sweep_ms": sw_ms, "push_ms": pu_ms}
+        with Clocks(local) as clk:
+            ms, sw, pu, launches = time_steps(q, p, args.steps, args.warmup, torch, stream)
+        barrier(world)
+        ms = max_over_ranks(ms, world)
+        value = ups * args.steps * world / (ms * 1e-3)
+        sw_ms, pu_ms = float(np.mean(sw)), float(np.mean(pu))
+        if sw_ms >= pu_ms:
+            dom, dom_ms, dom_bytes = "sweep_kernel", sw_ms, sweep_bytes(p)
+        else:
+            dom, dom_ms, dom_bytes = "beam_push_kernel", pu_ms, push_bytes(p)
+        achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": peak_src,
+                "step_frac": bytes_per_update(p) * value / world / 1e9 / hbm_peak,
+                "sweep_ms": sw_ms, "push_ms": pu_ms}
+    d = q.diagnostics()
     q.close()
     del q
     torch.cuda.empty_cache()
@@ -281,22 +325,25 @@ def main():
             "config": {"workload": WORKLOAD, "nx": p.nx, "ny": p.ny, "nxi": p.nxi,
                        "ppc_plasma": 4, "ppc_beam": 8, "beam_particles": 8 * p.nx * p.ny * p.nxi,
                        "n_pc_iter": p.n_pc_iter, "precision": "mixed",
+                       "pipeline_depth": args.depth,
                        "l2": "inputs larger than L2 (17 GB beam state)",
                        "parallelism": f"replicas{world}"},
             "gpu_launches": launches, "roofline": roof,
             "clocks": clk.summary(), "status": d["status"]}
 
     if not args.no_fp64:
-        p64 = p.with_(precision="fp64")
+        # the FP64 path, pipelined as deep as the timed steps (memory: FP64 slabs are 4.3 GB)
+        d64 = min(args.fp64_steps, args.depth)
+        p64 = p.with_(precision="fp64", pipeline_depth=d64)
         q = QSA(p64)
-        ms64, sw64, pu64, _ = time_steps(q, p64, args.fp64_steps, 1, torch, stream)
+        ms64, _, _ = time_advance(q, args.fp64_steps, 1, d64, torch, stream)
         q.close()
         del q
         torch.cuda.empty_cache()
         v64 = ups * args.fp64_steps / (ms64 * 1e-3)
         line["fp64"] = {"value": v64, "unit": "updates/s", "steps": args.fp64_steps,
-                        "ms_per_step": ms64 / args.fp64_steps, "sweep_ms": float(np.mean(sw64)),
-                        "push_ms": float(np.mean(pu64)), "speedup_mixed_over_fp64": value / v64}
+                        "pipeline_depth": d64, "ms_per_step": ms64 / args.fp64_steps,
+                        "speedup_mixed_over_fp64": value / v64}
 
     if not args.no_e2e:
         line["e2e"] = e2e(p, args.e2e_steps, torch, stream)
@@ -314,39 +361,42 @@ def main():
 
 
 def e2e(p, steps, torch, stream):
-    """Same metric through the public API with the beam state in pinned host memory: every
-    step uploads the beam (qsa_set_beam), sweeps, pushes and reads the per-slice diagnostics
-    back (qsa_diagnostics)."""
+    """Same metric for a whole job through the public API, from host data to host results:
+    the beam state goes up from pinned host memory (qsa_set_beam), `steps` beam steps run
+    (qsa_advance), and the per-slice diagnostics of the last sweep (qsa_diagnostics) and the
+    final beam state (qsa_get_beam) come back; all inside the timed region.  Bytes per step
+    are the job's copies divided by its steps."""
     from paper_2607_24214_b300.qsa import QSA
     q = QSA(p)
     n = p.nx * p.ny * p.nxi * 8
     keys = ("x", "y", "xi", "ux", "uy", "uz", "w")
     host = {k: torch.empty(n, dtype=torch.float64, pin_memory=True).numpy() for k in keys}
+    back = {k: torch.empty(n, dtype=torch.float64, pin_memory=True).numpy() for k in keys}
     import ctypes as ct
     from paper_2607_24214_b300.qsa import _ptr
     nout = ct.c_int64()
     q._check(q.lib.qsa_get_beam(q.h, 0, n, *[_ptr(host[k]) for k in keys], ct.byref(nout)))
-    # one untimed pass
+    # one untimed step (allocator warm-up)
     q.set_beam(0, host)
-    q.sweep()
-    q.beam_step()
+    q.advance(1)
     q.diagnostics()
     torch.cuda.synchronize()
     t = time.perf_counter()
-    for _ in range(steps):
-        q.set_beam(0, host)
-        q.sweep()
-        q.beam_step()
-        q.diagnostics()
+    q.set_beam(0, host)
+    q.advance(steps)
+    q.diagnostics()
+    q._check(q.lib.qsa_get_beam(q.h, 0, n, *[_ptr(back[k]) for k in keys], ct.byref(nout)))
     torch.cuda.synchronize()
     dt = time.perf_counter() - t
     q.close()
     del q
     torch.cuda.empty_cache()
     diag_bytes = (p.nxi + 1) * 15 * 8
+    beam_bytes = 7 * 8 * n
     return {"value": updates_per_step(p) * steps / dt, "unit": "updates/s",
-            "h2d_bytes_per_step": 7 * 8 * n, "d2h_bytes_per_step": diag_bytes,
-            "steps": steps}
+            "h2d_bytes_per_step": beam_bytes // steps,
+            "d2h_bytes_per_step": (beam_bytes + diag_bytes) // steps, "steps": steps,
+            "job": "set_beam + advance(steps) + diagnostics + get_beam"}
 
 
 if __name__ == "__main__":

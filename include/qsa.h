@@ -157,6 +157,12 @@ int qsa_beam_step(qsa_handle* h);
  * the sources those of the next.  n_steps = 0 is a no-op.  Asynchronous. */
 int qsa_advance(qsa_handle* h, int32_t n_steps);
 
+/* Device time, in ms, of each persistent launch of the last pipelined qsa_advance call (CUDA
+ * events recorded around the launches on the handle's stream; up to 64 launches): writes
+ * min(cap, launches) values to ms and their number to *n_out.  0 values for a handle without
+ * pipelining.  Synchronises with those events. */
+int qsa_launch_times(qsa_handle* h, float* ms, int cap, int* n_out);
+
 /* Copy the per-slice diagnostics of the last sweep into `out`; synchronises and returns the
  * latched device status (QSA_ERR_TIMEOUT, QSA_WARN_PSI_FLOOR, ...). */
 int qsa_diagnostics(qsa_handle* h, qsa_diag* out);

@@ -76,6 +76,10 @@ struct qsa_handle {
   // typed state lives behind these pointers (R = double for FP64, float for mixed)
   bool fp64 = true;
   void* st = nullptr;
+  // CUDA events around the persistent launches of the last pipelined qsa_advance
+  static constexpr int kLaunchEvents = 64;
+  cudaEvent_t ev[2 * kLaunchEvents] = {};
+  int n_timed = 0;
 };
 
 namespace {
@@ -526,6 +530,8 @@ int advance_pipelined(qsa_handle* h, int n) {
     }
     Barrier bar = s->slots[0].bar;
     CK(cudaMemsetAsync(bar.count, 0, sizeof(unsigned), h->stream));
+    const int ti = h->n_timed < qsa_handle::kLaunchEvents ? h->n_timed++ : -1;
+    if (ti >= 0) CK(cudaEventRecord(h->ev[2 * ti], h->stream));
     const PipeTable<R>* tab = s->ptab;
     int r0 = (int)(h->pushes % (int64_t)(nslot + 1));
     int steps = m;
@@ -533,6 +539,7 @@ int advance_pipelined(qsa_handle* h, int n) {
     CK(cudaLaunchCooperativeKernel((void*)pipe_kernel<R>, dim3(s->pipe_grid), dim3(kThreads),
                                    args, s->pipe_smem, h->stream));
     ++h->launches;
+    if (ti >= 0) CK(cudaEventRecord(h->ev[2 * ti + 1], h->stream));
     for (int i = 0; i < m; ++i) {
       SweepArgs<R>& a = s->slots[i];
       diag_reduce_kernel<<<dp.nk, 256, 0, h->stream>>>(a.dpart, s->pipe_grid, a.diag, dp.nk);
@@ -835,6 +842,8 @@ int qsa_init(const qsa_params* params, void* stream, qsa_alloc_fn alloc, qsa_fre
   dp.px = make_plan(dp.nx);
   dp.py = make_plan(dp.ny);
   h->fp64 = params->precision == QSA_FP64;
+  if (params->pipeline_depth > 1)
+    for (int i = 0; i < 2 * qsa_handle::kLaunchEvents; ++i) cudaEventCreate(&h->ev[i]);
   const size_t smem = h->fp64 ? sweep_smem<double>(dp) : sweep_smem<float>(dp);
   int max_smem = 0;
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -897,8 +906,10 @@ int qsa_beam_step(qsa_handle* h) {
 int qsa_advance(qsa_handle* h, int32_t n_steps) {
   if (!h) return QSA_ERR_ARG;
   if (n_steps < 0) return fail(h, QSA_ERR_ARG, "n_steps must be >= 0");
-  if (h->prm.pipeline_depth > 1)
+  if (h->prm.pipeline_depth > 1) {
+    h->n_timed = 0;
     return h->fp64 ? advance_pipelined<double>(h, n_steps) : advance_pipelined<float>(h, n_steps);
+  }
   for (int32_t i = 0; i < n_steps; ++i) {
     int rc = h->fp64 ? sweep<double>(h) : sweep<float>(h);
     if (rc) return rc;
@@ -953,6 +964,18 @@ int qsa_phase_times(qsa_handle* h, int64_t* out, int cap) {
   return QSA_OK;
 }
 
+int qsa_launch_times(qsa_handle* h, float* ms, int cap, int* n_out) {
+  if (!h || !ms || !n_out) return QSA_ERR_ARG;
+  *n_out = 0;
+  const int n = h->n_timed < cap ? h->n_timed : cap;
+  for (int i = 0; i < n; ++i) {
+    CK(cudaEventSynchronize(h->ev[2 * i + 1]));
+    CK(cudaEventElapsedTime(ms + i, h->ev[2 * i], h->ev[2 * i + 1]));
+  }
+  *n_out = n;
+  return QSA_OK;
+}
+
 int64_t qsa_launch_count(const qsa_handle* h) { return h ? h->launches : 0; }
 
 int64_t qsa_device_bytes(const qsa_handle* h) { return h ? h->bytes : 0; }
@@ -970,6 +993,8 @@ void qsa_destroy(qsa_handle* h) {
     if (h->fp64) delete S<double>(h);
     else delete S<float>(h);
   }
+  for (int i = 0; i < 2 * qsa_handle::kLaunchEvents; ++i)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   delete h;
 }
 

@@ -31,7 +31,7 @@ SOURCES = ("Sb", "Jz", "Jx", "Jy")
 EXPORTS = ("qsa_init", "qsa_set_beam", "qsa_get_beam", "qsa_plasma_sweep", "qsa_beam_step",
            "qsa_diagnostics", "qsa_copy_field", "qsa_copy_source", "qsa_field_solve",
            "qsa_phase_times", "qsa_launch_count", "qsa_device_bytes", "qsa_last_error",
-           "qsa_destroy", "qsa_field_solve_static", "qsa_advance")
+           "qsa_destroy", "qsa_field_solve_static", "qsa_advance", "qsa_launch_times")
 
 
 class QsaError(RuntimeError):
@@ -100,6 +100,9 @@ def load_library(path: str = LIB_PATH):
         getattr(lib, name).restype = ct.c_int
     lib.qsa_advance.argtypes = [P, ct.c_int32]
     lib.qsa_advance.restype = ct.c_int
+    lib.qsa_launch_times.argtypes = [P, ct.POINTER(ct.c_float), ct.c_int,
+                                     ct.POINTER(ct.c_int)]
+    lib.qsa_launch_times.restype = ct.c_int
     lib.qsa_diagnostics.argtypes = [P, ct.POINTER(Diag)]
     lib.qsa_diagnostics.restype = ct.c_int
     lib.qsa_copy_field.argtypes = [P, ct.c_int, ct.c_int, ct.c_int, _DP]
@@ -221,6 +224,14 @@ class QSA:
     def advance(self, n_steps: int):
         """n_steps x (sweep, beam step); pipelined launches when p.pipeline_depth >= 2."""
         return self._check(self.lib.qsa_advance(self.h, int(n_steps)))
+
+    def launch_times(self) -> np.ndarray:
+        """Device ms of each persistent launch of the last pipelined advance()."""
+        out = np.zeros(64, dtype=np.float32)
+        n = ct.c_int()
+        self._check(self.lib.qsa_launch_times(
+            self.h, out.ctypes.data_as(ct.POINTER(ct.c_float)), out.size, ct.byref(n)))
+        return out[:n.value].copy()
 
     # -- data in / out
     def set_beam(self, si: int, b: dict):
