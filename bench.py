@@ -218,7 +218,7 @@ def run_reference(args, p):
         cpu_baseline(p, 2)
     t0 = time.perf_counter()
     for _ in range(args.steps_ref):
-        v, _ = cpu_baseline(p)
+        v, _ = cpu_baseline(p, args.ref_slices)
         vals.append(v)
     wall = time.perf_counter() - t0
     val = float(np.median(vals))
@@ -226,9 +226,9 @@ def run_reference(args, p):
             "n_gpus": args.gpus, "steps": args.steps_ref, "warmup": args.warmup_ref,
             "ms_per_step": 1e3 * wall / max(args.steps_ref, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"first {CPU_SAMPLE_SLICES} slices"},
+            "config": {"workload": WORKLOAD, "sample": f"first {args.ref_slices} slices"},
             "cpu_baseline": {"value": val, "unit": "updates/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {CPU_SAMPLE_SLICES} of {p.nxi + 1} slices of "
+                             "sample": f"first {args.ref_slices} of {p.nxi + 1} slices of "
                                        f"one sweep, {p.nx}x{p.ny}, numpy FP64"},
             "e2e": {"value": val, "unit": "updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -248,6 +248,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--steps-ref", type=int, default=2)
+    ap.add_argument("--ref-slices", type=int, default=CPU_SAMPLE_SLICES,
+                    help="slices of the oracle sample per reference step")
     ap.add_argument("--warmup-ref", type=int, default=0)
     ap.add_argument("--nxi", type=int, default=0,
                     help="override the number of slices (small profiling cases only)")
