@@ -66,6 +66,11 @@ typedef struct {
   double xi_front, xi_back;/* beam occupies [xi_front, xi_back); xi_back < 0 means Lxi */
 } qsa_species;
 
+/* A transverse wave vector k = (2 pi mx / Lx, 2 pi my / Ly). */
+typedef struct {
+  int32_t mx, my;
+} qsa_kvec;
+
 /* Seeded transverse density mode: weight factor 1 + amplitude cos(k.x + phase). */
 typedef struct {
   int32_t mx, my;          /* k = (2 pi mx / Lx, 2 pi my / Ly) */
@@ -87,6 +92,9 @@ typedef struct {
   int64_t spin_limit;      /* iteration limit of every device-side wait */
   qsa_species species[QSA_MAX_SPECIES];
   qsa_mode modes[QSA_MAX_MODES];
+  int32_t n_diag_modes;    /* transverse modes whose amplitude every sweep records (0..16) */
+  int32_t _pad;
+  qsa_kvec diag_modes[QSA_MAX_MODES]; /* k != 0, |mx| <= nx/2, |my| <= ny/2 */
 } qsa_params;
 
 /* Allocator callbacks: alloc returns a device pointer (NULL on failure) of at least `bytes`
@@ -97,7 +105,11 @@ typedef void (*qsa_free_fn)(void* ptr, size_t bytes, void* ctx, void* stream);
 typedef struct qsa_handle qsa_handle;
 
 /* Per-slice diagnostics of the last sweep; every non-NULL pointer is a caller array of
- * nxi + 1 entries (energy: 6 * (nxi + 1), slice-major).  Any pointer may be NULL. */
+ * nxi + 1 entries unless stated (energy: 6 * (nxi + 1), slice-major).  Any pointer may be
+ * NULL.  The field amplitudes and the beam moments are those of the paper's growth and
+ * saturation figures: rms fields over the transverse plane and over xi segments of width
+ * 2 k_p^-1 (Fig. 2), Fourier amplitudes of single modes (the growth rates of Eq. 5), and the
+ * beam's rms momentum spread per xi position (Fig. 3f). */
 typedef struct {
   double* energy;       /* 1/2 sum F^2 dx dy dxi of E_x, E_y, E_z, B_x, B_y, B_z */
   double* psi0;         /* k = 0 mode of psi */
@@ -111,6 +123,20 @@ typedef struct {
   double* pc_residual;  /* ||B_perp(n) - B_perp(n-1)|| / ||B_perp(n)|| of the last solve */
   int64_t beam_lost;    /* out: beam particles that left the window (all species) */
   int64_t sweeps;       /* out: sweeps done by this handle */
+  double* rms;          /* [nxi+1][6]: sqrt(<F^2>) over the transverse plane of E_x, E_y, E_z,
+                           B_x, B_y, B_z (from the energies) */
+  double seg_width;     /* in: xi width of the rms_seg segments; <= 0 means 2 k_p^-1 */
+  double* rms_seg;      /* [ceil(Lxi / seg_width)][6]: sqrt of <F^2> averaged over the
+                           transverse plane and the slices j dxi of segment s, i.e.
+                           s seg_width <= j dxi < (s+1) seg_width (slice nxi joins the last) */
+  double* mode_amp;     /* [nxi+1][n_diag_modes][5][2]: Fourier coefficient F(k)/(nx ny)
+                           (re, im; F(x) = sum_k F(k) e^{i k.x} / (nx ny), forward transform
+                           with e^{-i k.x}) of psi, E_z, B_x, B_y, B_z at each slice */
+  double* beam_moments; /* [n_species][nxi][7]: over the live particles whose xi lies in cell
+                           c, sums of w/wbar, (w/wbar) u_x, (w/wbar) u_y, (w/wbar) du_z,
+                           (w/wbar) u_x^2, (w/wbar) u_y^2, (w/wbar) du_z^2, with
+                           du_z = u_z - sqrt(gamma_b^2 - 1) and wbar the species' nominal
+                           weight; of the current beam (after the last push) */
 } qsa_diag;
 
 /* Create a handle: validates params, allocates device state, builds every beam species on

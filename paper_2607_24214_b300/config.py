@@ -13,7 +13,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field, replace
-from typing import List
+from typing import List, Tuple
 
 MAX_SPECIES = 4
 MAX_MODES = 16
@@ -67,6 +67,7 @@ class Params:
     seed: int = 0
     spin_limit: int = 1 << 26
     pipeline_depth: int = 1          # beam steps in flight per qsa_advance launch (1: none)
+    diag_modes: List[Tuple[int, int]] = field(default_factory=list)  # (mx, my) recorded per slice
     steps: int = 1                   # beam steps of the named workload (not part of the C struct)
 
     @property

@@ -1,6 +1,7 @@
 // C ABI of the QS-PIC hot path (declarations and contracts in include/qsa.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -140,6 +141,7 @@ struct State {
   ModesDev modes{};
   std::vector<R*> srcs;             // source ring, S + 1 entries [nk][ny][nx][4]
   std::vector<int*> cmaxs;          // extent ring, S + 1 entries [nxi]
+  std::vector<double*> moms;        // beam-moment ring, S + 1 entries [n_species][nxi][7]
   int* dmin = nullptr;              // min over live particles of (xi cell - home layer)
   PipeTable<R>* ptab = nullptr;     // device copy of the pipeline table
   int pipe_grid = 0;
@@ -159,6 +161,12 @@ struct State {
 template <typename R>
 State<R>* S(qsa_handle* h) { return reinterpret_cast<State<R>*>(h->st); }
 
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);    \
+  } while (0)
+
 // Ring entries of the beam state after `pushes` pushes: its sources and its extents.
 template <typename R>
 R* ring_src(qsa_handle* h, int64_t pushes) {
@@ -170,12 +178,24 @@ int* ring_cmax(qsa_handle* h, int64_t pushes) {
   State<R>* s = S<R>(h);
   return s->cmaxs[(size_t)(pushes % (int64_t)s->cmaxs.size())];
 }
+template <typename R>
+double* ring_mom(qsa_handle* h, int64_t pushes) {
+  State<R>* s = S<R>(h);
+  return s->moms[(size_t)(pushes % (int64_t)s->moms.size())];
+}
+size_t mom_bytes(const qsa_handle* h) {
+  const int ns = h->prm.n_species > 0 ? h->prm.n_species : 1;
+  return (size_t)ns * (h->dp.nxi > 0 ? h->dp.nxi : 1) * 7 * sizeof(double);
+}
+// Zero the extent and moment ring entries that the beam state after `pushes` pushes fills.
+template <typename R>
+int clear_ring(qsa_handle* h, int64_t pushes) {
+  CK(cudaMemsetAsync(ring_cmax<R>(h, pushes), 0xFF,
+                     (size_t)(h->dp.nxi > 0 ? h->dp.nxi : 1) * sizeof(int), h->stream));
+  CK(cudaMemsetAsync(ring_mom<R>(h, pushes), 0, mom_bytes(h), h->stream));
+  return QSA_OK;
+}
 
-#define CK(call)                                              \
-  do {                                                        \
-    cudaError_t e_ = (call);                                  \
-    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);    \
-  } while (0)
 
 template <typename R>
 size_t sweep_smem(const DevParams& dp) {
@@ -296,6 +316,9 @@ int setup(qsa_handle* h) {
     if (i == 0 &&
         !(a.ptimes = (unsigned long long*)A(kTimedSlices * kTimedPhases * 2 * 8)))
       return fail(h, QSA_ERR_OOM, "sweep buffers");
+    if (dp.nmodes > 0 &&
+        !(a.mode_out = (R*)A((size_t)dp.nk * dp.nmodes * 10 * sizeof(R))))
+      return fail(h, QSA_ERR_OOM, "mode buffers");
     a.twx = twp;
     a.twy = twp + dp.nx;
     a.ktab = ktab;
@@ -313,9 +336,11 @@ int setup(qsa_handle* h) {
   for (int i = 0; i <= nslot; ++i) {
     R* sb = (R*)A((size_t)dp.nk * g * 4 * sizeof(R));
     int* cm = (int*)A((size_t)(dp.nxi > 0 ? dp.nxi : 1) * sizeof(int));
-    if (!sb || !cm) return fail(h, QSA_ERR_OOM, "source ring");
+    double* mo = (double*)A(mom_bytes(h));
+    if (!sb || !cm || !mo) return fail(h, QSA_ERR_OOM, "source ring");
     s->srcs.push_back(sb);
     s->cmaxs.push_back(cm);
+    s->moms.push_back(mo);
   }
   // beam species
   const qsa_params& P = h->prm;
@@ -387,6 +412,7 @@ int setup(qsa_handle* h) {
     for (int i = 0; i <= nslot; ++i) {
       t.srcbuf[i] = s->srcs[i];
       t.cmaxbuf[i] = s->cmaxs[i];
+      t.mombuf[i] = s->moms[i];
     }
     t.nslot = nslot;
     t.nspecies = (int)s->species.size();
@@ -412,15 +438,17 @@ int deposit_sources(qsa_handle* h) {
   const DevParams& dp = h->dp;
   R* src = ring_src<R>(h, h->pushes);
   int* cmax = ring_cmax<R>(h, h->pushes);
+  double* mom = ring_mom<R>(h, h->pushes);
   CK(cudaMemsetAsync(src, 0, (size_t)dp.nk * dp.nx * dp.ny * 4 * sizeof(R), h->stream));
-  CK(cudaMemsetAsync(cmax, 0xFF, (size_t)(dp.nxi > 0 ? dp.nxi : 1) * sizeof(int), h->stream));
+  if (int rc = clear_ring<R>(h, h->pushes)) return rc;
   CK(cudaMemsetAsync(s->dmin, 0, sizeof(int), h->stream));
   for (size_t si = 0; si < s->beams.size(); ++si) {
     const auto& b = s->beams[si];
     if (b.n == 0) continue;
     const unsigned groups = (unsigned)(s->species[si].nkb * dp.ny);
     beam_kernel<R, false><<<groups, kThreads, beam_smem_bytes<R>(dp.nx), h->stream>>>(
-        b, dp, s->species[si], s->bconst[si], nullptr, src, nullptr, Extent{cmax, s->dmin});
+        b, dp, s->species[si], s->bconst[si], nullptr, src, nullptr,
+        Extent{cmax, s->dmin, mom + si * (size_t)dp.nxi * 7});
     ++h->launches;
     CK(cudaGetLastError());
   }
@@ -516,8 +544,7 @@ int advance_pipelined(qsa_handle* h, int n) {
     for (int i = 1; i <= m; ++i) {
       CK(cudaMemsetAsync(ring_src<R>(h, h->pushes + i), 0, (size_t)dp.nk * g * 4 * sizeof(R),
                          h->stream));
-      CK(cudaMemsetAsync(ring_cmax<R>(h, h->pushes + i), 0xFF,
-                         (size_t)(dp.nxi > 0 ? dp.nxi : 1) * sizeof(int), h->stream));
+      if (int rc = clear_ring<R>(h, h->pushes + i)) return rc;
     }
     for (int i = 0; i < m; ++i) {
       SweepArgs<R>& a = s->slots[i];
@@ -560,15 +587,17 @@ int beam_step(qsa_handle* h) {
   const DevParams& dp = h->dp;
   R* src = ring_src<R>(h, h->pushes + 1);
   int* cmax = ring_cmax<R>(h, h->pushes + 1);
+  double* mom = ring_mom<R>(h, h->pushes + 1);
   const R* slab = s->slots[s->last_slot].slab;
   CK(cudaMemsetAsync(src, 0, (size_t)dp.nk * dp.nx * dp.ny * 4 * sizeof(R), h->stream));
-  CK(cudaMemsetAsync(cmax, 0xFF, (size_t)(dp.nxi > 0 ? dp.nxi : 1) * sizeof(int), h->stream));
+  if (int rc = clear_ring<R>(h, h->pushes + 1)) return rc;
   for (size_t si = 0; si < s->beams.size(); ++si) {
     const auto& b = s->beams[si];
     if (b.n == 0) continue;
     const unsigned groups = (unsigned)(s->species[si].nkb * dp.ny);
     beam_kernel<R, true><<<groups, kThreads, beam_smem_bytes<R>(dp.nx), h->stream>>>(
-        b, dp, s->species[si], s->bconst[si], slab, src, s->lost, Extent{cmax, nullptr});
+        b, dp, s->species[si], s->bconst[si], slab, src, s->lost,
+        Extent{cmax, nullptr, mom + si * (size_t)dp.nxi * 7});
     ++h->launches;
     CK(cudaGetLastError());
   }
@@ -615,6 +644,39 @@ int diagnostics(qsa_handle* h, qsa_diag* out) {
       const double den = row(D_PCDEN)[j];
       out->pc_residual[j] = den > 0 ? std::sqrt(row(D_PCNUM)[j] / den) : 0.0;
     }
+  }
+  // rms fields per slice, and over xi segments: <F^2> = 2 E / (Lx Ly dxi)
+  {
+    const double ms_norm = 2.0 / (h->dp.Lx * h->dp.Ly * h->dp.dxi);
+    const double W = out->seg_width > 0 ? out->seg_width : 2.0;
+    const int nseg = std::max(1, (int)std::ceil(h->dp.Lxi / W - 1e-12));
+    std::vector<double> acc((size_t)nseg * 6, 0.0), cnt(nseg, 0.0);
+    for (int j = 0; j < nk; ++j) {
+      const int sgi = std::min(nseg - 1, (int)std::floor(j * h->dp.dxi / W + 1e-12));
+      cnt[sgi] += 1.0;
+      for (int f = 0; f < 6; ++f) {
+        const double ms = row(D_E0 + f)[j] * ms_norm;
+        if (out->rms) out->rms[(size_t)j * 6 + f] = std::sqrt(ms);
+        acc[(size_t)sgi * 6 + f] += ms;
+      }
+    }
+    if (out->rms_seg)
+      for (int sgi = 0; sgi < nseg; ++sgi)
+        for (int f = 0; f < 6; ++f)
+          out->rms_seg[(size_t)sgi * 6 + f] =
+              cnt[sgi] > 0 ? std::sqrt(acc[(size_t)sgi * 6 + f] / cnt[sgi]) : 0.0;
+  }
+  if (out->mode_amp && h->dp.nmodes > 0) {
+    std::vector<R> mo((size_t)nk * h->dp.nmodes * 10);
+    CK(cudaMemcpyAsync(mo.data(), a.mode_out, mo.size() * sizeof(R), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < mo.size(); ++i) out->mode_amp[i] = (double)mo[i];
+  }
+  if (out->beam_moments && h->prm.n_species > 0) {
+    CK(cudaMemcpyAsync(out->beam_moments, ring_mom<R>(h, h->pushes), mom_bytes(h),
+                       cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
   }
   out->beam_lost = (int64_t)lost;
   out->sweeps = h->sweeps;
@@ -780,6 +842,14 @@ int validate(const qsa_params* p, std::string& why) {
   if (p->spin_limit < 0) return bad("spin_limit must be >= 0");
   if (p->pipeline_depth < 0 || p->pipeline_depth > kMaxPipe)
     return bad("pipeline_depth must be in 0..16");
+  if (p->n_diag_modes < 0 || p->n_diag_modes > QSA_MAX_MODES)
+    return bad("n_diag_modes must be in 0..16");
+  for (int m = 0; m < p->n_diag_modes; ++m) {
+    const qsa_kvec k = p->diag_modes[m];
+    if (k.mx == 0 && k.my == 0) return bad("diag mode k = 0 (psi0, E_z0 are separate outputs)");
+    if (2 * std::abs(k.mx) > p->nx || 2 * std::abs(k.my) > p->ny)
+      return bad("diag mode beyond the Nyquist index");
+  }
   const double dxi = p->Lxi / p->nxi;
   for (int s = 0; s < p->n_species; ++s) {
     const qsa_species& q = p->species[s];
@@ -841,6 +911,15 @@ int qsa_init(const qsa_params* params, void* stream, qsa_alloc_fn alloc, qsa_fre
   dp.spin_limit = params->spin_limit;
   dp.px = make_plan(dp.nx);
   dp.py = make_plan(dp.ny);
+  // diagnosed modes on the half spectrum: k itself when mx >= 0, else its conjugate -k
+  dp.nmodes = params->n_diag_modes;
+  for (int m = 0; m < dp.nmodes; ++m) {
+    const qsa_kvec k = params->diag_modes[m];
+    const int sg = k.mx < 0 ? -1 : 1;
+    dp.mkx[m] = sg * k.mx;
+    dp.mky[m] = ((sg * k.my) % dp.ny + dp.ny) % dp.ny;
+    dp.mconj[m] = k.mx < 0 ? 1 : 0;
+  }
   h->fp64 = params->precision == QSA_FP64;
   if (params->pipeline_depth > 1)
     for (int i = 0; i < 2 * qsa_handle::kLaunchEvents; ++i) cudaEventCreate(&h->ev[i]);

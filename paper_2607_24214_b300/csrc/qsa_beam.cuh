@@ -15,6 +15,8 @@
 // sqrt(gamma_b^2 - 1))): the reference is uniform in x, y (k = 0 only) and is kept in FP64
 // per node, so FP32 sums keep the 1e-4 density noise of the fluctuations.
 #pragma once
+#include <cmath>
+
 #include "qsa_common.cuh"
 
 namespace qsa {
@@ -64,6 +66,7 @@ struct BeamConst {
   BR cdx, cdy, cdk;  // dt/dx, dt/dy, dt/dxi
   BR refS, refJz;    // reference source weights qbar omvbar, qbar (1 - omvbar)
   BR qb, omvbar;     // qbar, 1 - v_z of the reference momentum
+  BR uzb_hi, uzb_lo; // sqrt(gamma_b^2 - 1) as a (leading, trailing) pair (trailing 0 in FP64)
 };
 template <typename BR>
 inline BeamConst<BR> beam_consts(const DevParams& p, const SpeciesDev& sp) {
@@ -76,6 +79,9 @@ inline BeamConst<BR> beam_consts(const DevParams& p, const SpeciesDev& sp) {
   c.refJz = BR(sp.qbar * (1.0 - sp.omvbar));
   c.qb = BR(sp.qbar);
   c.omvbar = BR(sp.omvbar);
+  const double uzb = std::sqrt(sp.gamma_b * sp.gamma_b - 1.0);
+  c.uzb_hi = BR(uzb);
+  c.uzb_lo = BR(uzb - (double)c.uzb_hi);
   return c;
 }
 
@@ -435,7 +441,16 @@ __device__ __forceinline__ void gather_cell(const BR* __restrict__ slab, const D
 struct Extent {
   int* cmax;
   int* dmin;
+  double* mom;  // [nxi][7] beam moments of the species per xi cell (see qsa_diag), or null
 };
+
+// u_z - sqrt(gamma_b^2 - 1) without cancellation of the leading parts
+__device__ __forceinline__ double uz_dev(double uz, const BeamConst<double>& c) {
+  return uz - c.uzb_hi;
+}
+__device__ __forceinline__ float uz_dev(float2 uz, const BeamConst<float>& c) {
+  return (uz.x - c.uzb_hi) + (uz.y - c.uzb_lo);
+}
 
 // One group of a species: the ppc * nx particles whose home is xi cell (layer) k and row iy.
 // PUSH = false: deposit the current beam (sources of the first sweep).  PUSH = true: push
@@ -455,12 +470,15 @@ __device__ void beam_group(const BeamArrays<BR>& b, const DevParams& p, const Sp
   const int nx = p.nx;
   const int tn = 2 * 4 * nx * 4;
   for (int e = threadIdx.x; e < tn; e += blockDim.x) g.tile[e] = BR(0);
+  __shared__ double s_mom[7];
   if (threadIdx.x == 0) {
     s_ext[0] = -1;
     s_ext[1] = 0;
+    for (int k = 0; k < 7; ++k) s_mom[k] = 0.0;
   }
   __syncthreads();
   int cmax_t = -1, dmin_t = 0;
+  BR mom_t[7] = {0, 0, 0, 0, 0, 0, 0};  // moments of the particles in the home layer
   // the aggregated deposit needs whole warps over consecutive columns
   const bool lane_agg = (nx % 32 == 0) && (blockDim.x % 32 == 0);
   const size_t base = (size_t)grp * sp.ppc * nx;
@@ -560,6 +578,16 @@ __device__ void beam_group(const BeamArrays<BR>& b, const DevParams& p, const Sp
           const int cell = (int)floor(hk[u] + oxi[u]);  // xi cell relative to the home layer
           cmax_t = max(cmax_t, g.kabs + cell);
           dmin_t = min(dmin_t, cell);
+          const BR wr = BR(1) + dw[u], duz = uz_dev(uz[u], bc);
+          const BR mv[7] = {wr, wr * ux[u], wr * uy[u], wr * duz, wr * ux[u] * ux[u],
+                            wr * uy[u] * uy[u], wr * duz * duz};
+          if (cell == 0) {
+#pragma unroll
+            for (int k = 0; k < 7; ++k) mom_t[k] += mv[k];
+          } else if (ext.mom && g.kabs + cell >= 0 && g.kabs + cell < p.nxi) {
+            for (int k = 0; k < 7; ++k)
+              atomicAdd(ext.mom + (size_t)(g.kabs + cell) * 7 + k, (double)mv[k]);
+          }
         }
         beam_sources(ux[u], uy[u], uz_lead(uz[u]), dw[u], bc, dv[u][0], dv[u][1], dv[u][2],
                      dv[u][3]);
@@ -618,14 +646,21 @@ __device__ void beam_group(const BeamArrays<BR>& b, const DevParams& p, const Sp
   }
   cmax_t = warp_max(cmax_t);
   dmin_t = warp_min(dmin_t);
+#pragma unroll
+  for (int k = 0; k < 7; ++k) mom_t[k] = warp_sum(mom_t[k]);
   if ((threadIdx.x & 31) == 0) {
     if (cmax_t > s_ext[0]) atomicMax(&s_ext[0], cmax_t);
     if (dmin_t < 0) atomicMin(&s_ext[1], dmin_t);
+    if (ext.mom)
+      for (int k = 0; k < 7; ++k) atomicAdd(&s_mom[k], (double)mom_t[k]);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     if (ext.cmax && s_ext[0] >= 0) atomicMax(ext.cmax + g.kabs, s_ext[0]);
     if (ext.dmin && s_ext[1] < 0) atomicMin(ext.dmin, s_ext[1]);
+    if (ext.mom && g.kabs < p.nxi)
+      for (int k = 0; k < 7; ++k)
+        if (s_mom[k] != 0.0) atomicAdd(ext.mom + (size_t)g.kabs * 7 + k, s_mom[k]);
   }
   for (int e = threadIdx.x; e < 2 * 4 * nx; e += blockDim.x) {
     const int dk = e / (4 * nx), r = (e / nx) % 4, x = e % nx;

@@ -53,6 +53,10 @@ struct DevParams {
   double psi_floor;
   long long spin_limit;
   FftPlan px, py;
+  // diagnosed transverse modes: stored at half-spectrum column mkx, row mky; mconj = 1 when
+  // the requested k is the conjugate (-k) of the stored one
+  int nmodes;
+  int mkx[16], mky[16], mconj[16];
 };
 
 // ---------------------------------------------------------------------------------------

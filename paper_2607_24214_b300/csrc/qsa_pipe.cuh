@@ -46,6 +46,7 @@ struct PipeTable {
   SweepArgs<R> st[kMaxPipe];    // sweep slots (src is taken from the ring)
   R* srcbuf[kMaxPipe + 1];      // source ring [nk][ny][nx][4]
   int* cmaxbuf[kMaxPipe + 1];   // extent ring: largest live xi cell per home layer [nxi]
+  double* mombuf[kMaxPipe + 1]; // beam-moment ring [nspecies][nxi][7]
   int nslot;                    // S: slots in use; the rings hold S + 1 entries
   int nspecies;
   int max_push;                 // layers a step pushes per tick at most
@@ -212,6 +213,7 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
         if (n == 0) continue;
         R* src_next = T->srcbuf[(r0 + s + 1) % S1];
         int* cmax_next = T->cmaxbuf[(r0 + s + 1) % S1];
+        double* mom_next = T->mombuf[(r0 + s + 1) % S1];
         const R* slab = sa[s].slab;
         for (int c = pf[s]; c < pf[s] + n; ++c) {
           for (int si = 0; si < nspec; ++si) {
@@ -221,7 +223,8 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
             if (q0 < 0) q0 += G;
             for (int q = q0; q < ny; q += G)
               beam_group<R, true>(sb[si], p, sp, sbc[si], slab, src_next, T->lost,
-                                  Extent{cmax_next, nullptr}, (c - sp.k0) * ny + q, tile);
+                                  Extent{cmax_next, nullptr, mom_next + (size_t)si * nxi * 7},
+                                  (c - sp.k0) * ny + q, tile);
             base += ny;
           }
         }
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
       if (!grid_sync(bar, epoch)) return;
       for (int k = 0; k < nc; ++k) {
         const int s = act_c[k];
-        col_phase_psi(sa[s], buf, tw, unit0(k, uc, G), G, nbc);
+        col_phase_psi(sa[s], buf, tw, unit0(k, uc, G), G, nbc, js[s] + 1);
       }
       if (!grid_sync(bar, epoch)) return;
       for (int k = 0; k < nc; ++k) {

@@ -120,6 +120,7 @@ struct SweepArgs {
   const C<R>* twy;
   const R* src;                             // [nk][ny][nx][4] beam S_b, J_z, J_x, J_y deviations
   R* slab;                                  // [nk][ny][nx][8]
+  R* mode_out;                              // [nk][nmodes][5][2] or null (diagnosed modes)
   double* diag;                             // [D_COUNT][nk]
   double* dpart;                            // [nk][gridDim.x][P_COUNT] partials
   const R* ktab;                            // wavenumber table, see kvec
@@ -739,6 +740,29 @@ __device__ __forceinline__ Kv<R> kvec(const R* __restrict__ ktab, int nxh, int n
   return k;
 }
 
+// Record the diagnosed modes that live in columns kb .. kb + nc - 1 of the column buffer O
+// (per column nf spectra of ny rows, in the order given by fields[]: output field index of
+// each spectrum, -1 to skip) as F(k)/(nx ny) of slice j.  Reads O only, before the inverse
+// transform's first stage barrier.
+template <typename R>
+__device__ __forceinline__ void record_modes(const SweepArgs<R>& a, const C<R>* O, int kb,
+                                             int nc, int nf, const int* fields, int j) {
+  const DevParams& p = a.p;
+  if (a.mode_out == nullptr || j < 0) return;
+  for (int m = threadIdx.x; m < p.nmodes; m += blockDim.x) {
+    const int c = p.mkx[m] - kb;
+    if (c < 0 || c >= nc) continue;
+    const R sg = p.mconj[m] ? R(-1) : R(1);
+    R* o = a.mode_out + ((size_t)j * p.nmodes + m) * 10;
+    for (int f = 0; f < nf; ++f) {
+      if (fields[f] < 0) continue;
+      const C<R> v = O[((size_t)c * nf + f) * p.ny + p.mky[m]];
+      o[2 * fields[f]] = v.x * a.k.scale;
+      o[2 * fields[f] + 1] = sg * v.y * a.k.scale;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ column phase: B, E_z
 // psi0: the k = 0 potential of the slice, which fixes the plasma reference state of the
 // deposits (needed for <J_z>, the source of the k = 0 mode).
@@ -819,6 +843,10 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
       Oc[3 * ny + ky] = oez;
     }
     __syncthreads();
+    if (last) {
+      const int fields[4] = {2, 3, 4, 1};  // B_x, B_y, B_z, E_z
+      record_modes(a, O, kb, nc, 4, fields, j);
+    }
     C<R>* W = block_fft(O, Z, nc * 4, p.py, tw, +1);
     for (int e = threadIdx.x; e < 4 * ny * nc; e += blockDim.x) {
       const int t = e / nc, c = e - t * nc, f = t / ny, ky = t - f * ny;
@@ -837,7 +865,7 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
 // ------------------------------------------------------------------ column phase: psi
 template <typename R>
 __device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int u0, int G,
-                              int nb) {
+                              int nb, int jn) {
   const DevParams& p = a.p;
   const int ny = p.ny, nxh = p.nxh;
   C<R>* A = buf;
@@ -872,6 +900,10 @@ __device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int u0
       Oc[2 * ny + ky] = cmuli(cscale(ps, k.kyd));
     }
     __syncthreads();
+    {
+      const int fields[3] = {0, -1, -1};  // psi
+      record_modes(a, O, kb, nc, 3, fields, jn);
+    }
     C<R>* W = block_fft(O, Z, nc * 3, p.py, tw, +1);
     for (int e = threadIdx.x; e < 3 * ny * nc; e += blockDim.x) {
       const int t = e / nc, c = e - t * nc, f = t / ny, ky = t - f * ny;
@@ -1010,7 +1042,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(SweepArgs<R> a) {
   if (!sync(-1, 0)) return;
   row_phase(a, buf, tw, DEP_INIT, 0, u0, G, 1);
   if (!sync(-1, 1)) return;
-  col_phase_psi(a, buf, tw, u0, G, 1);
+  col_phase_psi(a, buf, tw, u0, G, 1, 0);
   if (!sync(-1, 2)) return;
   irow_phase(a, buf, tw, true, 0, false, 0.0, u0, G, 1);
   if (!sync(-1, 3)) return;
@@ -1043,7 +1075,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(SweepArgs<R> a) {
       if (!sync(j, pc + 0)) return;
       row_phase(a, buf, tw, DEP_COMMIT, j + 1, u0, G, 1);
       if (!sync(j, pc + 1)) return;
-      col_phase_psi(a, buf, tw, u0, G, 1);
+      col_phase_psi(a, buf, tw, u0, G, 1, j + 1);
       if (!sync(j, pc + 2)) return;
       irow_phase(a, buf, tw, true, j + 1, false, 0.0, u0, G, 1);
       if (!sync(j, pc + 3)) return;
@@ -1073,7 +1105,7 @@ __global__ void __launch_bounds__(256, 2) solve_kernel(SweepArgs<R> a, int which
   } else {
     row_phase(a, buf, tw, DEP_COMMIT, 0, u0, G, 1);
     if (!grid_sync(a.bar, epoch)) return;
-    col_phase_psi(a, buf, tw, u0, G, 1);
+    col_phase_psi(a, buf, tw, u0, G, 1, -1);
     if (!grid_sync(a.bar, epoch)) return;
     irow_phase(a, buf, tw, true, 0, false, 0.0, u0, G, 1);
   }

@@ -53,6 +53,10 @@ class Mode(ct.Structure):
                 ("phase", ct.c_double)]
 
 
+class KVec(ct.Structure):
+    _fields_ = [("mx", ct.c_int32), ("my", ct.c_int32)]
+
+
 class ParamsC(ct.Structure):
     _fields_ = [("nx", ct.c_int32), ("ny", ct.c_int32), ("nxi", ct.c_int32),
                 ("ppc_plasma_x", ct.c_int32), ("ppc_plasma_y", ct.c_int32),
@@ -60,7 +64,8 @@ class ParamsC(ct.Structure):
                 ("n_pc_iter", ct.c_int32), ("pipeline_depth", ct.c_int32),
                 ("Lx", ct.c_double), ("Ly", ct.c_double), ("Lxi", ct.c_double),
                 ("dt", ct.c_double), ("psi_floor", ct.c_double), ("seed", ct.c_uint64),
-                ("spin_limit", ct.c_int64), ("species", Species * 4), ("modes", Mode * 16)]
+                ("spin_limit", ct.c_int64), ("species", Species * 4), ("modes", Mode * 16),
+                ("n_diag_modes", ct.c_int32), ("_pad", ct.c_int32), ("diag_modes", KVec * 16)]
 
 
 _DP = ct.POINTER(ct.c_double)
@@ -70,7 +75,8 @@ class Diag(ct.Structure):
     _fields_ = [("energy", _DP), ("psi0", _DP), ("ez0", _DP), ("jz_mean", _DP),
                 ("kappa2", _DP), ("opp_min", _DP), ("n_floor", _DP), ("invariant", _DP),
                 ("charge", _DP), ("pc_residual", _DP), ("beam_lost", ct.c_int64),
-                ("sweeps", ct.c_int64)]
+                ("sweeps", ct.c_int64), ("rms", _DP), ("seg_width", ct.c_double),
+                ("rms_seg", _DP), ("mode_amp", _DP), ("beam_moments", _DP)]
 
 
 ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_void_p)
@@ -152,6 +158,9 @@ def to_c_params(p: config.Params) -> ParamsC:
     for i, m in enumerate(p.modes):
         c.modes[i].mx, c.modes[i].my = m.mx, m.my
         c.modes[i].amplitude, c.modes[i].phase = m.amplitude, m.phase
+    c.n_diag_modes = len(p.diag_modes)
+    for i, (mx, my) in enumerate(p.diag_modes):
+        c.diag_modes[i].mx, c.diag_modes[i].my = mx, my
     return c
 
 
@@ -248,12 +257,21 @@ class QSA:
                                           ct.byref(nout)))
         return dict(zip(keys, arrs))
 
-    def diagnostics(self) -> dict:
-        nk = self.nk
+    def diagnostics(self, seg_width: float = 2.0) -> dict:
+        """Per-slice diagnostics of the last sweep (see qsa_diag).  Adds "beam_rms_u":
+        [species, xi cell, 3] weighted rms spread of u_x, u_y, u_z, and "beam_weight":
+        [species, xi cell] sum of w/wbar, both derived from the raw moment sums."""
+        nk, p = self.nk, self.p
         out = {k: np.zeros(nk) for k in ("psi0", "ez0", "jz_mean", "kappa2", "opp_min",
                                           "n_floor", "invariant", "charge", "pc_residual")}
         out["energy"] = np.zeros((nk, 6))
+        out["rms"] = np.zeros((nk, 6))
+        nseg = max(1, int(np.ceil(p.Lxi / seg_width - 1e-12)))
+        out["rms_seg"] = np.zeros((nseg, 6))
+        out["mode_amp"] = np.zeros((nk, max(len(p.diag_modes), 1), 5, 2))
+        out["beam_moments"] = np.zeros((max(len(p.species), 1), max(p.nxi, 1), 7))
         d = Diag()
+        d.seg_width = seg_width
         for k, v in out.items():
             setattr(d, k, _ptr(v))
         rc = self.lib.qsa_diagnostics(self.h, ct.byref(d))
@@ -261,6 +279,13 @@ class QSA:
         out["beam_lost"] = d.beam_lost
         out["sweeps"] = d.sweeps
         self._check(rc)
+        m = out["beam_moments"]
+        wsum = m[..., 0]
+        with np.errstate(invalid="ignore", divide="ignore"):
+            mean = m[..., 1:4] / wsum[..., None]
+            var = m[..., 4:7] / wsum[..., None] - mean ** 2
+        out["beam_weight"] = wsum
+        out["beam_rms_u"] = np.sqrt(np.maximum(var, 0.0))
         return out
 
     def field(self, f, j0=0, j1=None) -> np.ndarray:

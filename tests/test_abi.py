@@ -40,8 +40,10 @@ def test_struct_layout_matches_c():
 #include <stddef.h>
 #include "qsa.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(qsa_params), sizeof(qsa_species), sizeof(qsa_mode),
-         sizeof(qsa_diag), offsetof(qsa_params, species), offsetof(qsa_params, modes));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(qsa_params), sizeof(qsa_species),
+         sizeof(qsa_mode), sizeof(qsa_diag), offsetof(qsa_params, species),
+         offsetof(qsa_params, modes), offsetof(qsa_params, diag_modes),
+         offsetof(qsa_diag, seg_width), offsetof(qsa_diag, beam_moments));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -51,7 +53,9 @@ int main(void) {
         subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe])
         got = [int(v) for v in subprocess.check_output([exe]).split()]
     want = [ct.sizeof(qsa.ParamsC), ct.sizeof(qsa.Species), ct.sizeof(qsa.Mode),
-            ct.sizeof(qsa.Diag), qsa.ParamsC.species.offset, qsa.ParamsC.modes.offset]
+            ct.sizeof(qsa.Diag), qsa.ParamsC.species.offset, qsa.ParamsC.modes.offset,
+            qsa.ParamsC.diag_modes.offset, qsa.Diag.seg_width.offset,
+            qsa.Diag.beam_moments.offset]
     assert got == want
 
 
