@@ -213,6 +213,27 @@ int qsa_field_solve(qsa_handle* h, const double* S, const double* Jx, const doub
                     double* out);
 
 /* ---------------------------------------------------------------------------------------
+ * Linear spatiotemporal theory (Eq. 5), marched on the GPU for a batch of transverse modes:
+ * the procedure behind the growth curves of the paper's Fig. 1e.  For each mode m, Eq. 5 with
+ * growth rate Gamma_m (Gamma^2 = sum_s omega_bs^2 k^2/(k^2 + 1)) reads
+ *   (d_xi^2 + 1) d_tau^2 psi = Gamma_m^2 psi,
+ * with zero data ahead of the beam front (xi < 0).  So d_tau^2 psi(xi) =
+ * Gamma^2 int_0^xi sin(xi - xi') psi(xi') dxi', evaluated with the trapezoid rule on the grid
+ * xi_i = i dxi, i = 0..n_xi-1, and the state (psi, d_tau psi) advances by classical RK4 in tau
+ * with n_tau steps of tau_end / n_tau.  FP64 throughout.
+ * Arguments: gamma[n_modes]; psi0, dpsi0: psi and d_tau psi at tau = 0, [n_modes][n_xi];
+ * psi_out: [n_out][n_modes][n_xi], psi at tau = tau_end (o + 1) / n_out, o = 0..n_out-1
+ * (n_out must divide n_tau).  All host arrays (copied; device memory comes from
+ * cudaMallocAsync on `stream` and is released before the call returns).  Synchronises.
+ * Errors: QSA_ERR_ARG (n_modes < 1, n_xi outside 2..QSA_EQ5_MAX_XI, dxi <= 0, tau_end < 0,
+ * n_tau < 1, n_out not dividing n_tau, Gamma < 0, NULL array), QSA_ERR_CUDA; the message is
+ * in qsa_last_error(NULL). */
+#define QSA_EQ5_MAX_XI 2048
+int qsa_eq5_march(int32_t n_modes, int32_t n_xi, double dxi, const double* gamma,
+                  const double* psi0, const double* dpsi0, double tau_end, int32_t n_tau,
+                  int32_t n_out, double* psi_out, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Transverse field solve that allocates nothing.  The paper has no counterpart: this entry
  * point exists for callers that cannot call cudaMalloc (or any allocating routine) when they
  * need a solve, for instance a code whose own memory manager has already reserved the GPU's

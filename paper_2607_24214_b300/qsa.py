@@ -31,7 +31,8 @@ SOURCES = ("Sb", "Jz", "Jx", "Jy")
 EXPORTS = ("qsa_init", "qsa_set_beam", "qsa_get_beam", "qsa_plasma_sweep", "qsa_beam_step",
            "qsa_diagnostics", "qsa_copy_field", "qsa_copy_source", "qsa_field_solve",
            "qsa_phase_times", "qsa_launch_count", "qsa_device_bytes", "qsa_last_error",
-           "qsa_destroy", "qsa_field_solve_static", "qsa_advance", "qsa_launch_times")
+           "qsa_destroy", "qsa_field_solve_static", "qsa_advance", "qsa_launch_times",
+           "qsa_eq5_march")
 
 
 class QsaError(RuntimeError):
@@ -120,6 +121,9 @@ def load_library(path: str = LIB_PATH):
     lib.qsa_field_solve_static.argtypes = ([ct.c_int32, ct.c_int32, ct.c_double, ct.c_double,
                                             ct.c_double, ct.c_int32] + [P] * 8)
     lib.qsa_field_solve_static.restype = ct.c_int
+    lib.qsa_eq5_march.argtypes = ([ct.c_int32, ct.c_int32, ct.c_double] + [_DP] * 3 +
+                                  [ct.c_double, ct.c_int32, ct.c_int32, _DP, P])
+    lib.qsa_eq5_march.restype = ct.c_int
     lib.qsa_phase_times.argtypes = [P, ct.POINTER(ct.c_int64), ct.c_int]
     lib.qsa_phase_times.restype = ct.c_int
     lib.qsa_launch_count.argtypes = [P]
@@ -166,6 +170,24 @@ def to_c_params(p: config.Params) -> ParamsC:
 
 def _ptr(a):
     return a.ctypes.data_as(_DP)
+
+
+def eq5_march(gamma, psi0, dpsi0, dxi, tau_end, n_tau, n_out=1, stream=None):
+    """Eq. 5 marched on the GPU for a batch of modes (qsa_eq5_march): gamma [m], psi0 and
+    dpsi0 [m, n_xi] at tau = 0 on xi_i = i dxi.  Returns psi [n_out, m, n_xi] at
+    tau = tau_end (o + 1) / n_out."""
+    lib = load_library()
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    a = np.ascontiguousarray(psi0, dtype=np.float64)
+    b = np.ascontiguousarray(dpsi0, dtype=np.float64)
+    m, n = a.shape
+    out = np.empty((n_out, m, n))
+    strm = ct.c_void_p(stream.cuda_stream) if stream is not None else None
+    rc = lib.qsa_eq5_march(m, n, float(dxi), _ptr(g), _ptr(a), _ptr(b), float(tau_end),
+                           int(n_tau), int(n_out), _ptr(out), strm)
+    if rc != QSA_OK:
+        raise QsaError(rc, lib.qsa_last_error(None).decode())
+    return out
 
 
 class QSA:
