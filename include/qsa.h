@@ -183,10 +183,23 @@ int qsa_beam_step(qsa_handle* h);
  * the sources those of the next.  n_steps = 0 is a no-op.  Asynchronous. */
 int qsa_advance(qsa_handle* h, int32_t n_steps);
 
-/* Device time, in ms, of each persistent launch of the last pipelined qsa_advance call (CUDA
- * events recorded around the launches on the handle's stream; up to 64 launches): writes
- * min(cap, launches) values to ms and their number to *n_out.  0 values for a handle without
- * pipelining.  Synchronises with those events. */
+/* n_steps beam steps (sweep + push) of each of n_handles independent instances, which may
+ * differ in grid size, beam, box and every other parameter except precision, n_pc_iter and
+ * stream (the same for all; a handle may appear once).  Each step of up to 16 instances runs
+ * in one persistent launch whose phases cover the work of all of them (parameter scans over
+ * alpha and gamma_b).  The same result per instance as n_steps x (qsa_plasma_sweep;
+ * qsa_beam_step) on it, up to the summation order of the deposits.  The FFT work units (rows
+ * and half-spectrum columns per unit) are chosen by timing: with n_steps >= 8 and no earlier
+ * choice for handles[0], the first 4 steps run one candidate shape each (all compute the same
+ * steps) and the remaining steps use the fastest; the choice is kept in handles[0].  Device-
+ * side failures (timeouts) of these launches are latched in handles[0].  Uses handles[0]'s
+ * launch timing (qsa_launch_times).  Asynchronous, except during the timing steps. */
+int qsa_advance_batch(qsa_handle* const* handles, int32_t n_handles, int32_t n_steps);
+
+/* Device time, in ms, of each persistent launch of the last pipelined qsa_advance or
+ * qsa_advance_batch call led by h (CUDA events recorded around the launches on the handle's
+ * stream; up to 64 launches): writes min(cap, launches) values to ms and their number to
+ * *n_out.  0 values when there was none.  Synchronises with those events. */
 int qsa_launch_times(qsa_handle* h, float* ms, int cap, int* n_out);
 
 /* Copy the per-slice diagnostics of the last sweep into `out`; synchronises and returns the

@@ -122,6 +122,28 @@ def c3_pair_beam(ppc_xi: int = 1) -> Params:
                   precision="mixed", steps=400)
 
 
+def c4_parameter_scan(n: int = 64, seed: int = 0) -> List[Params]:
+    """Batched scan: n independent instances, transverse grids drawn uniformly from
+    {64, 96, 128, 192, 256}^2 (box N 2 pi / 32), 256 slices over 32, 4 ppc plasma; cold
+    electron beam, alpha log-uniform in [1e-3, 1e-1], gamma_b log-uniform in [10, 1e3], 4 ppc
+    (2x2x1), 1e-3 noise; dt = 0.1 / omega_b with omega_b = sqrt(alpha / gamma_b); 50 steps;
+    mixed precision.  Instance i draws from Random(seed + i) and uses seed + i for its beam."""
+    import random
+    out = []
+    for i in range(n):
+        rng = random.Random(seed + i)
+        N = rng.choice((64, 96, 128, 192, 256))
+        alpha = 10 ** rng.uniform(-3, -1)
+        gamma_b = 10 ** rng.uniform(1, 3)
+        L = N * DX_DEFAULT
+        out.append(Params(nx=N, ny=N, nxi=256, Lx=L, Ly=L, Lxi=32.0,
+                          dt=0.1 / math.sqrt(alpha / gamma_b),
+                          species=[Species(Z=-1, M=1, alpha=alpha, gamma_b=gamma_b, ppc_x=2,
+                                           ppc_y=2, ppc_xi=1, noise_rel=1e-3)],
+                          precision="mixed", steps=50, seed=seed + i))
+    return out
+
+
 def c5_seeded_modes(seed: int = 0) -> Params:
     """128x128 (box 8 pi), 256 slices over 32, electron beam alpha 1e-2, gamma_b 500, 8 ppc,
     16 seeded modes of amplitude 1e-3 (lowest |k| of the half plane, phases from the seed)."""

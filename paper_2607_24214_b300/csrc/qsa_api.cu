@@ -143,9 +143,8 @@ struct State {
   std::vector<int*> cmaxs;          // extent ring, S + 1 entries [nxi]
   std::vector<double*> moms;        // beam-moment ring, S + 1 entries [n_species][nxi][7]
   int* dmin = nullptr;              // min over live particles of (xi cell - home layer)
-  PipeTable<R>* ptab = nullptr;     // device copy of the pipeline table
-  int pipe_grid = 0;
-  size_t pipe_smem = 0;
+  PipeTable<R>* ptab = nullptr;     // device table of the multi-slot launches (lazy)
+  int tuned_nbr = 0, tuned_nbc = 0; // FFT units chosen by the batch autotuner (0: not yet)
   unsigned long long* lost = nullptr;
   unsigned* bar = nullptr;  // [0] count, [1] generation
   int* status = nullptr;
@@ -261,14 +260,10 @@ int setup(qsa_handle* h) {
   CK(cudaMemsetAsync(s->dmin, 0, sizeof(int), h->stream));
   // launch shapes of the persistent kernels
   const size_t smem = sweep_smem<R>(dp);
-  CK(cudaFuncSetAttribute(sweep_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)smem));
-  CK(cudaFuncSetAttribute(solve_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)smem));
-  CK(cudaFuncSetAttribute(beam_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)beam_smem_bytes<R>(dp.nx)));
-  CK(cudaFuncSetAttribute(beam_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)beam_smem_bytes<R>(dp.nx)));
+  CK(raise_dyn_smem((const void*)sweep_kernel<R>, smem));
+  CK(raise_dyn_smem((const void*)solve_kernel<R>, smem));
+  CK(raise_dyn_smem((const void*)beam_kernel<R, false>, beam_smem_bytes<R>(dp.nx)));
+  CK(raise_dyn_smem((const void*)beam_kernel<R, true>, beam_smem_bytes<R>(dp.nx)));
   int per_sm = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<R>, kThreads, smem));
   int per_sm2 = 0;
@@ -278,18 +273,10 @@ int setup(qsa_handle* h) {
   const int work = dp.ny > dp.nxh ? dp.ny : dp.nxh;
   int grid = per_sm * h->num_sms;
   if (grid > work) grid = work;
-  int dgrid = grid;  // blocks whose diagnostic partials a slot holds
-  if (nslot > 1) {
-    s->pipe_smem = pipe_smem_bytes<R>(dp.nx, dp.ny);
-    CK(cudaFuncSetAttribute(pipe_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)s->pipe_smem));
-    int per_sm3 = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, pipe_kernel<R>, kThreads,
-                                                     s->pipe_smem));
-    if (per_sm3 < 1) return fail(h, QSA_ERR_ARG, "pipelined kernel does not fit on an SM");
-    s->pipe_grid = per_sm3 * h->num_sms;
-    if (s->pipe_grid > dgrid) dgrid = s->pipe_grid;
-  }
+  // blocks whose diagnostic partials a slot holds: the single sweep's grid, or a multi-slot
+  // launch's (its register budget allows kPipeBlocksPerSM resident blocks per SM at most)
+  int dgrid = grid;
+  if (kPipeBlocksPerSM * h->num_sms > dgrid) dgrid = kPipeBlocksPerSM * h->num_sms;
   // sweep slots
   s->slots.resize(nslot);
   for (int i = 0; i < nslot; ++i) {
@@ -405,29 +392,6 @@ int setup(qsa_handle* h) {
   }
   CK(cudaMemcpyAsync(bref, s->bref_jz.data(), dp.nk * sizeof(double), cudaMemcpyHostToDevice,
                      h->stream));
-  // the pipeline table, on the device once
-  if (nslot > 1) {
-    PipeTable<R> t{};
-    for (int i = 0; i < nslot; ++i) t.st[i] = s->slots[i];
-    for (int i = 0; i <= nslot; ++i) {
-      t.srcbuf[i] = s->srcs[i];
-      t.cmaxbuf[i] = s->cmaxs[i];
-      t.mombuf[i] = s->moms[i];
-    }
-    t.nslot = nslot;
-    t.nspecies = (int)s->species.size();
-    t.max_push = 2;
-    for (int si = 0; si < t.nspecies; ++si) {
-      t.beam[si] = s->beams[si];
-      t.sp[si] = s->species[si];
-      t.bc[si] = s->bconst[si];
-    }
-    t.dmin = s->dmin;
-    t.lost = s->lost;
-    if (!(s->ptab = (PipeTable<R>*)A(sizeof(PipeTable<R>))))
-      return fail(h, QSA_ERR_OOM, "pipeline table");
-    CK(cudaMemcpyAsync(s->ptab, &t, sizeof(t), cudaMemcpyHostToDevice, h->stream));
-  }
   CK(cudaStreamSynchronize(h->stream));
   return QSA_OK;
 }
@@ -526,6 +490,91 @@ int sweep(qsa_handle* h) {
   return QSA_OK;
 }
 
+// ---- multi-slot launches (chained steps of one handle, or one step of several handles)
+
+// The beam side of a slot whose beam state has had `pushes` pushes.
+template <typename R>
+PipeSlot<R> make_slot(qsa_handle* h, int64_t pushes) {
+  State<R>* s = S<R>(h);
+  PipeSlot<R> ps{};
+  ps.src_next = ring_src<R>(h, pushes + 1);
+  ps.cmax_in = ring_cmax<R>(h, pushes);
+  ps.cmax_out = ring_cmax<R>(h, pushes + 1);
+  ps.mom_out = ring_mom<R>(h, pushes + 1);
+  ps.dmin = s->dmin;
+  ps.lost = s->lost;
+  ps.nspecies = (int)s->species.size();
+  for (int si = 0; si < ps.nspecies; ++si) {
+    ps.beam[si] = s->beams[si];
+    ps.sp[si] = s->species[si];
+    ps.bc[si] = s->bconst[si];
+  }
+  return ps;
+}
+
+// Zero what slot `a` of handle h starts from: the next sources and ring entries, the sweep
+// scratch that must start at zero, the diagnostics.
+template <typename R>
+int prepare_slot(qsa_handle* h, SweepArgs<R>& a, int64_t pushes) {
+  const DevParams& dp = h->dp;
+  const size_t g = (size_t)dp.nx * dp.ny, spec = (size_t)dp.nxh * dp.ny;
+  CK(cudaMemsetAsync(ring_src<R>(h, pushes + 1), 0, (size_t)dp.nk * g * 4 * sizeof(R),
+                     h->stream));
+  if (int rc = clear_ring<R>(h, pushes + 1)) return rc;
+  CK(cudaMemsetAsync(a.ovf, 0, g * kNF * sizeof(R), h->stream));
+  CK(cudaMemsetAsync(a.odirty, 0, (size_t)dp.ny * sizeof(int), h->stream));
+  CK(cudaMemsetAsync(a.bold, 0, 2 * spec * sizeof(C<R>), h->stream));
+  CK(cudaMemsetAsync(a.fg, 0, g * kFG * sizeof(R), h->stream));
+  const int nd = D_COUNT * dp.nk;
+  diag_init_kernel<<<(nd + 255) / 256, 256, 0, h->stream>>>(a.diag, dp.nk);
+  ++h->launches;
+  return QSA_OK;
+}
+
+// Upload table t (nslots slots, FFT units nbr x nbc) to the lead handle's device table and
+// launch the multi-slot kernel on the lead's stream, timed with the lead's events.  Returns
+// the grid in *grid_out (the diagnostic partials of every slot span it).
+template <typename R>
+int launch_slots(qsa_handle* lead, PipeTable<R>& t, int nslots, int nbr, int nbc,
+                 int* grid_out) {
+  qsa_handle* h = lead;
+  State<R>* s = S<R>(h);
+  t.nbr = nbr;
+  t.nbc = nbc;
+  t.max_push = 2;
+  t.nx_max = t.ny_max = 1;
+  for (int i = 0; i < nslots; ++i) {
+    t.nx_max = std::max(t.nx_max, t.st[i].p.nx);
+    t.ny_max = std::max(t.ny_max, t.st[i].p.ny);
+  }
+  const size_t smem = pipe_smem_bytes<R>(t.nx_max, t.ny_max, nbr, nbc);
+  CK(raise_dyn_smem((const void*)pipe_kernel<R>, smem));
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pipe_kernel<R>, kThreads, smem));
+  if (per_sm < 1) return fail(h, QSA_ERR_ARG, "multi-slot kernel does not fit on an SM");
+  int grid = std::min(per_sm, kPipeBlocksPerSM) * h->num_sms;
+  if (!h->ev[0])
+    for (int i = 0; i < 2 * qsa_handle::kLaunchEvents; ++i) CK(cudaEventCreate(&h->ev[i]));
+  if (!s->ptab && !(s->ptab = (PipeTable<R>*)dalloc(h, sizeof(PipeTable<R>))))
+    return fail(h, QSA_ERR_OOM, "slot table");
+  // pageable source: the call returns once t is staged, so t may change right after
+  CK(cudaMemcpyAsync(s->ptab, &t, sizeof(PipeTable<R>), cudaMemcpyHostToDevice, h->stream));
+  Barrier bar = s->slots[0].bar;
+  CK(cudaMemsetAsync(bar.count, 0, sizeof(unsigned), h->stream));
+  const int ti = h->n_timed < qsa_handle::kLaunchEvents ? h->n_timed++ : -1;
+  if (ti >= 0) CK(cudaEventRecord(h->ev[2 * ti], h->stream));
+  const PipeTable<R>* tab = s->ptab;
+  void* args[] = {&tab, &nslots, &bar};
+  CK(cudaLaunchCooperativeKernel((void*)pipe_kernel<R>, dim3(grid), dim3(kThreads), args, smem,
+                                 h->stream));
+  ++h->launches;
+  if (ti >= 0) CK(cudaEventRecord(h->ev[2 * ti + 1], h->stream));
+  *grid_out = grid;
+  return QSA_OK;
+}
+
+constexpr int kPipeRowBatch = 2, kPipeColBatch = 1;  // FFT units of the chained launches
+
 // n beam steps (sweep + push each) as wavefronts of up to S steps per persistent launch.
 template <typename R>
 int advance_pipelined(qsa_handle* h, int n) {
@@ -536,40 +585,23 @@ int advance_pipelined(qsa_handle* h, int n) {
     int rc = deposit_sources<R>(h);
     if (rc) return rc;
   }
-  const size_t g = (size_t)dp.nx * dp.ny;
-  const size_t spec = (size_t)dp.nxh * dp.ny;
-  const int nd = D_COUNT * dp.nk;
+  std::vector<PipeTable<R>> tv(1);  // ~30 KB: on the heap
+  PipeTable<R>& t = tv[0];
   while (n > 0) {
     const int m = n < nslot ? n : nslot;
-    for (int i = 1; i <= m; ++i) {
-      CK(cudaMemsetAsync(ring_src<R>(h, h->pushes + i), 0, (size_t)dp.nk * g * 4 * sizeof(R),
-                         h->stream));
-      if (int rc = clear_ring<R>(h, h->pushes + i)) return rc;
+    t = PipeTable<R>{};
+    t.chained = 1;
+    for (int i = 0; i < m; ++i) {
+      if (int rc = prepare_slot<R>(h, s->slots[i], h->pushes + i)) return rc;
+      t.st[i] = s->slots[i];
+      t.st[i].src = ring_src<R>(h, h->pushes + i);
+      t.slot[i] = make_slot<R>(h, h->pushes + i);
     }
+    int grid = 0;
+    if (int rc = launch_slots<R>(h, t, m, kPipeRowBatch, kPipeColBatch, &grid)) return rc;
     for (int i = 0; i < m; ++i) {
       SweepArgs<R>& a = s->slots[i];
-      CK(cudaMemsetAsync(a.ovf, 0, g * kNF * sizeof(R), h->stream));
-      CK(cudaMemsetAsync(a.odirty, 0, (size_t)dp.ny * sizeof(int), h->stream));
-      CK(cudaMemsetAsync(a.bold, 0, 2 * spec * sizeof(C<R>), h->stream));
-      CK(cudaMemsetAsync(a.fg, 0, g * kFG * sizeof(R), h->stream));
-      diag_init_kernel<<<(nd + 255) / 256, 256, 0, h->stream>>>(a.diag, dp.nk);
-      ++h->launches;
-    }
-    Barrier bar = s->slots[0].bar;
-    CK(cudaMemsetAsync(bar.count, 0, sizeof(unsigned), h->stream));
-    const int ti = h->n_timed < qsa_handle::kLaunchEvents ? h->n_timed++ : -1;
-    if (ti >= 0) CK(cudaEventRecord(h->ev[2 * ti], h->stream));
-    const PipeTable<R>* tab = s->ptab;
-    int r0 = (int)(h->pushes % (int64_t)(nslot + 1));
-    int steps = m;
-    void* args[] = {&tab, &r0, &steps, &bar};
-    CK(cudaLaunchCooperativeKernel((void*)pipe_kernel<R>, dim3(s->pipe_grid), dim3(kThreads),
-                                   args, s->pipe_smem, h->stream));
-    ++h->launches;
-    if (ti >= 0) CK(cudaEventRecord(h->ev[2 * ti + 1], h->stream));
-    for (int i = 0; i < m; ++i) {
-      SweepArgs<R>& a = s->slots[i];
-      diag_reduce_kernel<<<dp.nk, 256, 0, h->stream>>>(a.dpart, s->pipe_grid, a.diag, dp.nk);
+      diag_reduce_kernel<<<dp.nk, 256, 0, h->stream>>>(a.dpart, grid, a.diag, dp.nk);
       ++h->launches;
     }
     h->pushes += m;
@@ -578,6 +610,83 @@ int advance_pipelined(qsa_handle* h, int n) {
     n -= m;
   }
   h->src_valid = true;
+  return QSA_OK;
+}
+
+// FFT unit shapes the batch autotuner tries (rows x half-spectrum columns per unit).
+constexpr int kTuneShapes[4][2] = {{2, 1}, {1, 1}, {4, 1}, {2, 2}};
+
+// n_steps steps of every handle, each launch advancing up to kMaxPipe handles by one step.
+// With n_steps >= 2 x (shapes) and no earlier choice, the first steps time each FFT unit
+// shape on the real work (every shape computes the same steps) and the rest use the fastest.
+template <typename R>
+int advance_batch(qsa_handle* const* hs, int nh, int n_steps) {
+  qsa_handle* lead = hs[0];
+  State<R>* ls = S<R>(lead);
+  // a failure in a call made for another handle is reported through the lead
+  auto relay = [&](int rc, int i) {
+    if (hs[i] != lead) lead->err = "instance " + std::to_string(i) + ": " + hs[i]->err;
+    return rc;
+  };
+  for (int i = 0; i < nh; ++i)
+    if (!hs[i]->src_valid)
+      if (int rc = deposit_sources<R>(hs[i])) return relay(rc, i);
+  std::vector<PipeTable<R>> tv(1);
+  PipeTable<R>& t = tv[0];
+  const int nshape = 4;
+  const bool tune = ls->tuned_nbr == 0 && n_steps >= 2 * nshape;
+  std::vector<float> shape_ms(nshape, 0.f);
+  for (int step = 0; step < n_steps; ++step) {
+    int nbr = ls->tuned_nbr ? ls->tuned_nbr : kPipeRowBatch;
+    int nbc = ls->tuned_nbc ? ls->tuned_nbc : kPipeColBatch;
+    if (tune && step < nshape) {
+      nbr = kTuneShapes[step][0];
+      nbc = kTuneShapes[step][1];
+      lead->n_timed = 0;
+    }
+    for (int c0 = 0; c0 < nh; c0 += kMaxPipe) {
+      const int m = std::min(kMaxPipe, nh - c0);
+      t = PipeTable<R>{};
+      t.chained = 0;
+      for (int i = 0; i < m; ++i) {
+        qsa_handle* h = hs[c0 + i];
+        SweepArgs<R>& a = S<R>(h)->slots[0];
+        if (int rc = prepare_slot<R>(h, a, h->pushes)) return relay(rc, c0 + i);
+        t.st[i] = a;
+        t.st[i].src = ring_src<R>(h, h->pushes);
+        t.slot[i] = make_slot<R>(h, h->pushes);
+      }
+      int grid = 0;
+      if (int rc = launch_slots<R>(lead, t, m, nbr, nbc, &grid)) return rc;
+      for (int i = 0; i < m; ++i) {
+        qsa_handle* h = hs[c0 + i];
+        SweepArgs<R>& a = S<R>(h)->slots[0];
+        diag_reduce_kernel<<<h->dp.nk, 256, 0, h->stream>>>(a.dpart, grid, a.diag, h->dp.nk);
+        ++h->launches;
+        h->pushes += 1;
+        h->sweeps += 1;
+        S<R>(h)->last_slot = 0;
+        h->src_valid = true;
+      }
+    }
+    if (tune && step < nshape) {
+      qsa_handle* h = lead;  // error reporting of CK
+      float tot = 0.f, ms = 0.f;
+      for (int i = 0; i < lead->n_timed; ++i) {
+        CK(cudaEventSynchronize(lead->ev[2 * i + 1]));
+        CK(cudaEventElapsedTime(&ms, lead->ev[2 * i], lead->ev[2 * i + 1]));
+        tot += ms;
+      }
+      shape_ms[step] = tot;
+      if (step == nshape - 1) {
+        int best = 0;
+        for (int k = 1; k < nshape; ++k)
+          if (shape_ms[k] < shape_ms[best]) best = k;
+        ls->tuned_nbr = kTuneShapes[best][0];
+        ls->tuned_nbc = kTuneShapes[best][1];
+      }
+    }
+  }
   return QSA_OK;
 }
 
@@ -921,8 +1030,6 @@ int qsa_init(const qsa_params* params, void* stream, qsa_alloc_fn alloc, qsa_fre
     dp.mconj[m] = k.mx < 0 ? 1 : 0;
   }
   h->fp64 = params->precision == QSA_FP64;
-  if (params->pipeline_depth > 1)
-    for (int i = 0; i < 2 * qsa_handle::kLaunchEvents; ++i) cudaEventCreate(&h->ev[i]);
   const size_t smem = h->fp64 ? sweep_smem<double>(dp) : sweep_smem<float>(dp);
   int max_smem = 0;
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -996,6 +1103,25 @@ int qsa_advance(qsa_handle* h, int32_t n_steps) {
     if (rc) return rc;
   }
   return QSA_OK;
+}
+
+int qsa_advance_batch(qsa_handle* const* handles, int32_t n_handles, int32_t n_steps) {
+  if (!handles || n_handles < 1) return fail(nullptr, QSA_ERR_ARG, "no handles");
+  qsa_handle* lead = handles[0];
+  if (!lead) return fail(nullptr, QSA_ERR_ARG, "NULL handle");
+  if (n_steps < 0) return fail(lead, QSA_ERR_ARG, "n_steps must be >= 0");
+  for (int i = 0; i < n_handles; ++i) {
+    const qsa_handle* h = handles[i];
+    if (!h) return fail(lead, QSA_ERR_ARG, "NULL handle");
+    if (h->fp64 != lead->fp64) return fail(lead, QSA_ERR_ARG, "handles differ in precision");
+    if (h->stream != lead->stream) return fail(lead, QSA_ERR_ARG, "handles differ in stream");
+    if (h->dp.n_pc != lead->dp.n_pc) return fail(lead, QSA_ERR_ARG, "handles differ in n_pc_iter");
+    for (int k = 0; k < i; ++k)
+      if (handles[k] == h) return fail(lead, QSA_ERR_ARG, "a handle appears twice");
+  }
+  lead->n_timed = 0;
+  return lead->fp64 ? advance_batch<double>(handles, n_handles, n_steps)
+                    : advance_batch<float>(handles, n_handles, n_steps);
 }
 
 int qsa_diagnostics(qsa_handle* h, qsa_diag* out) {

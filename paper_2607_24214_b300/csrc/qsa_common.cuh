@@ -2,6 +2,11 @@
 // barrier, block reductions, float/double atomics and the Philox-4x32-10 generator.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <utility>
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace qsa {
@@ -58,6 +63,23 @@ struct DevParams {
   int nmodes;
   int mkx[16], mky[16], mconj[16];
 };
+
+// The largest dynamic shared memory a kernel may use is a setting of the function on the
+// device, shared by every handle and call in the process: raise it when a launch needs more,
+// never lower it (a smaller handle created later must not break a larger one's launches).
+inline cudaError_t raise_dyn_smem(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = done[std::make_pair(fn, dev)];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 
 // ---------------------------------------------------------------------------------------
 // Grid-wide barrier for a cooperative launch.  Every wait is bounded by spin_limit polls,

@@ -136,8 +136,7 @@ int solve_static(int nx, int ny, double Lx, double Ly, double kappa2, const R* S
   const size_t g = (size_t)nx * ny, spec = (size_t)dp.nxh * ny;
   const size_t smem = sweep_smem_bytes<R>(nx, ny);
   int per_sm = 0, sms = 0;
-  if (cudaFuncSetAttribute(solve_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess ||
+  if (raise_dyn_smem((const void*)solve_kernel<R>, smem) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<R>, kThreadsS, smem) !=
           cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

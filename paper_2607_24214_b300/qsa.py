@@ -32,7 +32,7 @@ EXPORTS = ("qsa_init", "qsa_set_beam", "qsa_get_beam", "qsa_plasma_sweep", "qsa_
            "qsa_diagnostics", "qsa_copy_field", "qsa_copy_source", "qsa_field_solve",
            "qsa_phase_times", "qsa_launch_count", "qsa_device_bytes", "qsa_last_error",
            "qsa_destroy", "qsa_field_solve_static", "qsa_advance", "qsa_launch_times",
-           "qsa_eq5_march")
+           "qsa_eq5_march", "qsa_advance_batch")
 
 
 class QsaError(RuntimeError):
@@ -107,6 +107,8 @@ def load_library(path: str = LIB_PATH):
         getattr(lib, name).restype = ct.c_int
     lib.qsa_advance.argtypes = [P, ct.c_int32]
     lib.qsa_advance.restype = ct.c_int
+    lib.qsa_advance_batch.argtypes = [ct.POINTER(P), ct.c_int32, ct.c_int32]
+    lib.qsa_advance_batch.restype = ct.c_int
     lib.qsa_launch_times.argtypes = [P, ct.POINTER(ct.c_float), ct.c_int,
                                      ct.POINTER(ct.c_int)]
     lib.qsa_launch_times.restype = ct.c_int
@@ -188,6 +190,17 @@ def eq5_march(gamma, psi0, dpsi0, dxi, tau_end, n_tau, n_out=1, stream=None):
     if rc != QSA_OK:
         raise QsaError(rc, lib.qsa_last_error(None).decode())
     return out
+
+
+def advance_batch(instances, n_steps: int):
+    """n_steps beam steps of every QSA instance (same precision, n_pc_iter and stream), up to
+    16 instances per persistent launch (qsa_advance_batch)."""
+    lib = load_library()
+    arr = (ct.c_void_p * len(instances))(*[q.h for q in instances])
+    rc = lib.qsa_advance_batch(arr, len(instances), int(n_steps))
+    if rc < 0:
+        raise QsaError(rc, lib.qsa_last_error(instances[0].h if instances else None).decode())
+    return rc
 
 
 class QSA:
