@@ -247,6 +247,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=4,
+                    help="timed steps of the batched C4 scan (after 8 untimed, autotuning)")
     ap.add_argument("--steps-ref", type=int, default=2)
     ap.add_argument("--ref-slices", type=int, default=CPU_SAMPLE_SLICES,
                     help="slices of the oracle sample per reference step")
@@ -350,6 +353,9 @@ def main():
     if not args.no_e2e:
         line["e2e"] = e2e(p, args.e2e_steps, torch, stream)
 
+    if not args.no_batch:
+        line["batched"] = batched(args.batch_steps, torch, stream)
+
     if rank == 0 and not args.no_cpu:
         v, dt = cpu_baseline(p)
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
@@ -360,6 +366,34 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def batched(steps, torch, stream):
+    """The batched parameter scan (64 instances of uneven grids, qsa_advance_batch): 8 untimed
+    steps (the first four time the FFT unit shapes), then `steps` timed steps of all
+    instances.  Same metric: plasma particle-slice updates of all instances per second."""
+    from paper_2607_24214_b300.qsa import QSA, advance_batch
+    ps = config.c4_parameter_scan()
+    qs = [QSA(pi) for pi in ps]
+    advance_batch(qs, 8)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    advance_batch(qs, steps)
+    t1.record(stream)
+    t1.synchronize()
+    ms = t0.elapsed_time(t1)
+    status = min(q.diagnostics()["status"] for q in qs)
+    for q in qs:
+        q.close()
+    del qs
+    torch.cuda.empty_cache()
+    ups = sum(updates_per_step(pi) for pi in ps)
+    return {"workload": "c4_parameter_scan_64", "value": ups * steps / (ms * 1e-3),
+            "unit": "updates/s", "instances": len(ps), "steps": steps,
+            "ms_per_step": ms / steps, "grids": sorted({pi.nx for pi in ps}),
+            "status": status}
 
 
 def e2e(p, steps, torch, stream):

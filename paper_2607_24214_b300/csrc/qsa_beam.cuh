@@ -457,9 +457,11 @@ __device__ __forceinline__ float uz_dev(float2 uz, const BeamConst<float>& c) {
 // every live particle by dt through the slab, drop those with xi >= Lxi, and deposit the
 // sources of the next sweep.  Called by every thread of the block; tile holds
 // beam_smem_bytes(nx).
+// The descriptors b, sp, bc come by value: the particle loop then reads them from registers,
+// not again after each store through memory the compiler cannot prove distinct.
 template <typename BR, bool PUSH>
-__device__ void beam_group(const BeamArrays<BR>& b, const DevParams& p, const SpeciesDev& sp,
-                           const BeamConst<BR>& bc, const BR* __restrict__ slab, BR* src,
+__device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const SpeciesDev sp,
+                           const BeamConst<BR> bc, const BR* __restrict__ slab, BR* src,
                            unsigned long long* lost, Extent ext, int grp, BR* tile) {
   using UZ = typename UzT<BR>::T;
   __shared__ int s_ext[2];

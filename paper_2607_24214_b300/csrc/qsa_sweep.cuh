@@ -376,6 +376,16 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
   R kap = R(0), inv = R(0), omin = R(1e30), nfloor = R(0);
   __shared__ double red[32];
   __shared__ int s_flag;
+  if (u0 >= ny) {  // no unit in this block: identity partials, no reductions
+    if (threadIdx.x == 0 && mode == DEP_TRIAL) {
+      if (first) {
+        *pslot(a.dpart, j, P_OPPMIN) = 1e30;
+        *pslot(a.dpart, j, P_NFLOOR) = 0.0;
+      }
+      if (last) *pslot(a.dpart, j, P_INV) = 0.0;
+    }
+    return;
+  }
   const DepFlags fl{&s_flag, a.odirty};
   R* __restrict__ pox = a.pox;
   R* __restrict__ poy = a.poy;
@@ -634,6 +644,10 @@ __device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, 
   R* __restrict__ ovf = a.ovf;
   const R* __restrict__ src = a.src;
   __shared__ double red[32];
+  if (u0 * nb >= ny) {  // no unit in this block
+    if (threadIdx.x == 0 && mode != DEP_TRIAL) *pslot(a.dpart, jj, P_CHARGE) = 0.0;
+    return;
+  }
   R charge = R(0);
   load_tw(tw, a.twx, nx);
   const int k0 = (mode == DEP_TRIAL) ? jj : jj - 1;  // beam-source nodes k0, k0 + 1
@@ -774,6 +788,13 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
   C<R>* A = buf;
   C<R>* B = buf + kNF * ny * nb;
   __shared__ R s_kap;
+  if (u0 * nb >= nxh) {  // no unit in this block
+    if (threadIdx.x == 0 && last) {
+      *pslot(a.dpart, j, P_PCNUM) = 0.0;
+      *pslot(a.dpart, j, P_PCDEN) = 0.0;
+    }
+    return;
+  }
   if (threadIdx.x == 0) s_kap = R(a.diag[D_KAPPA * p.nk + j]) * a.k.inv_npc;
   const R rdxi = a.k.rdxi;
   const C<R>* __restrict__ rspec = a.rspec;
@@ -871,6 +892,7 @@ __device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int u0
   C<R>* A = buf;
   C<R>* B = buf + kNF * ny * nb;
   const C<R>* __restrict__ rspec = a.rspec;
+  if (u0 * nb >= nxh) return;  // no unit in this block
   load_tw(tw, a.twy, ny);
   for (int u = u0; u * nb < nxh; u += G) {
     const int kb = u * nb, nc = min(nb, nxh - kb);
@@ -930,6 +952,11 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
   const C<R>* __restrict__ cspec = a.cspec;
   R* __restrict__ fg = a.fg;
   __shared__ double red[64];
+  if (u0 * nb >= ny) {  // no unit in this block
+    if (threadIdx.x == 0 && !psi_mode && last)
+      for (int f = 0; f < 6; ++f) *pslot(a.dpart, j, P_E0 + f) = 0.0;
+    return;
+  }
   R en[6] = {0, 0, 0, 0, 0, 0};
   bool bad = false;
   load_tw(tw, a.twx, nx);
