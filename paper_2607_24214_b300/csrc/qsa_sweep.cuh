@@ -195,6 +195,30 @@ __device__ __forceinline__ void gather8(const R* __restrict__ fg, const Cic<R>& 
     out[k] = gy * (gx * a[k] + c.fx * b[k]) + c.fy * (gx * d[k] + c.fx * e[k]);
 }
 
+// The same gather for the two particles of a thread when both sit in their home cell
+// (column ix, row iy; x1, y1 the next ones): the four corner nodes are loaded once.
+template <typename R>
+__device__ __forceinline__ void gather8_pair(const R* __restrict__ fg, int ix, int x1, int iy,
+                                             int y1, int nx, const Cic<R> (&c)[2],
+                                             R (&out)[2][8]) {
+  R a[8], b[8], d[8], e[8];
+  const R* pa = fg + ((size_t)iy * nx + ix) * kFG;
+  const R* pb = fg + ((size_t)iy * nx + x1) * kFG;
+  const R* pd = fg + ((size_t)y1 * nx + ix) * kFG;
+  const R* pe = fg + ((size_t)y1 * nx + x1) * kFG;
+  ld4(pa, a); ld4(pa + 4, a + 4);
+  ld4(pb, b); ld4(pb + 4, b + 4);
+  ld4(pd, d); ld4(pd + 4, d + 4);
+  ld4(pe, e); ld4(pe + 4, e + 4);
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const R gx = R(1) - c[u].fx, gy = R(1) - c[u].fy;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      out[u][k] = gy * (gx * a[k] + c[u].fx * b[k]) + c[u].fy * (gx * d[k] + c[u].fx * e[k]);
+  }
+}
+
 // Deposit v (already a density) at the four corners into the field-major tile [nf][4][nx],
 // or into the overflow grid [kNF][ny][nx] when the rows fall outside the tile.
 // Deposits outside the two home rows of the tile are rare (a particle that left its home
@@ -434,10 +458,25 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
             uys[u] = puy[ii[u]];
             pprev[u] = pps[ii[u]];
           }
+          bool pair_home = true;
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            c[u] = cic<R>(ix, crow, hx[u] + ox[u], hy[u] + oy[u], nx, ny, crow);
-            gather8(a.fg, c[u], nx, F[u]);
+            const R lx = hx[u] + ox[u], ly = hy[u] + oy[u];
+            if (ok[u]) pair_home = pair_home && lx >= R(0) && lx < R(1) && ly >= R(0) && ly < R(1);
+          }
+          if (pair_home) {
+            // both in the home cell: shared corners (ix, crow) .. (ix + 1, crow + 1)
+            const int gx1 = (ix + 1 == nx) ? 0 : ix + 1, gy1 = (crow + 1 == ny) ? 0 : crow + 1;
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+              c[u] = Cic<R>{ix, gx1, crow, gy1, 1, hx[u] + ox[u], hy[u] + oy[u]};
+            gather8_pair(a.fg, ix, gx1, crow, gy1, nx, c, F);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              c[u] = cic<R>(ix, crow, hx[u] + ox[u], hy[u] + oy[u], nx, ny, crow);
+              gather8(a.fg, c[u], nx, F[u]);
+            }
           }
           // arithmetic of both particles; their deposit values are kept for the deposit step
           bool home[2] = {false, false}, homeh[2] = {false, false};
@@ -597,7 +636,16 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
     }
     __syncthreads();
     R* dst = a.part + (size_t)crow * tile_elems;
-    for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) dst[e] = tile[e];
+    {
+      // the outer tile rows go out only when a deposit landed there (the row phase reads
+      // them only then)
+      const int fl = s_flag;
+      for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
+        const int r = (e / nx) & (kTileRows - 1);
+        if ((r == 0 && !(fl & 1)) || (r == kTileRows - 1 && !(fl & 2))) continue;
+        dst[e] = tile[e];
+      }
+    }
     if (threadIdx.x == 0) a.cflag[crow] = s_flag;
     __syncthreads();
   }
