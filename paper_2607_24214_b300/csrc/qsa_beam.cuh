@@ -67,6 +67,7 @@ struct BeamConst {
   BR refS, refJz;    // reference source weights qbar omvbar, qbar (1 - omvbar)
   BR qb, omvbar;     // qbar, 1 - v_z of the reference momentum
   BR uzb_hi, uzb_lo; // sqrt(gamma_b^2 - 1) as a (leading, trailing) pair (trailing 0 in FP64)
+  BR inv_ppx, inv_ppy, inv_ppxi;  // 1 / sub-lattice counts
 };
 template <typename BR>
 inline BeamConst<BR> beam_consts(const DevParams& p, const SpeciesDev& sp) {
@@ -82,6 +83,9 @@ inline BeamConst<BR> beam_consts(const DevParams& p, const SpeciesDev& sp) {
   const double uzb = std::sqrt(sp.gamma_b * sp.gamma_b - 1.0);
   c.uzb_hi = BR(uzb);
   c.uzb_lo = BR(uzb - (double)c.uzb_hi);
+  c.inv_ppx = BR(1.0 / sp.ppx);
+  c.inv_ppy = BR(1.0 / sp.ppy);
+  c.inv_ppxi = BR(1.0 / sp.ppxi);
   return c;
 }
 
@@ -252,6 +256,11 @@ __device__ __forceinline__ void deposit_particle(const Group<BR>& g, BR* src, co
   }
 }
 
+// FP32 quotient and square root through the hardware approximations (about 2 ulp): the mixed
+// path's beam arithmetic carries errors far below its 1e-4 field tolerance.
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float fast_sqrt(float x) { return x * rsqrtf(x); }  // x > 0
+
 // Source deviations of one particle with q = qbar (1 + dw): dS = q(1 - v_z) - qbar omvbar,
 // dJz = q v_z - qbar (1 - omvbar); J_perp = q u_perp/gamma (reference zero).
 __device__ __forceinline__ void beam_sources(double ux, double uy, double uz, double dw,
@@ -270,15 +279,16 @@ __device__ __forceinline__ void beam_sources(float ux, float uy, float uzf, floa
                                              const BeamConst<float>& c, float& dS, float& dJz,
                                              float& jx, float& jy) {
   const float up2 = ux * ux + uy * uy;
-  const float d = (1.0f + up2) / (sqrtf(1.0f + up2 + uzf * uzf) + uzf);  // gamma - u_z
+  const float d = fast_div(1.0f + up2, fast_sqrt(1.0f + up2 + uzf * uzf) + uzf);  // gamma - u_z
   const float g = uzf + d;
-  const float omv = d / g;                                               // 1 - v_z
+  const float ig = fast_div(1.0f, g);
+  const float omv = d * ig;                                              // 1 - v_z
   const float domv = omv - c.omvbar;
   dS = c.qb * (dw * omv + domv);
   dJz = c.qb * (dw * (1.0f - omv) - domv);
-  const float q = c.qb * (1.0f + dw);
-  jx = q * ux / g;
-  jy = q * uy / g;
+  const float q = c.qb * (1.0f + dw) * ig;
+  jx = q * ux;
+  jy = q * uy;
 }
 
 // 1/gamma and 1 - v_z = (1 + u_perp^2)/(gamma (gamma + u_z)) of the pushed momentum.
@@ -292,8 +302,8 @@ __device__ __forceinline__ void drift_rates(double ux, double uy, double uz, dou
 __device__ __forceinline__ void drift_rates(float ux, float uy, float uzf, float& ig,
                                             float& omv) {
   const float up2 = ux * ux + uy * uy;
-  const float d = (1.0f + up2) / (sqrtf(1.0f + up2 + uzf * uzf) + uzf);  // gamma - u_z
-  ig = 1.0f / (uzf + d);
+  const float d = fast_div(1.0f + up2, fast_sqrt(1.0f + up2 + uzf * uzf) + uzf);  // gamma - u_z
+  ig = fast_div(1.0f, uzf + d);
   omv = d * ig;
 }
 
@@ -365,18 +375,19 @@ __device__ __forceinline__ void boris(float& ux, float& uy, float2& uz, const fl
   const float mx = ux + h * (Wx + By), my = uy + h * (Wy - Bx);
   const float mzf = uz.x + h * Ez;
   const float mp2 = mx * mx + my * my;
-  const float gm = sqrtf(1.0f + mp2 + mzf * mzf);
-  const float dm = (1.0f + mp2) / (gm + mzf);  // gamma^- - m_z
-  const float ig = 1.0f / gm;
+  const float gm = fast_sqrt(1.0f + mp2 + mzf * mzf);
+  const float dm = fast_div(1.0f + mp2, gm + mzf);  // gamma^- - m_z
+  const float ig = fast_div(1.0f, gm);
   const float tx = h * Bx * ig, ty = h * By * ig, tz = h * Bz * ig;
   const float t2 = tx * tx + ty * ty + tz * tz;
-  const float sfac = 2.0f / (1.0f + t2);
+  const float i1t2 = fast_div(1.0f, 1.0f + t2);
+  const float sfac = 2.0f * i1t2;
   const float sx = sfac * tx, sy = sfac * ty, sz = sfac * tz;
   // u' = m + m x t, transverse parts without the m_z t cancellation
   const float pxp = ux + h * Wx + h * By * dm * ig + my * tz;
   const float pyp = uy + h * Wy - h * Bx * dm * ig - mx * tz;
   // eps = 1 - u'_z / (gamma^- (1 + t^2)), u'_z = m_z + m_x t_y - m_y t_x
-  const float eps = (dm + gm * t2 - (mx * ty - my * tx)) * ig / (1.0f + t2);
+  const float eps = (dm + gm * t2 - (mx * ty - my * tx)) * ig * i1t2;
   ux = ux + 2.0f * h * Wx + 2.0f * h * By * eps + pyp * sz;
   uy = uy + 2.0f * h * Wy - 2.0f * h * Bx * eps - pxp * sz;
   // u_z += du in double-float: Knuth's two-sum of the leading part and du, its rounding error
@@ -498,10 +509,14 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
     for (int u = 0; u < 2; ++u) {
       ok[u] = sub0 + u < sp.ppc;
       const int sub = ok[u] ? sub0 + u : sub0;
-      const int sx = sub % sp.ppx, sy = (sub / sp.ppx) % sp.ppy, sxi = sub / (sp.ppx * sp.ppy);
-      hx[u] = (BR(sx) + BR(0.5)) / BR(sp.ppx);
-      hy[u] = (BR(sy) + BR(0.5)) / BR(sp.ppy);
-      hk[u] = (BR(sxi) + BR(0.5)) / BR(sp.ppxi);
+      // sub = (sxi ppy + sy) ppx + sx, split with exact float quotients of small integers
+      const int q1 = (int)((float(sub) + 0.5f) * float(bc.inv_ppx));
+      const int sx = sub - q1 * sp.ppx;
+      const int sxi = (int)((float(q1) + 0.5f) * float(bc.inv_ppy));
+      const int sy = q1 - sxi * sp.ppy;
+      hx[u] = (BR(sx) + BR(0.5)) * bc.inv_ppx;
+      hy[u] = (BR(sy) + BR(0.5)) * bc.inv_ppy;
+      hk[u] = (BR(sxi) + BR(0.5)) * bc.inv_ppxi;
     }
     for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
       size_t si[2];
@@ -664,13 +679,16 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
       for (int k = 0; k < 7; ++k)
         if (s_mom[k] != 0.0) atomicAdd(ext.mom + (size_t)g.kabs * 7 + k, s_mom[k]);
   }
-  for (int e = threadIdx.x; e < 2 * 4 * nx; e += blockDim.x) {
-    const int dk = e / (4 * nx), r = (e / nx) % 4, x = e % nx;
-    const int k = g.kabs + dk;
-    const BR* t = g.tile + (size_t)(e / nx) * 4 * nx + x;
-    const BR t0 = t[0], t1 = t[nx], t2 = t[2 * nx], t3 = t[3 * nx];
-    if (k < p.nk && (t0 != BR(0) || t1 != BR(0) || t2 != BR(0) || t3 != BR(0)))
-      red4(src + (((size_t)k * p.ny + wrap(g.iy - 1 + r, p.ny)) * nx + x) * 4, t0, t1, t2, t3);
+  for (int row = 0; row < 2 * 4; ++row) {  // node kabs + row / 4, grid row iy - 1 + row % 4
+    const int k = g.kabs + (row >> 2);
+    if (k >= p.nk) continue;
+    BR* dst = src + ((size_t)k * p.ny + wrap(g.iy - 1 + (row & 3), p.ny)) * nx * 4;
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      const BR* t = g.tile + (size_t)row * 4 * nx + x;
+      const BR t0 = t[0], t1 = t[nx], t2 = t[2 * nx], t3 = t[3 * nx];
+      if (t0 != BR(0) || t1 != BR(0) || t2 != BR(0) || t3 != BR(0))
+        red4(dst + (size_t)x * 4, t0, t1, t2, t3);
+    }
   }
   if (my_lost && lost) atomicAdd(lost, (unsigned long long)my_lost);
   __syncthreads();  // the tile and s_ext are reused by the block's next group

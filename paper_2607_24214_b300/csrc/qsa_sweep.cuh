@@ -87,6 +87,7 @@ struct SweepConst {
   R floor_;        // psi_floor
   R inv_npc;       // 1 / (ppc nx ny): kappa^2 from the sum of 1/(1+psi)
   R scale;         // 1 / (nx ny): inverse FFT normalisation
+  R inv_ppx, inv_ppy;  // 1 / plasma sub-lattice counts
 };
 template <typename R>
 inline SweepConst<R> sweep_consts(const DevParams& p) {
@@ -99,6 +100,8 @@ inline SweepConst<R> sweep_consts(const DevParams& p) {
   k.floor_ = R(p.psi_floor);
   k.inv_npc = R(1.0 / ((double)p.ppc * p.nx * p.ny));
   k.scale = R(1.0 / ((double)p.nx * p.ny));
+  k.inv_ppx = R(1.0 / p.ppx);
+  k.inv_ppy = R(1.0 / p.ppy);
   return k;
 }
 
@@ -293,6 +296,10 @@ __device__ __forceinline__ void deposit_ref(R* tile, R* ovf, const DepFlags& fl,
   }
 }
 
+// Reciprocal: the FP32 path uses the fast hardware approximation (about 2 ulp), FP64 is exact.
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+
 // xi push u^{j-1/2} -> u^{j+1/2}: half kick, counter-clockwise rotation by
 // 2 atan(dxi B_z/(2(1+psi))), half kick; gamma/(1+psi) of both kicks taken at the predicted
 // pre-rotation momentum (the rotation keeps |u_perp|).  From the quasistatic invariant
@@ -308,7 +315,7 @@ __device__ __forceinline__ void push_xi(R& ux, R& uy, R opp, R iopp, R gx, R gy,
   const R kx = h * (g * gx - by), ky = h * (g * gy + bx);
   const R mx = ux + kx, my = uy + ky;
   const R t = h * bz * iopp;
-  const R s = R(2) * t / (R(1) + t * t);
+  const R s = R(2) * t * rcp(R(1) + t * t);
   const R px = mx - t * my, py = my + t * mx;
   const R qx = mx - s * py, qy = my + s * px;
   ux = qx + kx;
@@ -317,9 +324,6 @@ __device__ __forceinline__ void push_xi(R& ux, R& uy, R opp, R iopp, R gx, R gy,
 
 enum DepMode : int { DEP_INIT = 0, DEP_TRIAL = 1, DEP_COMMIT = 2 };
 
-// Reciprocal: the FP32 path uses the fast hardware approximation (about 2 ulp), FP64 is exact.
-__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
 template <typename R>
 struct W4 {
@@ -441,8 +445,10 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
         for (int u = 0; u < 2; ++u) {
           ok[u] = sub0 + u < p.ppc;
           const int sub = ok[u] ? sub0 + u : sub0;
-          hx[u] = (R(sub % p.ppx) + R(0.5)) / R(p.ppx);
-          hy[u] = (R(sub / p.ppx) + R(0.5)) / R(p.ppy);
+          // sub = sy ppx + sx, split with an exact float quotient of small integers
+          const int sy = (int)((float(sub) + 0.5f) * float(a.k.inv_ppx));
+          hx[u] = (R(sub - sy * p.ppx) + R(0.5)) * a.k.inv_ppx;
+          hy[u] = (R(sy) + R(0.5)) * a.k.inv_ppy;
         }
         for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
           size_t ii[2];
@@ -640,10 +646,11 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
       // the outer tile rows go out only when a deposit landed there (the row phase reads
       // them only then)
       const int fl = s_flag;
-      for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
-        const int r = (e / nx) & (kTileRows - 1);
+      for (int row = 0; row < nf * kTileRows; ++row) {
+        const int r = row & (kTileRows - 1);
         if ((r == 0 && !(fl & 1)) || (r == kTileRows - 1 && !(fl & 2))) continue;
-        dst[e] = tile[e];
+        for (int x = threadIdx.x; x < nx; x += blockDim.x)
+          dst[(size_t)row * nx + x] = tile[(size_t)row * nx + x];
       }
     }
     if (threadIdx.x == 0) a.cflag[crow] = s_flag;
