@@ -1020,6 +1020,9 @@ int qsa_init(const qsa_params* params, void* stream, qsa_alloc_fn alloc, qsa_fre
   dp.spin_limit = params->spin_limit;
   dp.px = make_plan(dp.nx);
   dp.py = make_plan(dp.ny);
+  dp.fd_nx = make_fastdiv(dp.nx);
+  dp.fd_ny = make_fastdiv(dp.ny);
+  dp.fd_nxh = make_fastdiv(dp.nxh);
   // diagnosed modes on the half spectrum: k itself when mx >= 0, else its conjugate -k
   dp.nmodes = params->n_diag_modes;
   for (int m = 0; m < dp.nmodes; ++m) {

@@ -48,6 +48,24 @@ struct FftPlan {
   int nssh[kMaxStages];  // log2(ns) when a power of two, else -1
 };
 
+// Division of a non-negative int below 2^20 by a fixed divisor d <= 4096 as a multiply-high:
+// m = ceil(2^32 / d) makes floor(e m / 2^32) exact there (the error e (m d - 2^32) < 2^32).
+struct FastDiv {
+  unsigned m;  // 0 for d = 1
+};
+inline FastDiv make_fastdiv(int d) {
+  FastDiv f;
+  f.m = d <= 1 ? 0u : (unsigned)((0x100000000ull + (unsigned long long)d - 1) / (unsigned)d);
+  return f;
+}
+__device__ __forceinline__ int div_by(int e, FastDiv f) {
+  return f.m ? (int)__umulhi((unsigned)e, f.m) : e;
+}
+// Division by a small count 1, 2 or 4 (FFT units per block), else a plain division.
+__device__ __forceinline__ int div_small(int e, int n) {
+  return n == 1 ? e : (n == 2 ? (e >> 1) : (n == 4 ? (e >> 2) : e / n));
+}
+
 struct DevParams {
   int nx, ny, nxi, nk;        // nk = nxi + 1 slices/nodes
   int nxh;                    // nx/2 + 1 half-spectrum columns
@@ -62,6 +80,7 @@ struct DevParams {
   // the requested k is the conjugate (-k) of the stored one
   int nmodes;
   int mkx[16], mky[16], mconj[16];
+  FastDiv fd_nx, fd_ny, fd_nxh;  // division by nx, ny, nx/2 + 1 in the per-element loops
 };
 
 // The largest dynamic shared memory a kernel may use is a setting of the function on the

@@ -133,6 +133,9 @@ int solve_static(int nx, int ny, double Lx, double Ly, double kappa2, const R* S
   dp.spin_limit = 1ll << 26;
   dp.px = plan_of(nx);
   dp.py = plan_of(ny);
+  dp.fd_nx = make_fastdiv(nx);
+  dp.fd_ny = make_fastdiv(ny);
+  dp.fd_nxh = make_fastdiv(dp.nxh);
   const size_t g = (size_t)nx * ny, spec = (size_t)dp.nxh * ny;
   const size_t smem = sweep_smem_bytes<R>(nx, ny);
   int per_sm = 0, sms = 0;

@@ -774,7 +774,8 @@ __device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, 
     C<R>* Z = block_fft(A, B, nr * npair, p.px, tw, -1);
     // unpack two real transforms: A_k = (Z_k + conj Z_{-k})/2, B_k = -i (Z_k - conj Z_{-k})/2
     for (int e = threadIdx.x; e < npair * nxh * nr; e += blockDim.x) {
-      const int t = e / nr, r = e - t * nr, pr = t / nxh, k = t - pr * nxh, q = qb + r;
+      const int t = div_small(e, nr), r = e - t * nr, pr = div_by(t, p.fd_nxh);
+      const int k = t - pr * nxh, q = qb + r;
       const C<R>* zr = Z + (r * npair + pr) * nx;
       const C<R> zk = zr[k];
       const C<R> zm = cconj(zr[k == 0 ? 0 : nx - k]);
@@ -861,7 +862,7 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
   for (int u = u0; u * nb < nxh; u += G) {
     const int kb = u * nb, nc = min(nb, nxh - kb);
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
-      const int c = e / ny, ky = e - c * ny, kx = kb + c;
+      const int c = div_by(e, p.fd_ny), ky = e - c * ny, kx = kb + c;
       C<R> v[kNF];
 #pragma unroll
       for (int f = 0; f < kNF; ++f) v[f] = rspec[((size_t)f * nxh + kx) * ny + ky];
@@ -873,7 +874,7 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
     C<R>* Z = block_fft(A, B, nc * kNF, p.py, tw, -1);
     C<R>* O = (Z == A) ? B : A;
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
-      const int c = e / ny, ky = e - c * ny, kx = kb + c;
+      const int c = div_by(e, p.fd_ny), ky = e - c * ny, kx = kb + c;
       const R pw = (kx == 0 || ((p.nx % 2 == 0) && 2 * kx == p.nx)) ? R(1) : R(2);
       const C<R>* Zc = Z + c * kNF * ny;
       C<R>* Oc = O + c * 4 * ny;
@@ -925,7 +926,7 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
     }
     C<R>* W = block_fft(O, Z, nc * 4, p.py, tw, +1);
     for (int e = threadIdx.x; e < 4 * ny * nc; e += blockDim.x) {
-      const int t = e / nc, c = e - t * nc, f = t / ny, ky = t - f * ny;
+      const int t = div_small(e, nc), c = e - t * nc, f = div_by(t, p.fd_ny), ky = t - f * ny;
       a.cspec[((size_t)f * ny + ky) * nxh + kb + c] = W[(c * 4 + f) * ny + ky];
     }
     __syncthreads();
@@ -952,7 +953,7 @@ __device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int u0
   for (int u = u0; u * nb < nxh; u += G) {
     const int kb = u * nb, nc = min(nb, nxh - kb);
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
-      const int c = e / ny, ky = e - c * ny, kx = kb + c;
+      const int c = div_by(e, p.fd_ny), ky = e - c * ny, kx = kb + c;
       C<R> v[3];
 #pragma unroll
       for (int f = 0; f < 3; ++f) v[f] = rspec[((size_t)f * nxh + kx) * ny + ky];
@@ -963,7 +964,7 @@ __device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int u0
     C<R>* Z = block_fft(A, B, nc * 3, p.py, tw, -1);
     C<R>* O = (Z == A) ? B : A;
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
-      const int c = e / ny, ky = e - c * ny, kx = kb + c;
+      const int c = div_by(e, p.fd_ny), ky = e - c * ny, kx = kb + c;
       const C<R>* Zc = Z + c * 3 * ny;
       C<R>* Oc = O + c * 3 * ny;
       const size_t ix0 = (size_t)kx * ny + ky, ix1 = ((size_t)nxh + kx) * ny + ky;
@@ -983,7 +984,7 @@ __device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int u0
     }
     C<R>* W = block_fft(O, Z, nc * 3, p.py, tw, +1);
     for (int e = threadIdx.x; e < 3 * ny * nc; e += blockDim.x) {
-      const int t = e / nc, c = e - t * nc, f = t / ny, ky = t - f * ny;
+      const int t = div_small(e, nc), c = e - t * nc, f = div_by(t, p.fd_ny), ky = t - f * ny;
       a.cspec[((size_t)f * ny + ky) * nxh + kb + c] = W[(c * 3 + f) * ny + ky];
     }
     __syncthreads();
@@ -1018,7 +1019,8 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
   for (int u = u0; u * nb < ny; u += G) {
     const int qb = u * nb, nr = min(nb, ny - qb);
     for (int e = threadIdx.x; e < nr * npair * nx; e += blockDim.x) {
-      const int rp = e / nx, k = e - rp * nx, r = rp / npair, pr = rp - r * npair, q = qb + r;
+      const int rp = div_by(e, p.fd_nx), k = e - rp * nx, r = rp >> 1, pr = rp - 2 * r,
+                q = qb + r;  // npair = 2
       const int f0 = 2 * pr, f1 = 2 * pr + 1;
       // full spectrum of z = a + i b from the half spectra of the real outputs a, b
       const int kk = (k < nxh) ? k : nx - k;
@@ -1038,7 +1040,7 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
     __syncthreads();
     C<R>* Z = block_fft(A, B, nr * npair, p.px, tw, +1);
     for (int e = threadIdx.x; e < nr * nx; e += blockDim.x) {
-      const int r = e / nx, x = e - r * nx, q = qb + r;
+      const int r = div_by(e, p.fd_nx), x = e - r * nx, q = qb + r;
       const C<R>* Zr = Z + r * npair * nx;
       R v[4];
       v[0] = Zr[x].x * scale;
