@@ -197,6 +197,30 @@ __device__ __forceinline__ void put(const Group<BR>& g, BR* src, const DevParams
   }
 }
 
+// Trilinear weights W of the eight corners of the home cell at (h + d) and their differences
+// dW = W - W(h) from the reference position h, both separable by axis: with a = h or 1 - h and
+// d = +-offset per axis, W = (a1 + d1)(a2 + d2)(a3 + d3) and the difference telescopes as
+// dW = d1 (a2 + d2)(a3 + d3) + a1 [d2 (a3 + d3) + a2 d3], free of cancellation.
+template <typename BR>
+__device__ __forceinline__ void home_weights(BR hx, BR hy, BR hk, BR ox, BR oy, BR oxi,
+                                             BR (&W)[2][2][2], BR (&dW)[2][2][2]) {
+#pragma unroll
+  for (int ck = 0; ck < 2; ++ck) {
+    const BR a3 = ck ? hk : BR(1) - hk, d3 = ck ? oxi : -oxi, K = a3 + d3;
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy) {
+      const BR a2 = cy ? hy : BR(1) - hy, d2 = cy ? oy : -oy;
+      const BR YK = (a2 + d2) * K, T = d2 * K + a2 * d3;
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) {
+        const BR a1 = cx ? hx : BR(1) - hx, d1 = cx ? ox : -ox;
+        W[ck][cy][cx] = (a1 + d1) * YK;
+        dW[ck][cy][cx] = d1 * YK + a1 * T;
+      }
+    }
+  }
+}
+
 // Deposit, per source quantity, dev W(x) + ref (W(x) - W(home)) (ref = 0 for J_x, J_y) for a
 // particle of home column ix, home sub-cell position (hx, hy, hk) and offsets (ox, oy, oxi) in
 // cells.  In the home cell the trilinear weight differences come from the offsets without
@@ -210,20 +234,17 @@ __device__ __forceinline__ void deposit_particle(const Group<BR>& g, BR* src, co
   const int nx = p.nx;
   if (lx >= BR(0) && lx < BR(1) && ly >= BR(0) && ly < BR(1) && lk >= BR(0) && lk < BR(1)) {
     const int x1 = (ix + 1 == nx) ? 0 : ix + 1;
+    BR Wc[2][2][2], dWc[2][2][2];
+    home_weights(hx, hy, hk, ox, oy, oxi, Wc, dWc);
 #pragma unroll
     for (int ck = 0; ck < 2; ++ck) {
       if (g.kabs + ck >= p.nk) continue;
-      const BR a3 = ck ? hk : BR(1) - hk, d3 = ck ? oxi : -oxi;
 #pragma unroll
       for (int cy = 0; cy < 2; ++cy) {
-        const BR a2 = cy ? hy : BR(1) - hy, d2 = cy ? oy : -oy;
         BR* row = g.tile + (size_t)(ck * 4 + 1 + cy) * 4 * nx;
 #pragma unroll
         for (int cx = 0; cx < 2; ++cx) {
-          const BR a1 = cx ? hx : BR(1) - hx, d1 = cx ? ox : -ox;
-          const BR w = (a1 + d1) * (a2 + d2) * (a3 + d3);
-          const BR dW = d1 * a2 * a3 + a1 * d2 * a3 + a1 * a2 * d3 + d1 * d2 * a3 +
-                        d1 * a2 * d3 + a1 * d2 * d3 + d1 * d2 * d3;
+          const BR w = Wc[ck][cy][cx], dW = dWc[ck][cy][cx];
           BR* t = row + (cx ? x1 : ix);
           atomicAdd(t, dS * w + refS * dW);
           atomicAdd(t + nx, dJz * w + refJz * dW);
@@ -641,14 +662,14 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
               for (int q = 0; q < 4; ++q) acc[cx][q] = BR(0);
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
+              // the separable, telescoped weights of home_weights, one (ck, cy) row at a time
               const BR a3 = ck ? hk[u] : BR(1) - hk[u], d3 = ck ? doxi[u] : -doxi[u];
               const BR a2 = cy ? hy[u] : BR(1) - hy[u], d2 = cy ? doy[u] : -doy[u];
+              const BR K = a3 + d3, YK = (a2 + d2) * K, T = d2 * K + a2 * d3;
 #pragma unroll
               for (int cx = 0; cx < 2; ++cx) {
                 const BR a1 = cx ? hx[u] : BR(1) - hx[u], d1 = cx ? dox[u] : -dox[u];
-                const BR w = (a1 + d1) * (a2 + d2) * (a3 + d3);
-                const BR dW = d1 * a2 * a3 + a1 * d2 * a3 + a1 * a2 * d3 + d1 * d2 * a3 +
-                              d1 * a2 * d3 + a1 * d2 * d3 + d1 * d2 * d3;
+                const BR w = (a1 + d1) * YK, dW = d1 * YK + a1 * T;
                 acc[cx][0] += dv[u][0] * w + refS * dW;
                 acc[cx][1] += dv[u][1] * w + refJz * dW;
                 acc[cx][2] += dv[u][2] * w;

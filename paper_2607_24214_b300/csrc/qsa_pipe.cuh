@@ -212,16 +212,15 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
         }
         if (!grid_sync(bar, epoch)) return;
         if (last) {
-          if (tid == 0) {
-            for (int k = 0; k < nt; ++k) {
-              const int s = act_t[k], j = js[s], nk = sa[s].p.nk;
-              const double jz = *((volatile double*)&sa[s].diag[D_JZ * nk + j]);
-              ez0n[s] = ez0h[s] - sa[s].p.dxi * jz;
-              ez0j[s] = 0.5 * (ez0h[s] + ez0n[s]);
-              if (blockIdx.x == 0) {
-                sa[s].diag[D_PSI0 * nk + j] = psi0[s];
-                sa[s].diag[D_EZ0 * nk + j] = ez0j[s];
-              }
+          // one thread per active slot (distinct slots: no two threads share an entry)
+          if (tid < nt) {
+            const int s = act_t[tid], j = js[s], nk = sa[s].p.nk;
+            const double jz = *((volatile double*)&sa[s].diag[D_JZ * nk + j]);
+            ez0n[s] = ez0h[s] - sa[s].p.dxi * jz;
+            ez0j[s] = 0.5 * (ez0h[s] + ez0n[s]);
+            if (blockIdx.x == 0) {
+              sa[s].diag[D_PSI0 * nk + j] = psi0[s];
+              sa[s].diag[D_EZ0 * nk + j] = ez0j[s];
             }
           }
           __syncthreads();
