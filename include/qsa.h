@@ -95,6 +95,12 @@ typedef struct {
   int32_t n_diag_modes;    /* transverse modes whose amplitude every sweep records (0..16) */
   int32_t _pad;
   qsa_kvec diag_modes[QSA_MAX_MODES]; /* k != 0, |mx| <= nx/2, |my| <= ny/2 */
+  double pc_tol;           /* 0: exactly n_pc_iter field solves per slice.  > 0: tolerance
+                              mode of the predictor-corrector for B_perp (section "QS-PIC"
+                              of the paper, iterated to convergence): stop after the first
+                              solve whose relative change ||B_perp(n) - B_perp(n-1)|| /
+                              ||B_perp(n)|| is below pc_tol, after n_pc_iter solves at most;
+                              the count per slice is reported in qsa_diag.pc_iters */
 } qsa_params;
 
 /* Allocator callbacks: alloc returns a device pointer (NULL on failure) of at least `bytes`
@@ -137,6 +143,8 @@ typedef struct {
                            (w/wbar) u_x^2, (w/wbar) u_y^2, (w/wbar) du_z^2, with
                            du_z = u_z - sqrt(gamma_b^2 - 1) and wbar the species' nominal
                            weight; of the current beam (after the last push) */
+  double* pc_iters;     /* field solves of the predictor-corrector at each slice (n_pc_iter
+                           unless pc_tol > 0) */
 } qsa_diag;
 
 /* Create a handle: validates params, allocates device state, builds every beam species on
@@ -184,8 +192,8 @@ int qsa_beam_step(qsa_handle* h);
 int qsa_advance(qsa_handle* h, int32_t n_steps);
 
 /* n_steps beam steps (sweep + push) of each of n_handles independent instances, which may
- * differ in grid size, beam, box and every other parameter except precision, n_pc_iter and
- * stream (the same for all; a handle may appear once).  Each step of up to 16 instances runs
+ * differ in grid size, beam, box and every other parameter except precision, n_pc_iter,
+ * pc_tol and stream (the same for all; a handle may appear once).  Each step of up to 16 instances runs
  * in one persistent launch whose phases cover the work of all of them (parameter scans over
  * alpha and gamma_b).  The same result per instance as n_steps x (qsa_plasma_sweep;
  * qsa_beam_step) on it, up to the summation order of the deposits.  The FFT work units (rows

@@ -43,6 +43,9 @@ Discrete scheme (the readings are listed in the design notes):
   * B_perp from a predictor-corrector of n_pc_iter field solves per slice, d_xi J_perp =
     (J_perp^{j+1/2} - J_perp^{j-1/2})/dxi, J_perp^{j+1/2} deposited at x^{j+1/2}; each solve is
     shifted by kappa^2 = <w/(1+psi_p)> / (Lx Ly): (k^2 + kappa^2) B_new = rhs + kappa^2 B_old;
+    with pc_tol > 0 (the corrector iterated to convergence instead of a fixed count) the
+    solves stop after the first whose change ||B_new - B_old|| / ||B_new|| (2-norms over the
+    grid) is below pc_tol, or is zero, after n_pc_iter solves at most;
   * mean mode by leapfrog in xi (FP64 scalars);
   * beam: Boris in tau with step dt, fields trilinear from the slab of slices 0..nxi,
     lost when xi >= Lxi; beam sources deposited CIC x linear-in-xi with velocities u/gamma.
@@ -236,6 +239,7 @@ def plasma_sweep(p, src, return_particles=False, return_psi=False, n_slices=None
     nk = p.nxi + 1 if n_slices is None else n_slices
     nsrc = src.shape[1]
     floor = p.psi_floor
+    pc_tol = getattr(p, "pc_tol", 0.0)
     cell = G.dx * G.dy
     # quiet lattice at xi = 0
     ppx, ppy = p.ppc_plasma_x, p.ppc_plasma_y
@@ -265,7 +269,8 @@ def plasma_sweep(p, src, return_particles=False, return_psi=False, n_slices=None
     slab = np.zeros((nk, 6, p.ny, p.nx))
     psi_slices = np.zeros((nk, p.ny, p.nx)) if return_psi else None
     diag = {k: np.zeros(nk) for k in ("kappa2", "psi0", "ez0", "jz_mean", "opp_min",
-                                      "n_floor", "invariant", "charge", "pc_residual")}
+                                      "n_floor", "invariant", "charge", "pc_residual",
+                                      "pc_iters")}
     # prologue: J_perp^{-1/2} (plasma at rest, beam half node 0), psi of slice 0
     Jx_prev, Jy_prev = 0.5 * src_at(2, 0), 0.5 * src_at(3, 0)
     psi0, ez0_half = 0.0, 0.0
@@ -304,6 +309,11 @@ def plasma_sweep(p, src, return_particles=False, return_psi=False, n_slices=None
             Bx_old, By_old = Bx, By
             Bx, By = solve_bperp(G, Jz, (Jxh - Jx_prev) / dxi, (Jyh - Jy_prev) / dxi,
                                  kappa2, Bx, By)
+            diag["pc_iters"][j] = it + 1
+            if pc_tol > 0 and it + 1 < p.n_pc_iter:
+                change = np.sqrt(np.sum((Bx - Bx_old) ** 2 + (By - By_old) ** 2))
+                if change == 0 or change < pc_tol * np.sqrt(np.sum(Bx ** 2 + By ** 2)):
+                    break
         num = np.sqrt(np.sum((Bx - Bx_old) ** 2 + (By - By_old) ** 2))
         den = np.sqrt(np.sum(Bx ** 2 + By ** 2))
         diag["pc_residual"][j] = num / den if den > 0 else 0.0

@@ -63,6 +63,7 @@ class Params:
     ppc_plasma_y: int = 2
     precision: str = "fp64"          # "fp64" or "mixed"
     n_pc_iter: int = 3
+    pc_tol: float = 0.0              # > 0: solves per slice until the B_perp change < pc_tol
     psi_floor: float = 0.05
     seed: int = 0
     spin_limit: int = 1 << 26

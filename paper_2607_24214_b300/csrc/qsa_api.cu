@@ -753,6 +753,7 @@ int diagnostics(qsa_handle* h, qsa_diag* out) {
       const double den = row(D_PCDEN)[j];
       out->pc_residual[j] = den > 0 ? std::sqrt(row(D_PCNUM)[j] / den) : 0.0;
     }
+    if (out->pc_iters) out->pc_iters[j] = row(D_NPC)[j];
   }
   // rms fields per slice, and over xi segments: <F^2> = 2 E / (Lx Ly dxi)
   {
@@ -947,6 +948,7 @@ int validate(const qsa_params* p, std::string& why) {
   if (p->n_modes < 0 || p->n_modes > QSA_MAX_MODES) return bad("n_modes out of range");
   if (p->precision != QSA_FP64 && p->precision != QSA_MIXED) return bad("unknown precision");
   if (p->n_pc_iter < 1 || p->n_pc_iter > 64) return bad("n_pc_iter must be in 1..64");
+  if (!(p->pc_tol >= 0.0 && p->pc_tol <= 1e100)) return bad("pc_tol must be finite and >= 0");
   if (!(p->psi_floor > 0 && p->psi_floor < 1)) return bad("psi_floor must be in (0, 1)");
   if (p->spin_limit < 0) return bad("spin_limit must be >= 0");
   if (p->pipeline_depth < 0 || p->pipeline_depth > kMaxPipe)
@@ -1008,6 +1010,7 @@ int qsa_init(const qsa_params* params, void* stream, qsa_alloc_fn alloc, qsa_fre
   dp.ppc = dp.ppx * dp.ppy;
   dp.np = dp.ppc * dp.nx * dp.ny;
   dp.n_pc = params->n_pc_iter;
+  dp.pc_tol2 = params->pc_tol * params->pc_tol;
   dp.nsmem_rows = kTileRows;
   dp.Lx = params->Lx;
   dp.Ly = params->Ly;
@@ -1119,6 +1122,8 @@ int qsa_advance_batch(qsa_handle* const* handles, int32_t n_handles, int32_t n_s
     if (h->fp64 != lead->fp64) return fail(lead, QSA_ERR_ARG, "handles differ in precision");
     if (h->stream != lead->stream) return fail(lead, QSA_ERR_ARG, "handles differ in stream");
     if (h->dp.n_pc != lead->dp.n_pc) return fail(lead, QSA_ERR_ARG, "handles differ in n_pc_iter");
+    if (h->dp.pc_tol2 != lead->dp.pc_tol2)
+      return fail(lead, QSA_ERR_ARG, "handles differ in pc_tol");
     for (int k = 0; k < i; ++k)
       if (handles[k] == h) return fail(lead, QSA_ERR_ARG, "a handle appears twice");
   }

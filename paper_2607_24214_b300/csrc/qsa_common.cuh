@@ -71,6 +71,7 @@ struct DevParams {
   int nxh;                    // nx/2 + 1 half-spectrum columns
   int ppx, ppy, ppc, np;      // plasma lattice
   int n_pc;
+  double pc_tol2;             // square of the predictor-corrector tolerance (0: fixed n_pc)
   int nsmem_rows;             // tile rows of the plasma deposit (4)
   double Lx, Ly, Lxi, dx, dy, dxi, dt;
   double psi_floor;
@@ -330,6 +331,12 @@ __device__ __forceinline__ U4 philox4x32_10(U4 ctr, uint32_t k0, uint32_t k1) {
   return ctr;
 }
 __device__ __forceinline__ double u01(uint32_t r) { return ((double)r + 0.5) * (1.0 / 4294967296.0); }
+
+// Asks the L2 cache to fetch `bytes` bytes at p (both multiples of 16) ahead of their use; no
+// registers and no shared memory are involved, and nothing waits for it.
+__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 // Periodic index: i mod n in [0, n), without a division when i is within one period.
 __device__ __forceinline__ int wrap(int i, int n) {

@@ -93,6 +93,8 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
   __shared__ int act_t[kMaxPipe], act_c[kMaxPipe];
   __shared__ int ot_dep[kMaxPipe], ot_row[kMaxPipe], ot_col[kMaxPipe];
   __shared__ int oc_dep[kMaxPipe], oc_row[kMaxPipe], oc_col[kMaxPipe], o_push[kMaxPipe];
+  __shared__ int ngrp[kMaxPipe];  // beam groups each slot pushes in this tick
+  __shared__ int pcdone[kMaxPipe];  // tolerance mode: the slot's slice has converged
   __shared__ int n_t, n_c, stop;
   const int tid = threadIdx.x, G = gridDim.x;
   {
@@ -117,6 +119,7 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
   C<R>* buf = reinterpret_cast<C<R>*>(smem);
   C<R>* tw = reinterpret_cast<C<R>*>(smem + phase_smem_bytes<R>(T->nx_max, T->ny_max, nbr, nbc));
   const int n_pc = sa[0].p.n_pc;  // the same in every slot
+  const bool tol = sa[0].p.pc_tol2 > 0.0;  // so is the predictor-corrector tolerance
   unsigned epoch = 0;
   // every tick processes at least one slice or one layer, so this bound is never reached by
   // a correct schedule; it keeps a scheduling fault from spinning forever
@@ -125,23 +128,50 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
   max_ticks *= chained ? nslots : 1;
 
   for (long long tick = 0;; ++tick) {
+    __syncthreads();  // the state thread 0 advanced at the end of the previous tick
+    if (tid < nslots) {
+      // per-slot part of the plan, one thread per slot: slot s reads only what the previous
+      // tick left (its own state and slot s - 1's pf), so the slots are independent
+      const int s = tid;
+      const DevParams& p = sa[s].p;
+      const int nk = p.nk, nxi = p.nxi;
+      int a = 0;
+      if (js[s] < nk) {
+        if (!chained || s == 0) {
+          a = 1;
+        } else {
+          const int need = min(nxi, js[s] + 2 + margin[s]);
+          a = pf[s - 1] >= need;
+        }
+      }
+      adv[s] = a;
+      // slab nodes 0 .. ready - 1 of slot s are complete at the commit slot of this tick
+      const int ready = js[s] + ((a && js[s] >= 0) ? 1 : 0);
+      const volatile int* cm = T->slot[s].cmax_in;
+      int c = pf[s], n = 0;
+      while (c < nxi && n < max_push) {
+        if (chained && s > 0 && c >= pf[s - 1]) break;
+        if (cm[c] + 2 > ready) break;
+        ++c;
+        ++n;
+      }
+      npush[s] = n;
+      // beam groups of the layers pushed: ny per layer and species present there
+      const PipeSlot<R>& ps = T->slot[s];
+      int ng = 0;
+      for (int l = pf[s]; l < pf[s] + n; ++l)
+        for (int si = 0; si < ps.nspecies; ++si)
+          if (l >= ps.sp[si].k0 && l < ps.sp[si].k0 + ps.sp[si].nkb) ng += p.ny;
+      ngrp[s] = ng;
+    }
+    __syncthreads();
     if (tid == 0) {
-      // plan of this tick (identical in every block)
+      // offsets of each slot's units in the phases of this tick (identical in every block)
       int nt = 0, nc = 0, all_done = 1;
       int udep = 0, urow = 0, ucol = 0, cdep = 0, crow = 0, ccol = 0;
       for (int s = 0; s < nslots; ++s) {
         const DevParams& p = sa[s].p;
-        const int nk = p.nk, nxi = p.nxi;
-        int a = 0;
-        if (js[s] < nk) {
-          if (!chained || s == 0) {
-            a = 1;
-          } else {
-            const int need = min(nxi, js[s] + 2 + margin[s]);
-            a = pf[s - 1] >= need;
-          }
-        }
-        adv[s] = a;
+        const int nk = p.nk, a = adv[s];
         const int ur = (p.ny + nbr - 1) / nbr, uc = (p.nxh + nbc - 1) / nbc;
         if (a && js[s] >= 0) {
           ot_dep[nt] = udep;
@@ -152,6 +182,7 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
           ucol += uc;
           act_t[nt++] = s;
         }
+        pcdone[s] = 0;
         if (a && js[s] < nk - 1) {
           oc_dep[nc] = cdep;
           oc_row[nc] = crow;
@@ -161,27 +192,13 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
           ccol += uc;
           act_c[nc++] = s;
         }
-        // slab nodes 0 .. ready - 1 of slot s are complete at the commit slot of this tick
-        const int ready = js[s] + ((a && js[s] >= 0) ? 1 : 0);
-        const volatile int* cm = T->slot[s].cmax_in;
-        int c = pf[s], n = 0;
-        while (c < nxi && n < max_push) {
-          if (chained && s > 0 && c >= pf[s - 1]) break;
-          if (cm[c] + 2 > ready) break;
-          ++c;
-          ++n;
-        }
-        npush[s] = n;
-        if (js[s] < nk || pf[s] < nxi) all_done = 0;
+        if (js[s] < nk || pf[s] < p.nxi) all_done = 0;
       }
       // beam groups of the commit slot follow its deposit units
       int up = cdep;
       for (int s = 0; s < nslots; ++s) {
         o_push[s] = up;
-        const PipeSlot<R>& ps = T->slot[s];
-        for (int c = pf[s]; c < pf[s] + npush[s]; ++c)
-          for (int si = 0; si < ps.nspecies; ++si)
-            if (c >= ps.sp[si].k0 && c < ps.sp[si].k0 + ps.sp[si].nkb) up += sa[s].p.ny;
+        up += ngrp[s];
       }
       n_t = nt;
       n_c = nc;
@@ -194,26 +211,32 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
     // ---- trial iterations of the slots that process a slice
     const int nt = n_t;
     if (nt > 0) {
+      // tolerance mode: every solve may be a slot's last, so each completes the slice's
+      // outputs; a slot whose B_perp has converged skips the remaining solves (its units
+      // idle), and the loop ends once every slot has
       for (int it = 0; it < n_pc; ++it) {
-        const bool first = (it == 0), last = (it == n_pc - 1);
+        const bool first = (it == 0), last = tol || (it == n_pc - 1);
         for (int k = 0; k < nt; ++k) {
           const int s = act_t[k];
+          if (pcdone[s]) continue;
           dep_phase(sa[s], tile, DEP_TRIAL, js[s], psi0[s], first, last, unit0(ot_dep[k], G), G);
         }
         if (!grid_sync(bar, epoch)) return;
         for (int k = 0; k < nt; ++k) {
           const int s = act_t[k];
+          if (pcdone[s]) continue;
           row_phase(sa[s], buf, tw, DEP_TRIAL, js[s], unit0(ot_row[k], G), G, nbr);
         }
         if (!grid_sync(bar, epoch)) return;
         for (int k = 0; k < nt; ++k) {
           const int s = act_t[k];
+          if (pcdone[s]) continue;
           col_phase_b(sa[s], buf, tw, js[s], last, psi0[s], unit0(ot_col[k], G), G, nbc);
         }
         if (!grid_sync(bar, epoch)) return;
         if (last) {
           // one thread per active slot (distinct slots: no two threads share an entry)
-          if (tid < nt) {
+          if (tid < nt && !pcdone[act_t[tid]]) {
             const int s = act_t[tid], j = js[s], nk = sa[s].p.nk;
             const double jz = *((volatile double*)&sa[s].diag[D_JZ * nk + j]);
             ez0n[s] = ez0h[s] - sa[s].p.dxi * jz;
@@ -221,15 +244,31 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
             if (blockIdx.x == 0) {
               sa[s].diag[D_PSI0 * nk + j] = psi0[s];
               sa[s].diag[D_EZ0 * nk + j] = ez0j[s];
+              sa[s].diag[D_NPC * nk + j] = (double)(it + 1);
             }
           }
           __syncthreads();
         }
         for (int k = 0; k < nt; ++k) {
           const int s = act_t[k];
+          if (pcdone[s]) continue;
           irow_phase(sa[s], buf, tw, false, js[s], last, ez0j[s], unit0(ot_row[k], G), G, nbr);
         }
         if (!grid_sync(bar, epoch)) return;
+        if (tol && it + 1 < n_pc) {
+          int left = 0;
+          for (int k = 0; k < nt; ++k) {
+            const int s = act_t[k];
+            if (pcdone[s]) continue;
+            if (pc_converged(sa[s], js[s])) {
+              if (tid == 0) pcdone[s] = 1;
+            } else {
+              ++left;
+            }
+          }
+          __syncthreads();
+          if (left == 0) break;
+        }
       }
     }
 
@@ -294,7 +333,6 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
         pf[s] += npush[s];
       }
     }
-    // the next tick's plan (thread 0) is followed by a __syncthreads before any use
   }
 }
 

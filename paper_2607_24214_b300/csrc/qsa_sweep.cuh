@@ -50,6 +50,7 @@ enum Diag : int {
   D_OPPMIN,     // ordered-key minimum of 1 + psi
   D_NFLOOR,
   D_INV,        // max invariant residual (non-negative double bits)
+  D_NPC,        // field solves of the predictor-corrector at the slice
   D_E0,         // six energies D_E0..D_E0+5
   D_COUNT = D_E0 + 6
 };
@@ -422,6 +423,20 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
   R* __restrict__ pps = a.ppsi;
 
   for (int crow = u0; crow < ny; crow += G) {
+    // (a bulk prefetch wants 16-byte multiples: chunks of other sizes go without)
+    if (threadIdx.x == 0 && mode != DEP_INIT && (per_chunk * sizeof(R)) % 16 == 0) {
+      // the plasma state of this chunk (first pass only) and of the block's next chunk into
+      // L2: the state was last touched a tick ago and has usually left the cache
+      const unsigned nbts = (unsigned)(per_chunk * sizeof(R));
+      for (int c2 = (crow == u0 ? crow : crow + G); c2 <= crow + G && c2 < ny; c2 += G) {
+        const size_t b2 = (size_t)c2 * per_chunk;
+        l2_prefetch(pox + b2, nbts);
+        l2_prefetch(poy + b2, nbts);
+        l2_prefetch(pux + b2, nbts);
+        l2_prefetch(puy + b2, nbts);
+        l2_prefetch(pps + b2, nbts);
+      }
+    }
     for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) tile[e] = R(0);
     if (threadIdx.x == 0) s_flag = 0;
     __syncthreads();
@@ -708,6 +723,12 @@ __device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, 
   const int k0 = (mode == DEP_TRIAL) ? jj : jj - 1;  // beam-source nodes k0, k0 + 1
   for (int u = u0; u * nb < ny; u += G) {
     const int qb = u * nb, nr = min(nb, ny - qb);
+    if (threadIdx.x == 0 && src != nullptr) {
+      // the unit's rows of the two beam-source nodes into L2 while the partials are read
+      const unsigned nbts = (unsigned)((size_t)nr * nx * 4 * sizeof(R));
+      if (k0 >= 0 && k0 < nk) l2_prefetch(src + ((size_t)k0 * ny + qb) * nx * 4, nbts);
+      if (k0 + 1 < nk) l2_prefetch(src + ((size_t)(k0 + 1) * ny + qb) * nx * 4, nbts);
+    }
     for (int r = 0; r < nr; ++r) {
     const int q = qb + r;
     // grid row q collects tile row t of chunk q + 1 - t; rows 1, 2 always, rows 0, 3 and the
@@ -1018,6 +1039,10 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
   load_tw(tw, a.twx, nx);
   for (int u = u0; u * nb < ny; u += G) {
     const int qb = u * nb, nr = min(nb, ny - qb);
+    // the slab of the last solve adds W = -grad psi from the field grid, written one slice
+    // earlier and by now often out of L2: fetch the unit's rows while the transforms run
+    if (!psi_mode && last && threadIdx.x == 0)
+      l2_prefetch(fg + (size_t)qb * nx * kFG, (unsigned)((size_t)nr * nx * kFG * sizeof(R)));
     for (int e = threadIdx.x; e < nr * npair * nx; e += blockDim.x) {
       const int rp = div_by(e, p.fd_nx), k = e - rp * nx, r = rp >> 1, pr = rp - 2 * r,
                 q = qb + r;  // npair = 2
@@ -1103,6 +1128,29 @@ __host__ __device__ inline size_t sweep_smem_bytes(int nx, int ny, int nbr = 1, 
 }
 
 // ------------------------------------------------------------------ the kernel
+// Tolerance mode of the predictor-corrector: has the last B_perp solve of slice j changed
+// B_perp by less than pc_tol (relative, in the 2-norm over the grid)?  The solve's squared
+// change and squared norm are in the per-block partial slots of slice j (written by every
+// block before the barrier that precedes this call); each block sums all of them in the same
+// order, so every block reaches the same answer.  Called by all threads of the block.
+template <typename R>
+__device__ bool pc_converged(const SweepArgs<R>& a, int j) {
+  __shared__ double red[32];
+  __shared__ int s_conv;
+  double num = 0.0, den = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const double* e = a.dpart + ((size_t)j * gridDim.x + b) * P_COUNT;
+    num += __ldcg(e + P_PCNUM);  // through L2: earlier iterations left these slots in L1
+    den += __ldcg(e + P_PCDEN);
+  }
+  const double N = block_sum_lo(num, red);
+  const double D = block_sum_lo(den, red);
+  // a zero field has converged; a non-finite sum never does
+  if (threadIdx.x == 0) s_conv = (N < a.p.pc_tol2 * D) || (N == 0.0);
+  __syncthreads();
+  return s_conv != 0;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256, 2) sweep_kernel(SweepArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1131,10 +1179,14 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(SweepArgs<R> a) {
   irow_phase(a, buf, tw, true, 0, false, 0.0, u0, G, 1);
   if (!sync(-1, 3)) return;
 
+  // tolerance mode: every solve may be the last, so each one completes the slice's outputs
+  // (slab, diagnostics), and the loop stops after the first that has converged
+  const bool tol = p.pc_tol2 > 0.0;
   for (int j = 0; j < p.nk; ++j) {
     double ez0n = ez0h, ez0j = ez0h;
+    int nsolve = p.n_pc;
     for (int it = 0; it < p.n_pc; ++it) {
-      const bool first = (it == 0), last = (it == p.n_pc - 1);
+      const bool first = (it == 0), last = tol || (it == p.n_pc - 1);
       dep_phase(a, tile, DEP_TRIAL, j, psi0, first, last, u0, G);
       if (!sync(j, 4 * it + 0)) return;
       row_phase(a, buf, tw, DEP_TRIAL, j, u0, G, 1);
@@ -1148,10 +1200,15 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(SweepArgs<R> a) {
       }
       irow_phase(a, buf, tw, false, j, last, ez0j, u0, G, 1);
       if (!sync(j, 4 * it + 3)) return;
+      if (tol && it + 1 < p.n_pc && pc_converged(a, j)) {
+        nsolve = it + 1;
+        break;
+      }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.diag[D_PSI0 * p.nk + j] = psi0;
       a.diag[D_EZ0 * p.nk + j] = ez0j;
+      a.diag[D_NPC * p.nk + j] = (double)nsolve;
     }
     if (j + 1 < p.nk) {
       const int pc = 4 * p.n_pc;

@@ -66,7 +66,8 @@ class ParamsC(ct.Structure):
                 ("Lx", ct.c_double), ("Ly", ct.c_double), ("Lxi", ct.c_double),
                 ("dt", ct.c_double), ("psi_floor", ct.c_double), ("seed", ct.c_uint64),
                 ("spin_limit", ct.c_int64), ("species", Species * 4), ("modes", Mode * 16),
-                ("n_diag_modes", ct.c_int32), ("_pad", ct.c_int32), ("diag_modes", KVec * 16)]
+                ("n_diag_modes", ct.c_int32), ("_pad", ct.c_int32), ("diag_modes", KVec * 16),
+                ("pc_tol", ct.c_double)]
 
 
 _DP = ct.POINTER(ct.c_double)
@@ -77,7 +78,8 @@ class Diag(ct.Structure):
                 ("kappa2", _DP), ("opp_min", _DP), ("n_floor", _DP), ("invariant", _DP),
                 ("charge", _DP), ("pc_residual", _DP), ("beam_lost", ct.c_int64),
                 ("sweeps", ct.c_int64), ("rms", _DP), ("seg_width", ct.c_double),
-                ("rms_seg", _DP), ("mode_amp", _DP), ("beam_moments", _DP)]
+                ("rms_seg", _DP), ("mode_amp", _DP), ("beam_moments", _DP),
+                ("pc_iters", _DP)]
 
 
 ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_void_p)
@@ -148,6 +150,7 @@ def to_c_params(p: config.Params) -> ParamsC:
     c.n_modes = len(p.modes)
     c.precision = 0 if p.precision == "fp64" else 1
     c.n_pc_iter = p.n_pc_iter
+    c.pc_tol = p.pc_tol
     c.pipeline_depth = p.pipeline_depth
     c.Lx, c.Ly, c.Lxi, c.dt = p.Lx, p.Ly, p.Lxi, p.dt
     c.psi_floor = p.psi_floor
@@ -298,7 +301,8 @@ class QSA:
         [species, xi cell] sum of w/wbar, both derived from the raw moment sums."""
         nk, p = self.nk, self.p
         out = {k: np.zeros(nk) for k in ("psi0", "ez0", "jz_mean", "kappa2", "opp_min",
-                                          "n_floor", "invariant", "charge", "pc_residual")}
+                                          "n_floor", "invariant", "charge", "pc_residual",
+                                          "pc_iters")}
         out["energy"] = np.zeros((nk, 6))
         out["rms"] = np.zeros((nk, 6))
         nseg = max(1, int(np.ceil(p.Lxi / seg_width - 1e-12)))
