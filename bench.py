@@ -58,6 +58,19 @@ def sweep_bytes(p):
     return 40.0 * ppc * cells * p.nxi + (16.0 + 24.0) * cells * (p.nxi + 1)
 
 
+# DRAM bytes (read + write) of one pipe_kernel launch from an ncu capture of the same kernel
+# on a small case of the same grid and depth: 256 x 256, 16 slices, 16 steps in flight
+# (profiles/pipe_kernel_c2grid_16slices_depth16.md): 14.55 GB read + 20.53 GB written over
+# 16 steps x 17 slices.  Every step-slice touches the same scratch and its share of the beam
+# stream, so a launch's traffic scales with its step-slices.
+PIPE_DRAM_BYTES_PER_STEP_SLICE = (14.553429e9 + 20.534880e9) / (16 * 17)
+
+
+def pipe_traffic(p, depth):
+    """DRAM bytes of one pipelined launch of `depth` steps, scaled from the capture above."""
+    return PIPE_DRAM_BYTES_PER_STEP_SLICE * depth * (p.nxi + 1)
+
+
 def pipe_bytes(p, depth):
     """Algorithmic HBM bytes of one pipelined launch of `depth` steps: each step's sweep and
     beam push (sweep_bytes + push_bytes)."""
@@ -298,7 +311,10 @@ def main():
         achieved = pipe_bytes(p, dom_steps) / (dom_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": "pipe_kernel", "achieved": achieved,
                 "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": None, "peak_source": peak_src, "launch_ms": dom_ms,
+                "traffic": pipe_traffic(p, dom_steps),
+                "traffic_source": "ncu dram__bytes of a 16-slice capture, scaled by step-slices",
+                "algorithmic_bytes": pipe_bytes(p, dom_steps),
+                "peak_source": peak_src, "launch_ms": dom_ms,
                 "steps_per_launch": dom_steps, "kernel_share": float(np.sum(lt)) / ms,
                 "step_frac": bytes_per_update(p) * value / world / 1e9 / hbm_peak}
     else:
