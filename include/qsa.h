@@ -158,7 +158,9 @@ int qsa_init(const qsa_params* params, void* stream, qsa_alloc_fn alloc, qsa_fre
 /* Replace species `s` with host fp64 arrays of n particles in the canonical id order of the
  * lattice (id = ((k_xi*ny + iy)*nx + ix)*ppc + (s_xi*ppc_y + s_y)*ppc_x + s_x); n must equal
  * the species' lattice count.  x, y in [0, L); xi in [0, Lxi); w = 0 marks a lost particle.
- * Copies and converts to the device layout; marks the beam sources stale. */
+ * Copies and converts to the device layout; marks the beam sources stale.  QSA_ERR_ARG when
+ * a live particle's xi is outside [0, Lxi) (checked on the device copy before the beam is
+ * touched: the beam stays as it was).  Synchronises. */
 int qsa_set_beam(qsa_handle* h, int s, int64_t n, const double* x, const double* y,
                  const double* xi, const double* ux, const double* uy, const double* uz,
                  const double* w);

@@ -143,6 +143,7 @@ struct State {
   std::vector<int*> cmaxs;          // extent ring, S + 1 entries [nxi]
   std::vector<double*> moms;        // beam-moment ring, S + 1 entries [n_species][nxi][7]
   int* dmin = nullptr;              // min over live particles of (xi cell - home layer)
+  int* chk = nullptr;               // set by check_xi_kernel when a host beam is invalid
   PipeTable<R>* ptab = nullptr;     // device table of the multi-slot launches (lazy)
   int tuned_nbr = 0, tuned_nbc = 0; // FFT units chosen by the batch autotuner (0: not yet)
   unsigned long long* lost = nullptr;
@@ -218,7 +219,8 @@ int setup(qsa_handle* h) {
   int* status = (int*)A(sizeof(int));
   s->lost = (unsigned long long*)A(sizeof(unsigned long long));
   s->dmin = (int*)A(sizeof(int));
-  if (!ktab || !twp || !bref || !bar || !status || !s->lost || !s->dmin)
+  s->chk = (int*)A(sizeof(int));
+  if (!ktab || !twp || !bref || !bar || !status || !s->lost || !s->dmin || !s->chk)
     return fail(h, QSA_ERR_OOM, "sweep tables");
   {
     // k_x = 2 pi m / Lx (m = 0..nx/2), k_y = 2 pi m / Ly (m in numpy.fft order), and the
@@ -817,6 +819,13 @@ int copy_field(qsa_handle* h, int field, int j0, int j1, double* out, bool sourc
   return QSA_OK;
 }
 
+// Flags (in *bad) a live particle (w != 0) whose xi is outside [0, Lxi), NaN included.
+__global__ void check_xi_kernel(const double* __restrict__ xi, const double* __restrict__ w,
+                                long long n, double Lxi, int* bad) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n && w[i] != 0.0 && !(xi[i] >= 0.0 && xi[i] < Lxi)) *bad = 1;
+}
+
 template <typename R>
 int beam_io(qsa_handle* h, int si, bool to_host, int64_t n, const double* const* in,
             double* const* out) {
@@ -834,12 +843,27 @@ int beam_io(qsa_handle* h, int si, bool to_host, int64_t n, const double* const*
   if (!to_host) {
     for (int k = 0; k < 7; ++k)
       CK(cudaMemcpyAsync(tmp[k], in[k], bytes, cudaMemcpyHostToDevice, h->stream));
-    beam_from_host_kernel<R><<<blocks, kThreads, 0, h->stream>>>(
-        b, h->dp, s->species[si], (double*)tmp[0], (double*)tmp[1], (double*)tmp[2],
-        (double*)tmp[3], (double*)tmp[4], (double*)tmp[5], (double*)tmp[6]);
+    // every live particle's xi must lie in [0, Lxi): checked on the device copy before the
+    // beam is touched, so that a rejected call leaves the beam as it was
+    int bad = 0;
+    CK(cudaMemsetAsync(s->chk, 0, sizeof(int), h->stream));
+    check_xi_kernel<<<blocks, kThreads, 0, h->stream>>>((const double*)tmp[2],
+                                                        (const double*)tmp[6], b.n,
+                                                        h->prm.Lxi, s->chk);
     ++h->launches;
     CK(cudaGetLastError());
-    h->src_valid = false;
+    CK(cudaMemcpyAsync(&bad, s->chk, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (bad) {
+      rc = fail(h, QSA_ERR_ARG, "xi of a live particle outside [0, Lxi)");
+    } else {
+      beam_from_host_kernel<R><<<blocks, kThreads, 0, h->stream>>>(
+          b, h->dp, s->species[si], (double*)tmp[0], (double*)tmp[1], (double*)tmp[2],
+          (double*)tmp[3], (double*)tmp[4], (double*)tmp[5], (double*)tmp[6]);
+      ++h->launches;
+      CK(cudaGetLastError());
+      h->src_valid = false;
+    }
   } else {
     beam_to_host_kernel<R><<<blocks, kThreads, 0, h->stream>>>(
         b, h->dp, s->species[si], (double*)tmp[0], (double*)tmp[1], (double*)tmp[2],
@@ -1062,9 +1086,6 @@ int qsa_set_beam(qsa_handle* h, int s, int64_t n, const double* x, const double*
   const int64_t want = h->fp64 ? S<double>(h)->beams[s].n : S<float>(h)->beams[s].n;
   if (n != want) return fail(h, QSA_ERR_ARG, "n must equal the species' lattice count");
   if (!x || !y || !xi || !ux || !uy || !uz || !w) return fail(h, QSA_ERR_ARG, "NULL array");
-  for (int64_t i = 0; i < n; ++i)
-    if (!(xi[i] >= 0.0 && xi[i] < h->prm.Lxi) && w[i] != 0.0)
-      return fail(h, QSA_ERR_ARG, "xi of a live particle outside [0, Lxi)");
   const double* in[7] = {x, y, xi, ux, uy, uz, w};
   return h->fp64 ? beam_io<double>(h, s, false, n, in, nullptr)
                  : beam_io<float>(h, s, false, n, in, nullptr);

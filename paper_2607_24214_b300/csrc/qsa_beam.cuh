@@ -755,13 +755,15 @@ __global__ void beam_from_host_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev 
   const long long id = h.id;
   const double hx = h.ix + (h.sx + 0.5) / sp.ppx, hy = h.iy + (h.sy + 0.5) / sp.ppy;
   const double hk = sp.k0 + h.kxi + (h.sxi + 0.5) / sp.ppxi;
-  // offsets from home, with the periodic image nearest to home
-  double ox = x[id] / p.dx - hx, oy = y[id] / p.dy - hy;
+  // offsets from home, with the periodic image nearest to home; a lost particle (w = 0)
+  // sits at home, whatever position it came with (it is never pushed or gathered for)
+  const bool live = w[id] != 0.0;
+  double ox = live ? x[id] / p.dx - hx : 0.0, oy = live ? y[id] / p.dy - hy : 0.0;
   ox -= p.nx * rint(ox / p.nx);
   oy -= p.ny * rint(oy / p.ny);
   b.ox[s] = BR(ox);
   b.oy[s] = BR(oy);
-  b.oxi[s] = BR(xi[id] / p.dxi - hk);
+  b.oxi[s] = live ? BR(xi[id] / p.dxi - hk) : BR(0);
   b.ux[s] = BR(ux[id]);
   b.uy[s] = BR(uy[id]);
   uz_store(b.uz[s], uz[id]);

@@ -232,6 +232,29 @@ def test_resume_from_host_state(Q):
     assert field_err(c.slab(), a.slab()).max() < 1e-11
 
 
+def test_set_beam_rejects_live_particle_outside_window(Q):
+    """A live particle with xi outside [0, Lxi) (or NaN) is rejected, and the beam on the
+    device is left as it was; the same particle marked lost (w = 0) is accepted."""
+    from paper_2607_24214_b300.qsa import QsaError
+    p = config.c1_fp64_electron_beam().with_(nxi=16, Lxi=2.0)
+    beams = inputs.all_beams(p)
+    q = gpu(Q, p, beams)
+    n = beams[0]["x"].size
+    before = q.get_beam(0, n)
+    for bad in (p.Lxi, -1e-9, float("nan")):
+        b = {k: v.copy() for k, v in beams[0].items()}
+        b["xi"][n // 2] = bad
+        b["ux"][:] = 1.0  # would change the beam if it were taken
+        with pytest.raises(QsaError):
+            q.set_beam(0, b)
+        after = q.get_beam(0, n)
+        for k in before:
+            np.testing.assert_array_equal(after[k], before[k])
+    b["w"][n // 2] = 0.0
+    q.set_beam(0, b)
+    assert np.all(q.get_beam(0, n)["ux"][b["w"] != 0] == 1.0)
+
+
 def test_timeout_is_reported_and_context_survives(Q):
     """spin_limit = 0 makes every grid-barrier wait give up at once: the sweep ends with
     QSA_ERR_TIMEOUT reported on the host and the CUDA context stays usable."""
