@@ -4,8 +4,11 @@ One step = one beam step of the method: a full plasma sweep (every xi slice: pus
 FFT field solves, predictor-corrector for B_perp) followed by the beam push with the deposit
 of the next sweep's beam sources.  Workload: the 256x256, 1024-slice, 4-ppc mixed precision
 electron-beam run (5.4e8 beam macroparticles), synthetic seeded inputs, state resident in
-HBM.  The steps run through qsa_advance with pipeline_depth steps in flight per persistent
-launch (a wavefront in xi; the same arithmetic as the steps one after the other).  Also
+HBM; by default its 200 beam steps are timed, through the linear stage into saturation
+(later steps cost more: the filamented beam's particles deposit away from their lattice
+homes), and the first launch's rate is reported beside it.  The steps run through
+qsa_advance with pipeline_depth steps in flight per persistent launch (a wavefront in xi;
+the same arithmetic as the steps one after the other).  Also
 measured: the same workload on the FP64 path, an end-to-end job through host buffers, the
 roofline of the dominant kernel (the pipelined launch), and the FP64 oracle on a bounded
 sample (CPU baseline).
@@ -58,17 +61,21 @@ def sweep_bytes(p):
     return 40.0 * ppc * cells * p.nxi + (16.0 + 24.0) * cells * (p.nxi + 1)
 
 
-# DRAM bytes (read + write) of one pipe_kernel launch from an ncu capture of the same kernel
-# on a small case of the same grid and depth: 256 x 256, 16 slices, 16 steps in flight
-# (profiles/pipe_kernel_c2grid_16slices_depth16.md): 14.55 GB read + 20.53 GB written over
-# 16 steps x 17 slices.  Every step-slice touches the same scratch and its share of the beam
-# stream, so a launch's traffic scales with its step-slices.
-PIPE_DRAM_BYTES_PER_STEP_SLICE = (14.553429e9 + 20.534880e9) / (16 * 17)
+# DRAM bytes (read + write) of each full 16-step pipe_kernel launch of this workload's
+# 200 timed steps (after 3 warm-up steps), from one ncu capture of dram__bytes_read.sum and
+# dram__bytes_write.sum (one pass) of `bench.py --no-fp64 --no-e2e --no-cpu --no-batch`
+# (profiles/pipe_kernel_c2_200steps_dram.md), in TB.  Later launches move more: the
+# filamented beam's particles deposit away from their homes.
+PIPE_DRAM_TB_PER_LAUNCH = [2.5183, 2.5182, 2.5183, 2.5183, 2.5179, 2.5196, 2.5304, 2.5834, 2.6468, 2.7274, 2.8174, 2.9207]
 
 
-def pipe_traffic(p, depth):
-    """DRAM bytes of one pipelined launch of `depth` steps, scaled from the capture above."""
-    return PIPE_DRAM_BYTES_PER_STEP_SLICE * depth * (p.nxi + 1)
+def pipe_traffic(p, depth, n_launches):
+    """Mean DRAM bytes of the first n_launches full launches, from the capture above; None
+    for another grid or depth, which the capture does not cover."""
+    if (p.nx, p.ny, p.nxi, depth) != (256, 256, 1024, 16) or n_launches < 1:
+        return None
+    tb = PIPE_DRAM_TB_PER_LAUNCH[:n_launches]
+    return 1e12 * sum(tb) / len(tb)
 
 
 def pipe_bytes(p, depth):
@@ -251,12 +258,13 @@ def run_reference(args, p):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--steps", type=int, default=200,
+                    help="timed beam steps (the workload's 200: the linear stage and saturation)")
     ap.add_argument("--depth", type=int, default=16, help="beam steps in flight per launch")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=4)
-    ap.add_argument("--e2e-steps", type=int, default=16)
+    ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -311,15 +319,24 @@ def main():
         achieved = pipe_bytes(p, dom_steps) / (dom_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": "pipe_kernel", "achieved": achieved,
                 "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": pipe_traffic(p, dom_steps),
-                "traffic_source": "ncu dram__bytes of a 16-slice capture, scaled by step-slices",
+                "traffic": pipe_traffic(p, dom_steps, len(full)),
+                "traffic_source": "ncu dram__bytes of the full launches of this workload",
                 "algorithmic_bytes": pipe_bytes(p, dom_steps),
                 "peak_source": peak_src, "launch_ms": dom_ms,
                 "steps_per_launch": dom_steps, "kernel_share": float(np.sum(lt)) / ms,
-                "step_frac": bytes_per_update(p) * value / world / 1e9 / hbm_peak}
+                "step_frac": bytes_per_update(p) * value / world / 1e9 / hbm_peak,
+                "launch_ms_each": [round(float(t), 1) for t in lt]}
+        # the first launch covers the linear stage only (the steps right after the warm-up);
+        # later steps cost more once the beam has filamented and its particles have left
+        # their lattice homes
+        first_ms = float(lt[0]) if len(lt) else ms
+        first_steps = min(args.depth, args.steps)
+        first = {"steps": first_steps, "ms_per_step": first_ms / first_steps,
+                 "value": ups * first_steps / (first_ms * 1e-3)}
     else:
         with Clocks(local) as clk:
             ms, sw, pu, launches = time_steps(q, p, args.steps, args.warmup, torch, stream)
+        first = None
         barrier(world)
         ms = max_over_ranks(ms, world)
         value = ups * args.steps * world / (ms * 1e-3)
@@ -351,6 +368,8 @@ def main():
                        "parallelism": f"replicas{world}"},
             "gpu_launches": launches, "roofline": roof,
             "clocks": clk.summary(), "status": d["status"]}
+    if first is not None:
+        line["first_launch"] = first
 
     if not args.no_fp64:
         # the FP64 path, pipelined as deep as the timed steps (memory: FP64 slabs are 4.3 GB)
@@ -364,7 +383,9 @@ def main():
         v64 = ups * args.fp64_steps / (ms64 * 1e-3)
         line["fp64"] = {"value": v64, "unit": "updates/s", "steps": args.fp64_steps,
                         "pipeline_depth": d64, "ms_per_step": ms64 / args.fp64_steps,
-                        "speedup_mixed_over_fp64": value / v64}
+                        "speedup_mixed_over_fp64": ((first["value"] if first else value) / v64),
+                        "speedup_basis": "mixed rate of the first pipelined launch (the same "
+                                         "linear-stage steps as the FP64 run)"}
 
     if not args.no_e2e:
         line["e2e"] = e2e(p, args.e2e_steps, torch, stream)

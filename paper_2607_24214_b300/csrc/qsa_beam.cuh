@@ -224,12 +224,12 @@ __device__ __forceinline__ void home_weights(BR hx, BR hy, BR hk, BR ox, BR oy, 
 // Deposit, per source quantity, dev W(x) + ref (W(x) - W(home)) (ref = 0 for J_x, J_y) for a
 // particle of home column ix, home sub-cell position (hx, hy, hk) and offsets (ox, oy, oxi) in
 // cells.  In the home cell the trilinear weight differences come from the offsets without
-// cancellation.
+// cancellation.  Out of it, home_ref = false leaves the -ref W(home) part to the caller.
 template <typename BR>
 __device__ __forceinline__ void deposit_particle(const Group<BR>& g, BR* src, const DevParams& p,
                                                  int ix, BR hx, BR hy, BR hk, BR ox, BR oy,
                                                  BR oxi, BR dS, BR dJz, BR jx, BR jy, BR refS,
-                                                 BR refJz) {
+                                                 BR refJz, bool home_ref = true) {
   const BR lx = hx + ox, ly = hy + oy, lk = hk + oxi;
   const int nx = p.nx;
   if (lx >= BR(0) && lx < BR(1) && ly >= BR(0) && ly < BR(1) && lk >= BR(0) && lk < BR(1)) {
@@ -257,7 +257,7 @@ __device__ __forceinline__ void deposit_particle(const Group<BR>& g, BR* src, co
   }
   // left the home cell: full weights at the new corners, minus the reference at home
 #pragma unroll 1
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = 0; pass < (home_ref ? 2 : 1); ++pass) {
     const BR mx = pass ? hx : lx, my = pass ? hy : ly, mk = pass ? hk : lk;
     const BR fx = floor(mx), fy = floor(my), fk = floor(mk);
     const BR ex = mx - fx, ey = my - fy, ek = mk - fk;
@@ -686,11 +686,50 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
           }
         }
       } else {
+        // the reference removed at home by the thread's particles that left the home cell:
+        // summed per home corner over both particles, then one lane-aggregated deposit
+        BR hw[2][2][2];
+#pragma unroll
+        for (int ck = 0; ck < 2; ++ck)
+#pragma unroll
+          for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+            for (int cx = 0; cx < 2; ++cx) hw[ck][cy][cx] = BR(0);
 #pragma unroll
         for (int u = 0; u < 2; ++u)
-          if (ok[u])
+          if (ok[u]) {
+            const bool away = lane_agg && !in_cell(hx[u] + dox[u], hy[u] + doy[u], hk[u] + doxi[u]);
             deposit_particle(g, src, p, ix, hx[u], hy[u], hk[u], dox[u], doy[u], doxi[u],
-                             dv[u][0], dv[u][1], dv[u][2], dv[u][3], refS, refJz);
+                             dv[u][0], dv[u][1], dv[u][2], dv[u][3], refS, refJz, !away);
+            if (away) {
+#pragma unroll
+              for (int ck = 0; ck < 2; ++ck)
+#pragma unroll
+                for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+                  for (int cx = 0; cx < 2; ++cx)
+                    hw[ck][cy][cx] += (ck ? hk[u] : BR(1) - hk[u]) * (cy ? hy[u] : BR(1) - hy[u]) *
+                                      (cx ? hx[u] : BR(1) - hx[u]);
+            }
+          }
+        if (lane_agg) {
+          const int lane = threadIdx.x & 31;
+#pragma unroll
+          for (int ck = 0; ck < 2; ++ck)
+#pragma unroll
+            for (int cy = 0; cy < 2; ++cy) {
+              BR* row = g.tile + (size_t)(ck * 4 + 1 + cy) * 4 * nx;
+#pragma unroll
+              for (int q = 0; q < 2; ++q) {
+                const BR rf = q ? -refJz : -refS;
+                const BR lft = rf * hw[ck][cy][0], rgt = rf * hw[ck][cy][1];
+                const BR from = __shfl_up_sync(0xffffffffu, rgt, 1);
+                const BR v = lft + (lane ? from : BR(0));
+                if (v != BR(0)) atomicAdd(row + (size_t)q * nx + ix, v);
+                if (lane == 31 && rgt != BR(0)) atomicAdd(row + (size_t)q * nx + x1, rgt);
+              }
+            }
+        }
       }
     }
   }
