@@ -127,9 +127,15 @@ def test_sweep_c1_mixed(Q):
     assert d["charge"].max() < 1e-5 * p.Lx * p.Ly
 
 
-@pytest.mark.parametrize("geom", ["2d3v", "odd", "radix3", "tiny"])
+@pytest.mark.parametrize("geom", ["2d3v", "odd", "radix3", "tiny", "ppc1_odd"])
 def test_sweep_geometries_fp64(Q, geom):
-    if geom == "2d3v":
+    if geom == "ppc1_odd":
+        # one plasma particle per cell on an odd grid: a deposit chunk of 9 particles is not
+        # a multiple of 16 bytes, so its L2 prefetch is skipped
+        p = config.c1_fp64_electron_beam().with_(nx=9, ny=12, Lx=9 * 0.2, Ly=12 * 0.2,
+                                                 nxi=24, Lxi=3.0, ppc_plasma_x=1,
+                                                 ppc_plasma_y=1)
+    elif geom == "2d3v":
         p = config.v_pair_single_mode(Lxi=6.0, eps=1e-3)
     elif geom == "odd":
         p = config.c1_fp64_electron_beam().with_(nx=9, ny=12, Lx=9 * 0.2, Ly=12 * 0.2,
@@ -140,6 +146,13 @@ def test_sweep_geometries_fp64(Q, geom):
     else:
         p = config.c1_fp64_electron_beam().with_(nx=2, ny=3, Lx=0.4, Ly=0.6, nxi=8, Lxi=1.0)
     _sweep_parity(Q, p, TOL["fp64"])
+
+
+def test_sweep_ppc1_odd_mixed(Q):
+    p = config.c1_fp64_electron_beam().with_(nx=9, ny=12, Lx=9 * 0.2, Ly=12 * 0.2, nxi=24,
+                                             Lxi=3.0, ppc_plasma_x=1, ppc_plasma_y=1,
+                                             precision="mixed")
+    _sweep_parity(Q, p, TOL["mixed"])
 
 
 def test_sweep_without_beam(Q):
