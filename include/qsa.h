@@ -95,12 +95,13 @@ typedef struct {
   int32_t n_diag_modes;    /* transverse modes whose amplitude every sweep records (0..16) */
   int32_t _pad;
   qsa_kvec diag_modes[QSA_MAX_MODES]; /* k != 0, |mx| <= nx/2, |my| <= ny/2 */
-  double pc_tol;           /* 0: exactly n_pc_iter field solves per slice.  > 0: tolerance
-                              mode of the predictor-corrector for B_perp (section "QS-PIC"
-                              of the paper, iterated to convergence): stop after the first
-                              solve whose relative change ||B_perp(n) - B_perp(n-1)|| /
-                              ||B_perp(n)|| is below pc_tol, after n_pc_iter solves at most;
-                              the count per slice is reported in qsa_diag.pc_iters */
+  double pc_tol;           /* 0: exactly n_pc_iter field solves per slice.  > 0: the B_perp
+                              predictor-corrector (part of the QS-PIC scheme, whose discrete
+                              steps the paper does not print) iterated to a tolerance: stop
+                              after the first solve whose relative change
+                              ||B_perp(n) - B_perp(n-1)|| / ||B_perp(n)|| (2-norms over the
+                              grid) is below pc_tol, after n_pc_iter solves at most; the
+                              count per slice is reported in qsa_diag.pc_iters */
 } qsa_params;
 
 /* Allocator callbacks: alloc returns a device pointer (NULL on failure) of at least `bytes`
