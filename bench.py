@@ -263,7 +263,8 @@ def main():
     ap.add_argument("--depth", type=int, default=16, help="beam steps in flight per launch")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--fp64-steps", type=int, default=16,
+                    help="FP64 steps, pipelined as deep as the mixed run (at most --depth)")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -372,7 +373,7 @@ def main():
         line["first_launch"] = first
 
     if not args.no_fp64:
-        # the FP64 path, pipelined as deep as the timed steps (memory: FP64 slabs are 4.3 GB)
+        # the FP64 path, pipelined as deep as the mixed run (137 GB on the device at depth 16)
         d64 = min(args.fp64_steps, args.depth)
         p64 = p.with_(precision="fp64", pipeline_depth=d64)
         q = QSA(p64)
