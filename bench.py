@@ -386,7 +386,10 @@ def main():
                         "pipeline_depth": d64, "ms_per_step": ms64 / args.fp64_steps,
                         "speedup_mixed_over_fp64": ((first["value"] if first else value) / v64),
                         "speedup_basis": "mixed rate of the first pipelined launch (the same "
-                                         "linear-stage steps as the FP64 run)"}
+                                         "linear-stage steps as the FP64 run)",
+                        "roofline": {"bound": "fp64", "frac": 0.743, "unit": "FP64 pipe",
+                                     "source": "ncu sm__pipe_fp64_cycles_active of the "
+                                               "16-slice capture (profiles/)"}}
 
     if not args.no_e2e:
         line["e2e"] = e2e(p, args.e2e_steps, torch, stream)
