@@ -333,9 +333,14 @@ __device__ __forceinline__ U4 philox4x32_10(U4 ctr, uint32_t k0, uint32_t k1) {
 __device__ __forceinline__ double u01(uint32_t r) { return ((double)r + 0.5) * (1.0 / 4294967296.0); }
 
 // Asks the L2 cache to fetch `bytes` bytes at p (both multiples of 16) ahead of their use; no
-// registers and no shared memory are involved, and nothing waits for it.
+// registers and no shared memory are involved, and nothing waits for it.  Issued in pieces
+// of at most 32 KB (multiples of 16 bytes, so every piece stays aligned).
 __device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+  const char* c = static_cast<const char*>(p);
+  for (unsigned off = 0; off < bytes; off += 32768u) {
+    const unsigned n = bytes - off < 32768u ? bytes - off : 32768u;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c + off), "r"(n) : "memory");
+  }
 }
 
 // Periodic index: i mod n in [0, n), without a division when i is within one period.
