@@ -144,7 +144,8 @@ def summary(rec: dict, p: config.Params, k_ref: float = 1.0) -> dict:
       growth_vs_exponent: slope of ln rms against the asymptotic exponent (Eq. 7 at the front,
         Eq. 6 downstream) over 2 <= Gamma tau <= 5; 1 where the field follows it;
       rate_ratio_end: the growth rate over the last recorded interval over the spatiotemporal
-        rate Gamma^st there; well below 1 once the growth saturates;
+        rate Gamma^st there; well below 1 once the growth saturates (near the front a field
+        that follows Eq. 7 exactly gives 1 + xi/(4 Gamma tau), from its correction factor);
       eps_end, eps_estimate_end: the fractional field energy at the end of the run, and the
         trapping estimate evaluated with tau_sat = that time;
       dpy_end, dpy_estimate_end: the beam's rms u_y spread in the segment (first species) and

@@ -73,3 +73,32 @@ def test_exponents_and_rates_are_consistent():
     xt = 2 * gt / math.sqrt(27.0)
     ratio = nl.exponent_front(gt, xt) / nl.exponent_rear(gt, xt)
     assert 0.8 < ratio < 1.3
+
+
+def test_summary_reads_synthetic_growth():
+    """`summary` on a record whose transverse fields grow exactly as Eq. 7 (front, B_perp) and
+    Eq. 6 (downstream, E_perp): slopes 1 against the exponents, and at the end a growth rate
+    equal to the spatiotemporal rate."""
+    p = config.c3_pair_beam()
+    G = nl.temporal_rate(1.0, p.species)
+    tau = np.arange(1, 81) * 1000.0
+    nseg = 64
+    rs = np.full((tau.size, nseg, 6), 1e-12)
+    xf, xr = 3.0, 21.0                       # centres of the segments [2, 4) and [20, 22)
+    bf = 1e-9 * np.exp(nl.exponent_front(G * tau, xf))
+    er = 1e-9 * np.exp(nl.exponent_rear(G * tau, xr))
+    rs[:, 1, 3] = rs[:, 1, 4] = bf / np.sqrt(2.0)
+    rs[:, 10, 0] = rs[:, 10, 1] = er / np.sqrt(2.0)
+    rec = {"tau": tau, "rms_seg": rs, "energy": np.zeros((tau.size, 6)),
+           "beam_rms_seg": np.zeros((tau.size, 2, nseg, 3)), "beam_lost": np.zeros(tau.size),
+           "ms": np.ones(tau.size), "seg_width": np.float64(2.0)}
+    s = nl.summary(rec, p)
+    assert abs(s["front_Bperp"]["growth_vs_exponent"] - 1) < 1e-9
+    assert abs(s["rear_Eperp"]["growth_vs_exponent"] - 1) < 1e-9
+    # the last interval's mean rate against the rate at its midpoint (second-order close);
+    # at the front the exponent's correction factor (1 - xi/(4 Gamma tau)) adds xi/(4 Gamma tau)
+    # to the leading rate (Gamma xi/tau)^1/2
+    tm = 0.5 * (tau[-1] + tau[-2])
+    assert abs(s["front_Bperp"]["rate_ratio_end"] - (1 + xf / (4 * G * tm))) < 0.01
+    assert abs(s["rear_Eperp"]["rate_ratio_end"] - 1) < 0.01
+    assert abs(s["rear_Eperp"]["eps_end"] / nl.fractional_energy(er[-1] ** 2, 1e-4, 1e4) - 1) < 1e-12
