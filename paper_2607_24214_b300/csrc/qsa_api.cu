@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/qsa.h"
+#include <nvtx3/nvToolsExt.h>
 #include "qsa_beam.cuh"
 #include "qsa_common.cuh"
 #include "qsa_fft.cuh"
@@ -1003,10 +1004,21 @@ int validate(const qsa_params* p, std::string& why) {
 
 }  // namespace
 
+namespace {
+// An NVTX range around each call of the C ABI, so that a timeline tool shows which call a
+// launch or a copy belongs to (NVTX is header-only: without a tool attached it costs a
+// few nanoseconds per call).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
+
 extern "C" {
 
 int qsa_init(const qsa_params* params, void* stream, qsa_alloc_fn alloc, qsa_free_fn free_fn,
              void* alloc_ctx, qsa_handle** out) {
+  NvtxRange nvtx_range("qsa_init");
   if (!out) return fail(nullptr, QSA_ERR_ARG, "out is NULL");
   *out = nullptr;
   std::string why;
@@ -1081,6 +1093,7 @@ int qsa_init(const qsa_params* params, void* stream, qsa_alloc_fn alloc, qsa_fre
 int qsa_set_beam(qsa_handle* h, int s, int64_t n, const double* x, const double* y,
                  const double* xi, const double* ux, const double* uy, const double* uz,
                  const double* w) {
+  NvtxRange nvtx_range("qsa_set_beam");
   if (!h) return QSA_ERR_ARG;
   if (s < 0 || s >= h->prm.n_species) return fail(h, QSA_ERR_ARG, "species index");
   const int64_t want = h->fp64 ? S<double>(h)->beams[s].n : S<float>(h)->beams[s].n;
@@ -1093,6 +1106,7 @@ int qsa_set_beam(qsa_handle* h, int s, int64_t n, const double* x, const double*
 
 int qsa_get_beam(qsa_handle* h, int s, int64_t cap, double* x, double* y, double* xi,
                  double* ux, double* uy, double* uz, double* w, int64_t* n_out) {
+  NvtxRange nvtx_range("qsa_get_beam");
   if (!h) return QSA_ERR_ARG;
   if (s < 0 || s >= h->prm.n_species) return fail(h, QSA_ERR_ARG, "species index");
   const int64_t n = h->fp64 ? S<double>(h)->beams[s].n : S<float>(h)->beams[s].n;
@@ -1106,17 +1120,20 @@ int qsa_get_beam(qsa_handle* h, int s, int64_t cap, double* x, double* y, double
 }
 
 int qsa_plasma_sweep(qsa_handle* h) {
+  NvtxRange nvtx_range("qsa_plasma_sweep");
   if (!h) return QSA_ERR_ARG;
   return h->fp64 ? sweep<double>(h) : sweep<float>(h);
 }
 
 int qsa_beam_step(qsa_handle* h) {
+  NvtxRange nvtx_range("qsa_beam_step");
   if (!h) return QSA_ERR_ARG;
   if (h->sweeps == 0) return fail(h, QSA_ERR_STATE, "beam step before any sweep");
   return h->fp64 ? beam_step<double>(h) : beam_step<float>(h);
 }
 
 int qsa_advance(qsa_handle* h, int32_t n_steps) {
+  NvtxRange nvtx_range("qsa_advance");
   if (!h) return QSA_ERR_ARG;
   if (n_steps < 0) return fail(h, QSA_ERR_ARG, "n_steps must be >= 0");
   if (h->prm.pipeline_depth > 1) {
@@ -1133,6 +1150,7 @@ int qsa_advance(qsa_handle* h, int32_t n_steps) {
 }
 
 int qsa_advance_batch(qsa_handle* const* handles, int32_t n_handles, int32_t n_steps) {
+  NvtxRange nvtx_range("qsa_advance_batch");
   if (!handles || n_handles < 1) return fail(nullptr, QSA_ERR_ARG, "no handles");
   qsa_handle* lead = handles[0];
   if (!lead) return fail(nullptr, QSA_ERR_ARG, "NULL handle");
@@ -1154,11 +1172,13 @@ int qsa_advance_batch(qsa_handle* const* handles, int32_t n_handles, int32_t n_s
 }
 
 int qsa_diagnostics(qsa_handle* h, qsa_diag* out) {
+  NvtxRange nvtx_range("qsa_diagnostics");
   if (!h || !out) return QSA_ERR_ARG;
   return h->fp64 ? diagnostics<double>(h, out) : diagnostics<float>(h, out);
 }
 
 int qsa_copy_field(qsa_handle* h, int field, int j0, int j1, double* host_out) {
+  NvtxRange nvtx_range("qsa_copy_field");
   if (!h || !host_out) return QSA_ERR_ARG;
   if (field < 0 || field > 5 || j0 < 0 || j1 > h->dp.nk || j0 >= j1)
     return fail(h, QSA_ERR_ARG, "field or slice range");
@@ -1167,6 +1187,7 @@ int qsa_copy_field(qsa_handle* h, int field, int j0, int j1, double* host_out) {
 }
 
 int qsa_copy_source(qsa_handle* h, int q, int j0, int j1, double* host_out) {
+  NvtxRange nvtx_range("qsa_copy_source");
   if (!h || !host_out) return QSA_ERR_ARG;
   if (q < 0 || q > 3 || j0 < 0 || j1 > h->dp.nk || j0 >= j1)
     return fail(h, QSA_ERR_ARG, "source or node range");
@@ -1181,6 +1202,7 @@ int qsa_copy_source(qsa_handle* h, int q, int j0, int j1, double* host_out) {
 int qsa_field_solve(qsa_handle* h, const double* S_, const double* Jx, const double* Jy,
                     const double* Jz, const double* Dx, const double* Dy, double kappa2,
                     double* out) {
+  NvtxRange nvtx_range("qsa_field_solve");
   if (!h || !S_ || !Jx || !Jy || !Jz || !Dx || !Dy || !out) return QSA_ERR_ARG;
   if (!(kappa2 >= 0)) return fail(h, QSA_ERR_ARG, "kappa2 must be >= 0");
   const double* in[6] = {S_, Jx, Jy, Jz, Dx, Dy};
