@@ -5,8 +5,8 @@ FFT field solves, predictor-corrector for B_perp) followed by the beam push with
 of the next sweep's beam sources.  Workload: the 256x256, 1024-slice, 4-ppc mixed precision
 electron-beam run (5.4e8 beam macroparticles), synthetic seeded inputs, state resident in
 HBM; by default its 200 beam steps are timed, through the linear stage into saturation
-(later steps cost more: the filamented beam's particles deposit away from their lattice
-homes), and the first launch's rate is reported beside it.  The steps run through
+(later steps cost more: the filamented beam's particles gather and deposit away from their
+lattice homes), and the first launch's rate is reported beside it.  The steps run through
 qsa_advance with pipeline_depth steps in flight per persistent launch (a wavefront in xi;
 the same arithmetic as the steps one after the other).  Also
 measured: the same workload on the FP64 path, an end-to-end job through host buffers, the
