@@ -66,7 +66,8 @@ def sweep_bytes(p):
 # dram__bytes_write.sum (one pass) of `bench.py --no-fp64 --no-e2e --no-cpu --no-batch`
 # (profiles/pipe_kernel_c2_200steps_dram.md), in TB.  Later launches move more: the
 # filamented beam's particles deposit away from their homes.
-PIPE_DRAM_TB_PER_LAUNCH = [2.5183, 2.5182, 2.5183, 2.5183, 2.5179, 2.5196, 2.5304, 2.5834, 2.6468, 2.7274, 2.8174, 2.9207]
+PIPE_DRAM_TB_PER_LAUNCH = [2.5183, 2.5182, 2.5183, 2.5183, 2.5179, 2.5196,
+                           2.5304, 2.5834, 2.6468, 2.7274, 2.8174, 2.9207]
 
 
 def pipe_traffic(p, depth, n_launches):
@@ -270,6 +271,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="skip the full-size pair-beam workload (224 GB on the device)")
     ap.add_argument("--batch-steps", type=int, default=4,
                     help="timed steps of the batched C4 scan (after 8 untimed, autotuning)")
     ap.add_argument("--steps-ref", type=int, default=2)
@@ -397,6 +400,9 @@ def main():
     if not args.no_batch:
         line["batched"] = batched(args.batch_steps, torch, stream)
 
+    if not args.no_c3:
+        line["pair_beam"] = pair_beam(torch, stream)
+
     if rank == 0 and not args.no_cpu:
         v, dt = cpu_baseline(p)
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
@@ -407,6 +413,37 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def pair_beam(torch, stream, steps=6, depth=3):
+    """The full-size pair-beam workload (512 x 512, 2048 slices, electrons and positrons of
+    4 ppc each, 4.3e9 beam particles, mixed precision, 224 GB on the device at depth 3):
+    `steps` timed beam steps after `depth` untimed ones (the linear stage).  Same metric."""
+    from paper_2607_24214_b300.qsa import QSA
+    p = config.c3_pair_beam().with_(pipeline_depth=depth)
+    torch.cuda.empty_cache()
+    try:
+        q = QSA(p)
+    except Exception as e:  # a device with less free memory than the workload needs
+        return {"workload": "c3_pair_beam_512x512_2048slices", "unavailable": str(e)[:200]}
+    q.advance(depth)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    q.advance(steps)
+    t1.record(stream)
+    t1.synchronize()
+    ms = t0.elapsed_time(t1)
+    st = q.diagnostics()["status"]
+    q.close()
+    del q
+    torch.cuda.empty_cache()
+    return {"workload": "c3_pair_beam_512x512_2048slices",
+            "value": updates_per_step(p) * steps / (ms * 1e-3),
+            "unit": "updates/s", "steps": steps, "warmup": depth, "pipeline_depth": depth,
+            "ms_per_step": ms / steps, "beam_particles": 2 * 4 * p.nx * p.ny * p.nxi,
+            "status": st}
 
 
 def batched(steps, torch, stream):
