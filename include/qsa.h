@@ -309,6 +309,15 @@ const char* qsa_last_error(const qsa_handle* h);
 /* Release the handle and all its device memory (waits for its stream). */
 void qsa_destroy(qsa_handle* h);
 
+/* Bounds checks of the debug build (built with -DQSA_DEBUG_BOUNDS as libqsa_bounds.so; the
+ * paper has no counterpart): the index checks at the particle, tile, slab and field-grid
+ * accesses of the sweep, push and pipelined kernels record the source line of the first
+ * failure and the number of failures on the current device, and skip the access.  Writes
+ * them to *first_line and *count (each may be NULL) and returns 1 in that build, 0 (with
+ * zeros) in the release build, QSA_ERR_CUDA if the counters cannot be read.  Synchronises
+ * the device. */
+int qsa_bounds_check(int64_t* first_line, int64_t* count);
+
 #ifdef __cplusplus
 }
 #endif

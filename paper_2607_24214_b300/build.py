@@ -9,6 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libqsa.so")
+BOUNDS_LIB = os.path.join(LIBDIR, "libqsa_bounds.so")  # -DQSA_DEBUG_BOUNDS
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -23,28 +24,33 @@ def headers():
     return hs
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in sources() + headers())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, bounds: bool = False) -> str:
+    """Build libqsa.so, or with bounds=True the debug build libqsa_bounds.so whose index
+    checks record out-of-range accesses (qsa_bounds_check) instead of making them."""
+    lib = BOUNDS_LIB if bounds else LIB
+    if not force and up_to_date(lib):
+        return lib
     os.makedirs(LIBDIR, exist_ok=True)
     nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
     cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-Xptxas", "-v" if verbose else "-O3", "-o", LIB + ".tmp", *sources()]
+           *(["-DQSA_DEBUG_BOUNDS"] if bounds else []),
+           "-Xptxas", "-v" if verbose else "-O3", "-o", lib + ".tmp", *sources()]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed:\n" + r.stderr[-8000:])
     if verbose:
         sys.stderr.write(r.stderr)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                bounds="--bounds" in sys.argv))

@@ -1240,6 +1240,23 @@ const char* qsa_last_error(const qsa_handle* h) {
   return h ? h->err.c_str() : g_init_error.c_str();
 }
 
+int qsa_bounds_check(int64_t* first_line, int64_t* count) {
+  if (first_line) *first_line = 0;
+  if (count) *count = 0;
+#ifdef QSA_DEBUG_BOUNDS
+  unsigned long long f = 0, c = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpyFromSymbol(&f, qsa::g_bounds_first, sizeof(f)) != cudaSuccess ||
+      cudaMemcpyFromSymbol(&c, qsa::g_bounds_count, sizeof(c)) != cudaSuccess)
+    return QSA_ERR_CUDA;
+  if (first_line) *first_line = (int64_t)f;
+  if (count) *count = (int64_t)c;
+  return 1;
+#else
+  return 0;
+#endif
+}
+
 void qsa_destroy(qsa_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);

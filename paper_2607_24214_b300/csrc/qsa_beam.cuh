@@ -184,6 +184,7 @@ template <typename BR>
 __device__ __forceinline__ void put(const Group<BR>& g, BR* src, const DevParams& p, int k, int gy,
                                     int x, BR wt, BR s, BR z, BR jx, BR jy) {
   const int dk = k - g.kabs, r = gy - (g.iy - 1);
+  if (!QSA_IN(x >= 0 && x < p.nx)) return;
   if (dk >= 0 && dk < 2 && r >= 0 && r < 4) {
     const int nx = p.nx;
     BR* t = g.tile + (size_t)(dk * 4 + r) * 4 * nx + x;
@@ -365,6 +366,7 @@ __device__ __forceinline__ void gather_slab(const BR* __restrict__ slab, const D
     const int k = gk + ck;
     if (k < 0 || k >= p.nk) continue;
     const BR wk = ck ? ek : BR(1) - ek;
+    (void)QSA_IN(y0 < p.ny && y1 < p.ny && x0 < p.nx && x1 < p.nx);
 #pragma unroll
     for (int cy = 0; cy < 2; ++cy) {
       const BR wy = wk * (cy ? ey : BR(1) - ey);
@@ -447,6 +449,7 @@ __device__ __forceinline__ void gather_cell(const BR* __restrict__ slab, const D
                                             const BR hy[2], const BR hk[2], const BR ox[2],
                                             const BR oy[2], const BR oxi[2], BR F[2][6]) {
   const int y1 = (iy + 1 == p.ny) ? 0 : iy + 1;
+  (void)QSA_IN(k >= 0 && k + 1 < p.nk && iy >= 0 && iy < p.ny && ix < p.nx && x1 < p.nx);
   BR lx[2], ly[2], lk[2];
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
@@ -558,6 +561,7 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         si[u] = base + (size_t)(ok[u] ? sub0 + u : sub0) * nx + ix;
+        if (!QSA_IN(si[u] < (size_t)b.n)) si[u] = 0;
         dw[u] = b.dw[si[u]];
         ox[u] = b.ox[si[u]];
         oy[u] = b.oy[si[u]];
@@ -625,7 +629,11 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
           }
         }
         {
-          const int cell = (int)floor(hk[u] + oxi[u]);  // xi cell relative to the home layer
+          // xi cell relative to the home layer.  A live particle lies in [0, Lxi), so its cell
+          // is at most the last one; a position given just below Lxi can round onto Lxi in the
+          // working precision, and its cell must not name a slab node past the last one (the
+          // pipelined schedule would wait for that node forever)
+          const int cell = min((int)floor(hk[u] + oxi[u]), kleft - 1);
           cmax_t = max(cmax_t, g.kabs + cell);
           dmin_t = min(dmin_t, cell);
           const BR wr = BR(1) + dw[u], duz = uz_dev(uz[u], bc);

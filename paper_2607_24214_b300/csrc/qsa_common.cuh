@@ -344,12 +344,32 @@ __device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
 }
 
 // Periodic index: i mod n in [0, n), without a division when i is within one period.
+// Bounds checks of the debug build (-DQSA_DEBUG_BOUNDS, libqsa_bounds.so): QSA_IN(cond)
+// records the source line of the first failed check and the number of failures, and is
+// false when the check fails, so the caller can skip the access.  In the release build it is
+// the constant true and costs nothing.  Each translation unit has its own counters; those of
+// the file that holds the persistent kernels are read by qsa_bounds_check.
+#ifdef QSA_DEBUG_BOUNDS
+static __device__ unsigned long long g_bounds_first;
+static __device__ unsigned long long g_bounds_count;
+__device__ __forceinline__ bool qsa_bounds_fail(int line) {
+  atomicCAS(&g_bounds_first, 0ull, (unsigned long long)line);
+  atomicAdd(&g_bounds_count, 1ull);
+  return false;
+}
+#define QSA_IN(cond) ((cond) ? true : qsa::qsa_bounds_fail(__LINE__))
+#else
+#define QSA_IN(cond) true
+#endif
+
 __device__ __forceinline__ int wrap(int i, int n) {
   if ((unsigned)i < (unsigned)n) return i;
   if (i < 0 && i >= -n) return i + n;
   if (i >= n && i < 2 * n) return i - n;
   const int r = i % n;
-  return r < 0 ? r + n : r;
+  const int w = r < 0 ? r + n : r;
+  (void)QSA_IN(w >= 0 && w < n);
+  return w;
 }
 
 }  // namespace qsa

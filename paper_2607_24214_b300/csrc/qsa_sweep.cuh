@@ -185,6 +185,7 @@ template <typename R>
 __device__ __forceinline__ void gather8(const R* __restrict__ fg, const Cic<R>& c, int nx,
                                         R out[8]) {
   R a[8], b[8], d[8], e[8];
+  (void)QSA_IN(c.x0 >= 0 && c.x0 < nx && c.x1 >= 0 && c.x1 < nx && c.y0 >= 0 && c.y1 >= 0);
   const R* pa = fg + ((size_t)c.y0 * nx + c.x0) * kFG;
   const R* pb = fg + ((size_t)c.y0 * nx + c.x1) * kFG;
   const R* pd = fg + ((size_t)c.y1 * nx + c.x0) * kFG;
@@ -246,6 +247,7 @@ __device__ __forceinline__ void deposit(R* tile, R* ovf, const DepFlags& fl, con
                                         int f, int nx, int ny, R v) {
   const R gx = R(1) - c.fx, gy = R(1) - c.fy;
   const R w00 = gx * gy * v, w01 = c.fx * gy * v, w10 = gx * c.fy * v, w11 = c.fx * c.fy * v;
+  if (!QSA_IN(c.x0 < nx && c.x1 < nx && c.y0 < ny && c.y1 < ny && f < kNF)) return;
   if (c.ty >= 0 && c.ty <= kTileRows - 2) {
     if (c.ty != 1) flag_rows(fl, c.ty);
     R* r0 = tile + ((size_t)f * kTileRows + c.ty) * nx;
@@ -342,6 +344,7 @@ template <typename R, int N>
 __device__ __forceinline__ void deposit_n(R* tile, R* ovf, const DepFlags& fl, const Cic<R>& c,
                                           const W4<R>& w, int f0, int nx, int ny,
                                           const R (&v)[N]) {
+  if (!QSA_IN(c.x0 < nx && c.x1 < nx && c.y0 < ny && c.y1 < ny && f0 + N <= kNF)) return;
   if (c.ty >= 0 && c.ty <= kTileRows - 2) {
     if (c.ty != 1) flag_rows(fl, c.ty);
 #pragma unroll
@@ -473,6 +476,7 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             ii[u] = base + (size_t)(ok[u] ? sub0 + u : sub0) * nx + ix;
+            if (!QSA_IN(ii[u] < (size_t)p.np)) ii[u] = 0;
             ox[u] = pox[ii[u]];
             oy[u] = poy[ii[u]];
             uxs[u] = pux[ii[u]];

@@ -15,6 +15,8 @@ from . import config
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libqsa.so")
+# the bounds-checked debug build (build.build(bounds=True)); QSA_LIBRARY selects another file
+BOUNDS_LIB_PATH = os.path.join(_HERE, "_lib", "libqsa_bounds.so")
 
 QSA_OK = 0
 QSA_ERR_ARG = -1
@@ -32,7 +34,7 @@ EXPORTS = ("qsa_init", "qsa_set_beam", "qsa_get_beam", "qsa_plasma_sweep", "qsa_
            "qsa_diagnostics", "qsa_copy_field", "qsa_copy_source", "qsa_field_solve",
            "qsa_phase_times", "qsa_launch_count", "qsa_device_bytes", "qsa_last_error",
            "qsa_destroy", "qsa_field_solve_static", "qsa_advance", "qsa_launch_times",
-           "qsa_eq5_march", "qsa_advance_batch")
+           "qsa_eq5_march", "qsa_advance_batch", "qsa_bounds_check")
 
 
 class QsaError(RuntimeError):
@@ -88,11 +90,15 @@ FREE_FN = ct.CFUNCTYPE(None, ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_void_p)
 _lib = None
 
 
-def load_library(path: str = LIB_PATH):
-    """Load libqsa.so (built by paper_2607_24214_b300.build) and declare its signatures."""
+def load_library(path: str = None):
+    """Load libqsa.so (built by paper_2607_24214_b300.build) and declare its signatures.
+    The environment variable QSA_LIBRARY, when set, names the file instead (for example the
+    bounds-checked debug build)."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = os.environ.get("QSA_LIBRARY") or LIB_PATH
     if not os.path.exists(path):
         raise ImportError(f"{path} is missing: build it with `python -m "
                           f"paper_2607_24214_b300.build` (nvcc, sm_103a)")
@@ -111,6 +117,8 @@ def load_library(path: str = LIB_PATH):
     lib.qsa_advance.restype = ct.c_int
     lib.qsa_advance_batch.argtypes = [ct.POINTER(P), ct.c_int32, ct.c_int32]
     lib.qsa_advance_batch.restype = ct.c_int
+    lib.qsa_bounds_check.argtypes = [ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int64)]
+    lib.qsa_bounds_check.restype = ct.c_int
     lib.qsa_launch_times.argtypes = [P, ct.POINTER(ct.c_float), ct.c_int,
                                      ct.POINTER(ct.c_int)]
     lib.qsa_launch_times.restype = ct.c_int
@@ -193,6 +201,17 @@ def eq5_march(gamma, psi0, dpsi0, dxi, tau_end, n_tau, n_out=1, stream=None):
     if rc != QSA_OK:
         raise QsaError(rc, lib.qsa_last_error(None).decode())
     return out
+
+
+def bounds_check():
+    """(enabled, first failing source line, failures) of the bounds-checked debug build's
+    index checks on the current device; enabled is False for the release build."""
+    lib = load_library()
+    first, count = ct.c_int64(), ct.c_int64()
+    rc = lib.qsa_bounds_check(ct.byref(first), ct.byref(count))
+    if rc < 0:
+        raise QsaError(rc, "bounds counters could not be read")
+    return rc == 1, first.value, count.value
 
 
 def advance_batch(instances, n_steps: int):

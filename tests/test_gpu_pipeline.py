@@ -35,6 +35,17 @@ def field_err(a, b):
     return np.array(out)
 
 
+def field_err_trans(a, b):
+    """Errors of (W_x, W_y, E_z, B_x, B_y, B_z) with the transverse components against the
+    transverse field magnitude (the largest of |W|, |B|) and E_z against its own scale: B_z
+    of a nearly cold, round beam is small, and FP32 summation-order noise of the deposits is
+    measured against the fields it perturbs, not against B_z alone (the same reading as the
+    full-size pair-beam test)."""
+    trans = max(np.abs(b[:, f]).max() for f in (0, 1, 3, 4, 5))
+    scales = [trans, trans, np.abs(b[:, 2]).max(), trans, trans, trans]
+    return np.array([np.abs(a[:, f] - b[:, f]).max() / scales[f] for f in range(6)])
+
+
 def make(Q, p, beams):
     q = Q(p)
     for si, b in enumerate(beams):
@@ -42,7 +53,7 @@ def make(Q, p, beams):
     return q
 
 
-def compare(Q, p, beams, n, depth, tol):
+def compare(Q, p, beams, n, depth, tol, err=field_err):
     """advance(n) at `depth` vs n sequential steps; then one more sweep on both."""
     a = make(Q, p.with_(pipeline_depth=1), beams)
     for _ in range(n):
@@ -53,7 +64,7 @@ def compare(Q, p, beams, n, depth, tol):
     da, db = a.diagnostics(), b.diagnostics()
     assert db["sweeps"] == n and da["beam_lost"] == db["beam_lost"]
     # the last sweep's slab (that of step n - 1) and its k = 0 mode
-    assert field_err(b.slab(), a.slab()).max() <= tol
+    assert err(b.slab(), a.slab()).max() <= tol
     for k in ("psi0", "ez0"):
         scale = max(np.abs(da[k]).max(), 1e-300)
         assert np.abs(db[k] - da[k]).max() <= tol * scale, k
@@ -71,7 +82,7 @@ def compare(Q, p, beams, n, depth, tol):
     # a single sweep after the pipelined launches reads the right sources
     a.sweep()
     b.sweep()
-    assert field_err(b.slab(), a.slab()).max() <= tol
+    assert err(b.slab(), a.slab()).max() <= tol
     return a, b
 
 
@@ -104,17 +115,20 @@ def test_pipelined_slow_beam_drift_and_loss(Q):
     assert b.diagnostics()["beam_lost"] > 1000
 
 
-def test_pipelined_particles_off_home(Q):
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_pipelined_particles_off_home(Q, prec):
     """Particles up to 2.5 cells ahead of or behind their home layer (a state qsa_set_beam
     accepts); a particle ahead of its home deposits into nodes that an earlier layer also
-    feeds, which the schedule covers with its margin."""
-    p = config.c1_fp64_electron_beam().with_(nxi=32, Lxi=4.0)
+    feeds, which the schedule covers with its margin.  The clipped ones sit just below the
+    window's end, where FP32 rounds them onto it: their xi cell must still be the last one,
+    or the schedule waits for a slab node that does not exist."""
+    p = config.c1_fp64_electron_beam().with_(nxi=32, Lxi=4.0, precision=prec)
     beams = inputs.all_beams(p)
     rng = np.random.default_rng(7)
     b0 = beams[0]
     b0["xi"] = np.clip(b0["xi"] + rng.uniform(-2.5, 2.5, b0["xi"].size) * p.dxi, 0.0,
                        p.Lxi * (1 - 1e-12))
-    compare(Q, p, beams, 5, 4, TOL["fp64"])
+    compare(Q, p, beams, 5, 4, TOL[prec], field_err if prec == "fp64" else field_err_trans)
 
 
 def test_pipelined_pair_beam_partial_window(Q):
