@@ -66,8 +66,8 @@ def sweep_bytes(p):
 # dram__bytes_write.sum (one pass) of `bench.py --no-fp64 --no-e2e --no-cpu --no-batch`
 # (profiles/pipe_kernel_c2_200steps_dram.md), in TB.  Later launches move more: the
 # filamented beam's particles deposit away from their homes.
-PIPE_DRAM_TB_PER_LAUNCH = [2.5183, 2.5182, 2.5183, 2.5183, 2.5179, 2.5196,
-                           2.5304, 2.5834, 2.6468, 2.7274, 2.8174, 2.9207]
+PIPE_DRAM_TB_PER_LAUNCH = [2.5330, 2.5329, 2.5329, 2.5329, 2.5326, 2.5341,
+                           2.5447, 2.5972, 2.6607, 2.7446, 2.8388, 2.9475]
 
 
 def pipe_traffic(p, depth, n_launches):
