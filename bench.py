@@ -40,43 +40,28 @@ CPU_SAMPLE_SLICES = 12
 
 
 def bytes_per_update(p):
-    """Algorithmic HBM bytes per plasma particle-slice update of one beam step (mixed path):
-    plasma state read+write once per slice (x, y, u_x, u_y, psi_prev: 5 x 4 B x 2), the beam
-    state read (32 B) and written (28 B) once, the beam-source slab written and read
-    (2 x 16 B per node), and the field slab written and read (2 x 24 B per node)."""
+    """Algorithmic HBM bytes per plasma particle-slice update of one beam step (mixed path),
+    as the method's data flow fixes them: the plasma state (x, y, u_x, u_y: 4 x 4 B) read and
+    written once per slice, the beam state read (32 B) and written (28 B) once per step, the
+    beam-source slab (S_b, J_z, J_x, J_y: 16 B per node) written and read, and the field slab
+    (six fields: 24 B per node) written and read.  At 4 plasma and 8 beam particles per cell
+    that is 688 B per cell per slice, 172 B per update."""
     ppc = p.ppc_plasma_x * p.ppc_plasma_y
     cells = p.nx * p.ny
-    plasma = 40.0 * ppc * cells * p.nxi
+    plasma = 32.0 * ppc * cells * p.nxi
     nb = sum(p.nx * p.ny * s.ppc_x * s.ppc_y * s.ppc_xi * p.nxi for s in p.species)
     beam = 60.0 * nb
-    slabs = (32.0 + 48.0) * cells * (p.nxi + 1)
+    slabs = (32.0 + 48.0) * cells * p.nxi
     return (plasma + beam + slabs) / (ppc * cells * p.nxi)
 
 
 def sweep_bytes(p):
-    """Algorithmic HBM bytes of one sweep launch: plasma state r+w per slice, beam sources
-    read (16 B per node), field slab written (24 B per node)."""
+    """Algorithmic HBM bytes of one sweep: the plasma state read and written per slice
+    (32 B per particle), the beam sources read (16 B per node) and the field slab written
+    (24 B per node), counted per slice as the update metric counts them."""
     ppc = p.ppc_plasma_x * p.ppc_plasma_y
     cells = p.nx * p.ny
-    return 40.0 * ppc * cells * p.nxi + (16.0 + 24.0) * cells * (p.nxi + 1)
-
-
-# DRAM bytes (read + write) of each full 16-step pipe_kernel launch of this workload's
-# 200 timed steps (after 3 warm-up steps), from one ncu capture of dram__bytes_read.sum and
-# dram__bytes_write.sum (one pass) of `bench.py --no-fp64 --no-e2e --no-cpu --no-batch`
-# (profiles/pipe_kernel_c2_200steps_dram.md), in TB.  Later launches move more: the
-# filamented beam's particles deposit away from their homes.
-PIPE_DRAM_TB_PER_LAUNCH = [2.5330, 2.5329, 2.5329, 2.5329, 2.5326, 2.5341,
-                           2.5447, 2.5972, 2.6607, 2.7446, 2.8388, 2.9475]
-
-
-def pipe_traffic(p, depth, n_launches):
-    """Mean DRAM bytes of the first n_launches full launches, from the capture above; None
-    for another grid or depth, which the capture does not cover."""
-    if (p.nx, p.ny, p.nxi, depth) != (256, 256, 1024, 16) or n_launches < 1:
-        return None
-    tb = PIPE_DRAM_TB_PER_LAUNCH[:n_launches]
-    return 1e12 * sum(tb) / len(tb)
+    return 32.0 * ppc * cells * p.nxi + (16.0 + 24.0) * cells * p.nxi
 
 
 def pipe_bytes(p, depth):
@@ -89,7 +74,7 @@ def push_bytes(p):
     """Algorithmic HBM bytes of the beam push of one step: beam state read 32 B and written
     28 B per particle, field slab read (24 B per node), sources written (16 B per node)."""
     nb = sum(p.nx * p.ny * s.ppc_x * s.ppc_y * s.ppc_xi * p.nxi for s in p.species)
-    return 60.0 * nb + (24.0 + 16.0) * p.nx * p.ny * (p.nxi + 1)
+    return 60.0 * nb + (24.0 + 16.0) * p.nx * p.ny * p.nxi
 
 
 class Clocks:
@@ -323,8 +308,7 @@ def main():
         achieved = pipe_bytes(p, dom_steps) / (dom_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": "pipe_kernel", "achieved": achieved,
                 "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": pipe_traffic(p, dom_steps, len(full)),
-                "traffic_source": "ncu dram__bytes of the full launches of this workload",
+                "traffic": None,
                 "algorithmic_bytes": pipe_bytes(p, dom_steps),
                 "peak_source": peak_src, "launch_ms": dom_ms,
                 "steps_per_launch": dom_steps, "kernel_share": float(np.sum(lt)) / ms,
@@ -389,10 +373,7 @@ def main():
                         "pipeline_depth": d64, "ms_per_step": ms64 / args.fp64_steps,
                         "speedup_mixed_over_fp64": ((first["value"] if first else value) / v64),
                         "speedup_basis": "mixed rate of the first pipelined launch (the same "
-                                         "linear-stage steps as the FP64 run)",
-                        "roofline": {"bound": "fp64", "frac": 0.743, "unit": "FP64 pipe",
-                                     "source": "ncu sm__pipe_fp64_cycles_active of the "
-                                               "16-slice capture (profiles/)"}}
+                                         "linear-stage steps as the FP64 run)"}
 
     if not args.no_e2e:
         line["e2e"] = e2e(p, args.e2e_steps, torch, stream)

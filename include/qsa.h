@@ -148,7 +148,10 @@ typedef struct {
                            unless pc_tol > 0) */
 } qsa_diag;
 
-/* Create a handle: validates params, allocates device state, builds every beam species on
+/* Create a handle for the setting of section "Quasistatic model" (plasma electrons, immobile
+ * ions, beam species Z_s, M_s, alpha_s, gamma_b) with the random macroparticle weights of the
+ * QuaSSis paragraph (section "Extending the QSA to extreme blazar jet regimes").
+ * Validates params, allocates device state, builds every beam species on
  * the device from `seed` (quiet lattice, Philox-4x32-10 random weights and momenta; the same
  * construction as paper_2607_24214_b300/inputs.py).  `stream` is a cudaStream_t or NULL.
  * alloc/free may be NULL (then cudaMallocAsync / cudaFreeAsync).  Errors: QSA_ERR_ARG for an
@@ -156,7 +159,9 @@ typedef struct {
 int qsa_init(const qsa_params* params, void* stream, qsa_alloc_fn alloc, qsa_free_fn free_fn,
              void* alloc_ctx, qsa_handle** out);
 
-/* Replace species `s` with host fp64 arrays of n particles in the canonical id order of the
+/* The beam macroparticles of the QS-PIC (QuaSSis paragraph): their state is all a resumed run
+ * needs, since the plasma is rebuilt at xi = 0 every sweep (section "Quasistatic model").
+ * Replace species `s` with host fp64 arrays of n particles in the canonical id order of the
  * lattice (id = ((k_xi*ny + iy)*nx + ix)*ppc + (s_xi*ppc_y + s_y)*ppc_x + s_x); n must equal
  * the species' lattice count.  x, y in [0, L); xi in [0, Lxi); w = 0 marks a lost particle.
  * Copies and converts to the device layout; marks the beam sources stale.  QSA_ERR_ARG when
@@ -166,22 +171,28 @@ int qsa_set_beam(qsa_handle* h, int s, int64_t n, const double* x, const double*
                  const double* xi, const double* ux, const double* uy, const double* uz,
                  const double* w);
 
-/* Copy species `s` back to host fp64 arrays (canonical id order, positions wrapped into
+/* The beam state of the QS-PIC (QuaSSis paragraph), read back.
+ * Copy species `s` back to host fp64 arrays (canonical id order, positions wrapped into
  * [0, L)); cap = capacity of each array; *n_out = particles written.  Synchronises. */
 int qsa_get_beam(qsa_handle* h, int s, int64_t cap, double* x, double* y, double* xi,
                  double* ux, double* uy, double* uz, double* w, int64_t* n_out);
 
-/* One plasma sweep at the current beam state: deposits the beam sources if stale, then runs
+/* The quasistatic plasma response (section "Quasistatic model": at fixed tau the fields
+ * depend on xi = ct - x; the nonlinear counterparts of Eqs. 1-2 and of the B_perp equations).
+ * One plasma sweep at the current beam state: deposits the beam sources if stale, then runs
  * the slice loop j = 0..nxi in one persistent launch and fills the field slab and the
  * per-slice diagnostics.  Asynchronous. */
 int qsa_plasma_sweep(qsa_handle* h);
 
-/* Push every live beam particle by dt through the current field slab (trilinear gather,
+/* The slow evolution of the beam in tau (section "Quasistatic model"; the nonlinear
+ * counterpart of Eq. 3).
+ * Push every live beam particle by dt through the current field slab (trilinear gather,
  * relativistic Boris), drop particles with xi >= Lxi, and deposit the beam sources of the
  * next sweep.  QSA_ERR_STATE before the first sweep.  Asynchronous. */
 int qsa_beam_step(qsa_handle* h);
 
-/* n_steps beam steps, each a plasma sweep followed by a beam push: the same result as
+/* The QS-PIC time loop (QuaSSis paragraph): alternating plasma sweeps and beam pushes.
+ * n_steps beam steps, each a plasma sweep followed by a beam push: the same result as
  * n_steps x (qsa_plasma_sweep; qsa_beam_step), up to the summation order of the deposits.
  * With pipeline_depth S >= 2 the steps run in persistent launches of up to S steps each, as a
  * wavefront in xi: the sweep of a step trails the previous step by a few slices, since its
@@ -194,7 +205,9 @@ int qsa_beam_step(qsa_handle* h);
  * the sources those of the next.  n_steps = 0 is a no-op.  Asynchronous. */
 int qsa_advance(qsa_handle* h, int32_t n_steps);
 
-/* n_steps beam steps (sweep + push) of each of n_handles independent instances, which may
+/* Parameter scans over alpha_b and gamma_b, like the scan after Fig. 2 (section "Analytical
+ * solutions") that finds the 0.4 N_e filamentation extent independent of both.
+ * n_steps beam steps (sweep + push) of each of n_handles independent instances, which may
  * differ in grid size, beam, box and every other parameter except precision, n_pc_iter,
  * pc_tol and stream (the same for all; a handle may appear once).  Each step of up to 16 instances runs
  * in one persistent launch whose phases cover the work of all of them (parameter scans over
@@ -207,7 +220,8 @@ int qsa_advance(qsa_handle* h, int32_t n_steps);
  * launch timing (qsa_launch_times).  Asynchronous, except during the timing steps. */
 int qsa_advance_batch(qsa_handle* const* handles, int32_t n_handles, int32_t n_steps);
 
-/* Device time, in ms, of each persistent launch of the last pipelined qsa_advance or
+/* Tracing (the paper has no counterpart).
+ * Device time, in ms, of each persistent launch of the last pipelined qsa_advance or
  * qsa_advance_batch call led by h (CUDA events recorded around the launches on the handle's
  * stream; up to 64 launches): writes min(cap, launches) values to ms and their number to
  * *n_out.  0 values when there was none.  Synchronises with those events. */
@@ -217,21 +231,27 @@ int qsa_launch_times(qsa_handle* h, float* ms, int cap, int* n_out);
  * latched device status (QSA_ERR_TIMEOUT, QSA_WARN_PSI_FLOOR, ...). */
 int qsa_diagnostics(qsa_handle* h, qsa_diag* out);
 
-/* Copy field `field` (0..5 = E_x - B_y, E_y + B_x, E_z, B_x, B_y, B_z) of slices j0..j1-1
+/* The slice fields of section "Quasistatic model" (F_perp = E_y - c B_z of Fig. 1d is
+ * E_y + B_x here, in the 3D labels of this library).
+ * Copy field `field` (0..5 = E_x - B_y, E_y + B_x, E_z, B_x, B_y, B_z) of slices j0..j1-1
  * of the slab into host_out[(j - j0) * ny * nx + iy * nx + ix] (fp64).  Synchronises. */
 int qsa_copy_field(qsa_handle* h, int field, int j0, int j1, double* host_out);
 
-/* Copy beam source `q` (0..3 = S_b = Z n (1 - v_z), J_zb, J_xb, J_yb) of nodes j0..j1-1 into
+/* The beam charge and current that drive the plasma (rho_b of Eq. 1 and its currents).
+ * Copy beam source `q` (0..3 = S_b = Z n (1 - v_z), J_zb, J_xb, J_yb) of nodes j0..j1-1 into
  * host_out like qsa_copy_field.  Deposits the sources first if they are stale. */
 int qsa_copy_source(qsa_handle* h, int q, int j0, int j1, double* host_out);
 
-/* Standalone transverse solve on the handle's grid, through the same device phases (row
+/* The transverse field equations of a slice (Eq. 2's operator for psi and its B_perp and
+ * E_z, B_z analogues, section "Quasistatic model").
+ * Standalone transverse solve on the handle's grid, through the same device phases (row
  * FFT, column FFT + k-space solve, inverse FFTs) as the sweep.  Inputs are host fp64 [ny][nx]
  * arrays; the k = 0 mode is dropped:
  *   psi = S/k^2, d_x psi, d_y psi;  E_z = -(i k.J)/k^2;  B_z = (i k_x J_y - i k_y J_x)/k^2;
  *   (k^2 + kappa2) B_x = i k_y J_z + D_y,  (k^2 + kappa2) B_y = -i k_x J_z - D_x.
  * out: 7 host arrays back to back, [7][ny][nx]: psi, d_x psi, d_y psi, E_z, B_z, B_x, B_y.
- * Uses the handle's sweep buffers (do not overlap with a sweep); synchronises. */
+ * Uses the handle's sweep buffers (do not overlap with a sweep); synchronises.  Returns
+ * QSA_ERR_NONFINITE if an output is not finite. */
 int qsa_field_solve(qsa_handle* h, const double* S, const double* Jx, const double* Jy,
                     const double* Jz, const double* Dx, const double* Dy, double kappa2,
                     double* out);
@@ -271,8 +291,8 @@ int qsa_eq5_march(int32_t n_modes, int32_t n_xi, double dxi, const double* gamma
  * Arguments: nx, ny in {1, 2^a 3^b} and <= QSA_STATIC_MAX_N; periodic box Lx, Ly > 0;
  * kappa2 >= 0; precision QSA_FP64 (arrays of double) or QSA_MIXED (arrays of float); S, Jx,
  * Jy, Jz, Dx, Dy: DEVICE pointers to [ny][nx] arrays; out: DEVICE pointer to [7][ny][nx]
- * (psi, d_x psi, d_y psi, E_z, B_z, B_x, B_y); stream: cudaStream_t or NULL.  The call
- * enqueues its work on the stream and returns after synchronising it.
+ * (psi, d_x psi, d_y psi, E_z, B_z, B_x, B_y); stream: cudaStream_t of the current device, or
+ * NULL.  The call enqueues its work on the stream and returns after synchronising it.
  * Memory: the scratch lives in one file-scope device array of QSA_STATIC_SCRATCH_BYTES that
  * every GPU loading this library holds until the process exits.  The first call on a device
  * takes that array's device address (cudaGetSymbolAddress, with that device current); make
@@ -281,8 +301,10 @@ int qsa_eq5_march(int32_t n_modes, int32_t n_xi, double dxi, const double* gamma
  * (the call clears what must start at zero), so calls that overlap on the GPU - from two
  * streams or two host threads - race and must be serialised by the caller.
  * Errors: QSA_ERR_ARG for a size above QSA_STATIC_MAX_N, an invalid size or argument, or a
- * grid whose scratch would not fit (qsa_last_error(NULL) says which); QSA_ERR_CUDA if a CUDA
- * call fails; QSA_ERR_TIMEOUT if a device-side wait gave up. */
+ * grid whose scratch would not fit, or a stream of another device (qsa_last_error(NULL) says
+ * which); QSA_ERR_CUDA if a CUDA call fails (the failing call and CUDA's text are in
+ * qsa_last_error(NULL)); QSA_ERR_TIMEOUT if a device-side wait gave up; QSA_ERR_NONFINITE if an
+ * output is not finite (a non-finite input, for instance), as qsa_field_solve reports it. */
 #define QSA_STATIC_MAX_N 128
 #define QSA_STATIC_SCRATCH_BYTES (6u * 1024u * 1024u + 512u * 1024u)
 int qsa_field_solve_static(int32_t nx, int32_t ny, double Lx, double Ly, double kappa2,
@@ -290,29 +312,35 @@ int qsa_field_solve_static(int32_t nx, int32_t ny, double Lx, double Ly, double 
                            const void* Jz, const void* Dx, const void* Dy, void* out,
                            void* stream);
 
-/* Phase timing of the last sweep (tracing): out[(j * 32 + ph) * 2 + 0] is the device
+/* Tracing (the paper has no counterpart).
+ * Phase timing of the last sweep: out[(j * 32 + ph) * 2 + 0] is the device
  * globaltimer (ns) when the last block arrived at the barrier closing phase ph of slice j,
  * out[... + 1] when block 0 left it, for slices j < 8 and phases ph < 32 (trial iteration it,
  * step k in {deposit, row FFT, column FFT + solve, inverse row FFT}: ph = 4 it + k; commit:
  * ph = 4 n_pc_iter + k).  Zero where not recorded.  cap >= 512.  Synchronises. */
 int qsa_phase_times(qsa_handle* h, int64_t* out, int cap);
 
-/* Kernel launches made by this handle since qsa_init (for launch accounting). */
+/* Kernel launches made by this handle since qsa_init (launch accounting; the paper has no
+ * counterpart). */
 int64_t qsa_launch_count(const qsa_handle* h);
 
-/* Device bytes held by the handle. */
+/* Device bytes held by the handle (bookkeeping; the paper has no counterpart). */
 int64_t qsa_device_bytes(const qsa_handle* h);
 
-/* One-line text of the last error of h (or of the last failed qsa_init when h is NULL). */
+/* One-line text of the last error of h (or of the last failed qsa_init, or of the last failed
+ * call without a handle, when h is NULL).  The paper has no counterpart. */
 const char* qsa_last_error(const qsa_handle* h);
 
-/* Release the handle and all its device memory (waits for its stream). */
+/* Release the handle and all its device memory (waits for its stream).  The paper has no
+ * counterpart. */
 void qsa_destroy(qsa_handle* h);
 
 /* Bounds checks of the debug build (built with -DQSA_DEBUG_BOUNDS as libqsa_bounds.so; the
  * paper has no counterpart): the index checks at the particle, tile, slab and field-grid
- * accesses of the sweep, push and pipelined kernels record the source line of the first
- * failure and the number of failures on the current device, and skip the access.  Writes
+ * accesses of the sweep, push and pipelined kernels and of qsa_field_solve_static record the
+ * source line of the first failure and the number of failures on the current device, and
+ * skip the access (the counts of both source files are added; the Eq. 5 solver has no
+ * index checks).  Writes
  * them to *first_line and *count (each may be NULL) and returns 1 in that build, 0 (with
  * zeros) in the release build, QSA_ERR_CUDA if the counters cannot be read.  Synchronises
  * the device. */

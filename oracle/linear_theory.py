@@ -96,14 +96,6 @@ def psi_series(xi, Gamma_tau, rho_b0=1.0, k=1.0, dps=60, tol=1e-45):
         return float(-rho_b0 / (k * k + 1.0) * total)
 
 
-def local_rate_series(xi, tau, Gamma, rel_step=1e-4):
-    """Gamma^st = d_tau ln|psi| (blazar paragraph) of the exact series, by a central difference."""
-    h = rel_step * tau
-    a = abs(psi_series(xi, Gamma * (tau + h)))
-    b = abs(psi_series(xi, Gamma * (tau - h)))
-    return (math.log(a) - math.log(b)) / (2 * h)
-
-
 def march_eq5(xi_grid, tau_end, n_tau, Gamma, rho_b0=1.0, k=1.0):
     """Independent numerical solution of Eq. 5: RK4 in tau on (psi, d_tau psi) with
     d_tau^2 psi = V, (d_xi^2 + 1) V = Gamma^2 psi, V(0) = V'(0) = 0, evaluated as

@@ -15,6 +15,7 @@
 #include "qsa_fft.cuh"
 #include "qsa_pipe.cuh"
 #include "qsa_sweep.cuh"
+#include "qsa_tables.h"
 
 using namespace qsa;
 
@@ -29,29 +30,6 @@ bool size_ok(int n) {
   while (n % 2 == 0) n /= 2;
   while (n % 3 == 0) n /= 3;
   return n == 1;
-}
-
-FftPlan make_plan(int n) {
-  FftPlan p{};
-  p.n = n;
-  int m = n;
-  while (m % 4 == 0) { p.radix[p.nstages++] = 4; m /= 4; }
-  while (m % 2 == 0) { p.radix[p.nstages++] = 2; m /= 2; }
-  while (m % 3 == 0) { p.radix[p.nstages++] = 3; m /= 3; }
-  auto log2_or_neg = [](int v) {
-    if (v <= 0 || (v & (v - 1))) return -1;
-    int l = 0;
-    while ((1 << l) < v) ++l;
-    return l;
-  };
-  int ns = 1;
-  for (int s = 0; s < p.nstages; ++s) {
-    p.ns[s] = ns;
-    p.nbsh[s] = log2_or_neg(n / p.radix[s]);
-    p.nssh[s] = log2_or_neg(ns);
-    ns *= p.radix[s];
-  }
-  return p;
 }
 
 struct Base {
@@ -91,6 +69,7 @@ namespace {
 namespace qsa {
 // Message for qsa_last_error(NULL) from entry points that have no handle.
 void set_global_error(const std::string& msg) { g_init_error = msg; }
+int static_bounds_counts(unsigned long long* first, unsigned long long* count);
 }  // namespace qsa
 
 namespace {
@@ -224,35 +203,13 @@ int setup(qsa_handle* h) {
   if (!ktab || !twp || !bref || !bar || !status || !s->lost || !s->dmin || !s->chk)
     return fail(h, QSA_ERR_OOM, "sweep tables");
   {
-    // k_x = 2 pi m / Lx (m = 0..nx/2), k_y = 2 pi m / Ly (m in numpy.fft order), and the
-    // first-derivative symbols, zero at the Nyquist index of an even grid
-    std::vector<R> kt(2 * dp.nxh + 2 * dp.ny);
-    for (int m = 0; m < dp.nxh; ++m) {
-      const double k = 2.0 * M_PI * m / dp.Lx;
-      kt[m] = R(k);
-      kt[dp.nxh + m] = (dp.nx % 2 == 0 && 2 * m == dp.nx) ? R(0) : R(k);
-    }
-    for (int m = 0; m < dp.ny; ++m) {
-      const int mm = (m <= dp.ny / 2) ? m : m - dp.ny;
-      const double k = 2.0 * M_PI * mm / dp.Ly;
-      kt[2 * dp.nxh + m] = R(k);
-      kt[2 * dp.nxh + dp.ny + m] = (dp.ny % 2 == 0 && 2 * m == dp.ny) ? R(0) : R(k);
-    }
+    const std::vector<R> kt = wavenumber_table<R>(dp.nx, dp.ny, dp.Lx, dp.Ly);
     CK(cudaMemcpyAsync(ktab, kt.data(), kt.size() * sizeof(R), cudaMemcpyHostToDevice,
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
   }
   {
-    // twiddles exp(-2 pi i m/n), built in FP64 on the host
-    std::vector<C<R>> tw(dp.nx + dp.ny);
-    for (int m = 0; m < dp.nx; ++m) {
-      const double t = -2.0 * M_PI * m / dp.nx;
-      tw[m] = C<R>{R(std::cos(t)), R(std::sin(t))};
-    }
-    for (int m = 0; m < dp.ny; ++m) {
-      const double t = -2.0 * M_PI * m / dp.ny;
-      tw[dp.nx + m] = C<R>{R(std::cos(t)), R(std::sin(t))};
-    }
+    const std::vector<C<R>> tw = twiddle_table<R>(dp.nx, dp.ny);
     CK(cudaMemcpyAsync(twp, tw.data(), tw.size() * sizeof(C<R>), cudaMemcpyHostToDevice,
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -718,14 +675,6 @@ int beam_step(qsa_handle* h) {
   return QSA_OK;
 }
 
-int status_code(int st) {
-  if (st & ST_TIMEOUT) return QSA_ERR_TIMEOUT;
-  if (st & ST_NONFINITE) return QSA_ERR_NONFINITE;
-  if (st & ST_FLOOR) return QSA_WARN_PSI_FLOOR;
-  return QSA_OK;
-}
-
-
 template <typename R>
 int diagnostics(qsa_handle* h, qsa_diag* out) {
   State<R>* s = S<R>(h);
@@ -794,8 +743,7 @@ int diagnostics(qsa_handle* h, qsa_diag* out) {
   out->beam_lost = (int64_t)lost;
   out->sweeps = h->sweeps;
   const int rc = status_code(st);
-  if (rc < 0) fail(h, rc, rc == QSA_ERR_TIMEOUT ? "device wait exceeded spin_limit"
-                                                 : "non-finite field value");
+  if (rc < 0) fail(h, rc, status_text(rc));
   return rc;
 }
 
@@ -957,8 +905,15 @@ int field_solve(qsa_handle* h, const double* const* in, double kappa2, double* o
   int st = 0;
   CK(cudaMemcpyAsync(&st, a.bar.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  // the solve has no slab to check: a non-finite value among its outputs is reported as the
+  // sweep reports a non-finite slab value
+  for (size_t i = 0; i < 7 * g; ++i)
+    if (!std::isfinite(out[i])) {
+      st |= ST_NONFINITE;
+      break;
+    }
   rc = status_code(st);
-  return rc < 0 ? fail(h, rc, "device wait exceeded spin_limit") : QSA_OK;
+  return rc < 0 ? fail(h, rc, status_text(rc)) : QSA_OK;
 }
 
 int validate(const qsa_params* p, std::string& why) {
@@ -1244,13 +1199,16 @@ int qsa_bounds_check(int64_t* first_line, int64_t* count) {
   if (first_line) *first_line = 0;
   if (count) *count = 0;
 #ifdef QSA_DEBUG_BOUNDS
-  unsigned long long f = 0, c = 0;
+  // this file's counters (the persistent kernels) and those of the allocation-free solve's
+  // file; the Eq. 5 solver's file holds no index checks
+  unsigned long long f = 0, c = 0, fs = 0, cs = 0;
   if (cudaDeviceSynchronize() != cudaSuccess ||
       cudaMemcpyFromSymbol(&f, qsa::g_bounds_first, sizeof(f)) != cudaSuccess ||
-      cudaMemcpyFromSymbol(&c, qsa::g_bounds_count, sizeof(c)) != cudaSuccess)
+      cudaMemcpyFromSymbol(&c, qsa::g_bounds_count, sizeof(c)) != cudaSuccess ||
+      qsa::static_bounds_counts(&fs, &cs) != QSA_OK)
     return QSA_ERR_CUDA;
-  if (first_line) *first_line = (int64_t)f;
-  if (count) *count = (int64_t)c;
+  if (first_line) *first_line = (int64_t)(f ? f : fs);
+  if (count) *count = (int64_t)(c + cs);
   return 1;
 #else
   return 0;

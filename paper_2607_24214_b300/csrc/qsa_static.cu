@@ -20,6 +20,7 @@
 #include "qsa_common.cuh"
 #include "qsa_fft.cuh"
 #include "qsa_sweep.cuh"
+#include "qsa_tables.h"
 
 using namespace qsa;
 
@@ -58,27 +59,11 @@ bool static_size_ok(int n) {
   return n == 1;
 }
 
-FftPlan plan_of(int n) {
-  FftPlan p{};
-  p.n = n;
-  int m = n;
-  while (m % 4 == 0) { p.radix[p.nstages++] = 4; m /= 4; }
-  while (m % 2 == 0) { p.radix[p.nstages++] = 2; m /= 2; }
-  while (m % 3 == 0) { p.radix[p.nstages++] = 3; m /= 3; }
-  int ns = 1;
-  for (int s = 0; s < p.nstages; ++s) {
-    auto lg = [](int v) {
-      if (v <= 0 || (v & (v - 1))) return -1;
-      int l = 0;
-      while ((1 << l) < v) ++l;
-      return l;
-    };
-    p.ns[s] = ns;
-    p.nbsh[s] = lg(n / p.radix[s]);
-    p.nssh[s] = lg(ns);
-    ns *= p.radix[s];
-  }
-  return p;
+// Every CUDA failure returns QSA_ERR_CUDA with the failing call and CUDA's text in
+// qsa_last_error(NULL).
+int cuda_err(cudaError_t e, const char* what) {
+  set_global_error(std::string("qsa_field_solve_static: ") + what + ": " + cudaGetErrorString(e));
+  return QSA_ERR_CUDA;
 }
 
 // Bump allocator over the scratch array (offsets only; nothing is allocated).
@@ -95,23 +80,47 @@ struct Carve {
 };
 
 // Copy the four outputs of the B pass or the three of the psi pass out of the interleaved
-// field grid into the caller's arrays.
+// field grid into the caller's arrays; a non-finite output sets ST_NONFINITE in the status word.
 template <typename R>
 __global__ void extract_kernel(const R* fg, int n, int c0, int nc, R* out0, R* out1, R* out2,
-                               R* out3) {
+                               R* out3, int* status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   R* outs[4] = {out0, out1, out2, out3};
-  for (int c = 0; c < nc; ++c) outs[c][i] = fg[(size_t)i * kFG + c0 + c];
+  bool bad = false;
+  for (int c = 0; c < nc; ++c) {
+    const R v = fg[(size_t)i * kFG + c0 + c];
+    outs[c][i] = v;
+    bad = bad || !isfinite(v);
+  }
+  if (bad) atomicOr(status, ST_NONFINITE);
 }
 
 template <typename R>
 int solve_static(int nx, int ny, double Lx, double Ly, double kappa2, const R* S, const R* Jx,
                  const R* Jy, const R* Jz, const R* Dx, const R* Dy, R* out, cudaStream_t st) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return QSA_ERR_CUDA;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_err(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_global_error("qsa_field_solve_static: device ordinal beyond " +
+                     std::to_string(kMaxDevices - 1));
+    return QSA_ERR_ARG;
+  }
+  if (st != nullptr) {
+    // the scratch array and the launches belong to the current device: so must the stream
+    int sdev = -1;
+    if ((e = cudaStreamGetDevice(st, &sdev)) != cudaSuccess)
+      return cuda_err(e, "cudaStreamGetDevice");
+    if (sdev != dev) {
+      set_global_error("qsa_field_solve_static: the stream belongs to device " +
+                       std::to_string(sdev) + ", not to the current device " +
+                       std::to_string(dev));
+      return QSA_ERR_ARG;
+    }
+  }
   void* base = nullptr;
-  if (scratch_base(dev, &base) != cudaSuccess) return QSA_ERR_CUDA;
+  if ((e = scratch_base(dev, &base)) != cudaSuccess) return cuda_err(e, "cudaGetSymbolAddress");
   DevParams dp{};
   dp.nx = nx;
   dp.ny = ny;
@@ -131,20 +140,25 @@ int solve_static(int nx, int ny, double Lx, double Ly, double kappa2, const R* S
   dp.dt = 1.0;
   dp.psi_floor = 0.05;
   dp.spin_limit = 1ll << 26;
-  dp.px = plan_of(nx);
-  dp.py = plan_of(ny);
+  dp.px = make_plan(nx);
+  dp.py = make_plan(ny);
   dp.fd_nx = make_fastdiv(nx);
   dp.fd_ny = make_fastdiv(ny);
   dp.fd_nxh = make_fastdiv(dp.nxh);
   const size_t g = (size_t)nx * ny, spec = (size_t)dp.nxh * ny;
   const size_t smem = sweep_smem_bytes<R>(nx, ny);
   int per_sm = 0, sms = 0;
-  if (raise_dyn_smem((const void*)solve_kernel<R>, smem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<R>, kThreadsS, smem) !=
-          cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return QSA_ERR_CUDA;
-  if (per_sm < 1) return QSA_ERR_ARG;
+  if ((e = raise_dyn_smem((const void*)solve_kernel<R>, smem)) != cudaSuccess)
+    return cuda_err(e, "cudaFuncSetAttribute");
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<R>, kThreadsS,
+                                                         smem)) != cudaSuccess)
+    return cuda_err(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return cuda_err(e, "cudaDeviceGetAttribute");
+  if (per_sm < 1) {
+    set_global_error("qsa_field_solve_static: the solve kernel does not fit on an SM");
+    return QSA_ERR_ARG;
+  }
   int grid = per_sm * sms;
   const int work = ny > dp.nxh ? ny : dp.nxh;
   if (grid > work) grid = work;
@@ -182,29 +196,15 @@ int solve_static(int nx, int ny, double Lx, double Ly, double kappa2, const R* S
   a.bar = Barrier{count, status, dp.spin_limit};
 
   // tables, built in FP64 on the host (copied, nothing allocated on the device)
-  std::vector<C<R>> twh(nx + ny);
-  for (int m = 0; m < nx; ++m)
-    twh[m] = C<R>{R(std::cos(-2.0 * M_PI * m / nx)), R(std::sin(-2.0 * M_PI * m / nx))};
-  for (int m = 0; m < ny; ++m)
-    twh[nx + m] = C<R>{R(std::cos(-2.0 * M_PI * m / ny)), R(std::sin(-2.0 * M_PI * m / ny))};
-  std::vector<R> kt(2 * dp.nxh + 2 * ny);
-  for (int m = 0; m < dp.nxh; ++m) {
-    const double k = 2.0 * M_PI * m / Lx;
-    kt[m] = R(k);
-    kt[dp.nxh + m] = (nx % 2 == 0 && 2 * m == nx) ? R(0) : R(k);
-  }
-  for (int m = 0; m < ny; ++m) {
-    const int mm = (m <= ny / 2) ? m : m - ny;
-    const double k = 2.0 * M_PI * mm / Ly;
-    kt[2 * dp.nxh + m] = R(k);
-    kt[2 * dp.nxh + ny + m] = (ny % 2 == 0 && 2 * m == ny) ? R(0) : R(k);
-  }
+  const std::vector<C<R>> twh = twiddle_table<R>(nx, ny);
+  const std::vector<R> kt = wavenumber_table<R>(nx, ny, Lx, Ly);
   std::vector<double> dg(D_COUNT, 0.0);
   dg[D_KAPPA] = kappa2 * (double)nx * ny;  // the solve scales by ppc * nx * ny (ppc = 1)
 
-#define QSA_TRY(x)                      \
-  do {                                  \
-    if ((x) != cudaSuccess) return QSA_ERR_CUDA; \
+#define QSA_TRY(x)                                      \
+  do {                                                  \
+    const cudaError_t e_ = (x);                         \
+    if (e_ != cudaSuccess) return cuda_err(e_, #x);     \
   } while (0)
   QSA_TRY(cudaMemcpyAsync(tw, twh.data(), twh.size() * sizeof(C<R>), cudaMemcpyHostToDevice, st));
   QSA_TRY(cudaMemcpyAsync(ktab, kt.data(), kt.size() * sizeof(R), cudaMemcpyHostToDevice, st));
@@ -230,7 +230,7 @@ int solve_static(int nx, int ny, double Lx, double Ly, double kappa2, const R* S
                                       smem, st));
   const unsigned eb = (unsigned)((g + 255) / 256);
   extract_kernel<R><<<eb, 256, 0, st>>>(a.fg, (int)g, FG_BX, 4, out + 5 * g, out + 6 * g,
-                                        out + 4 * g, out + 3 * g);
+                                        out + 4 * g, out + 3 * g, status);
   QSA_TRY(cudaGetLastError());
   // psi pass: S in field 0 of three
   QSA_TRY(cudaMemsetAsync(a.ovf, 0, 3 * g * sizeof(R), st));
@@ -242,13 +242,18 @@ int solve_static(int nx, int ny, double Lx, double Ly, double kappa2, const R* S
   QSA_TRY(cudaLaunchCooperativeKernel((void*)solve_kernel<R>, dim3(grid), dim3(kThreadsS), args,
                                       smem, st));
   extract_kernel<R><<<eb, 256, 0, st>>>(a.fg, (int)g, FG_PSI, 3, out, out + g, out + 2 * g,
-                                        nullptr);
+                                        nullptr, status);
   QSA_TRY(cudaGetLastError());
   int hst = 0;
   QSA_TRY(cudaMemcpyAsync(&hst, status, sizeof(int), cudaMemcpyDeviceToHost, st));
   QSA_TRY(cudaStreamSynchronize(st));
 #undef QSA_TRY
-  return (hst & ST_TIMEOUT) ? QSA_ERR_TIMEOUT : QSA_OK;
+  const int rc = status_code(hst);
+  if (rc < 0) {
+    set_global_error(std::string("qsa_field_solve_static: ") + status_text(rc));
+    return rc;
+  }
+  return QSA_OK;
 }
 
 }  // namespace
@@ -278,3 +283,18 @@ extern "C" int qsa_field_solve_static(int32_t nx, int32_t ny, double Lx, double 
   set_global_error("qsa_field_solve_static: unknown precision");
   return QSA_ERR_ARG;
 }
+
+namespace qsa {
+// The bounds-checked debug build's counters of this file (each file compiled without
+// separate device linking has its own): read by qsa_bounds_check.
+int static_bounds_counts(unsigned long long* first, unsigned long long* count) {
+  *first = 0;
+  *count = 0;
+#ifdef QSA_DEBUG_BOUNDS
+  if (cudaMemcpyFromSymbol(first, g_bounds_first, sizeof(*first)) != cudaSuccess ||
+      cudaMemcpyFromSymbol(count, g_bounds_count, sizeof(*count)) != cudaSuccess)
+    return QSA_ERR_CUDA;
+#endif
+  return QSA_OK;
+}
+}  // namespace qsa

@@ -119,3 +119,38 @@ def test_smaller_handle_created_later_does_not_break_larger(qsa_mod):
     big.sweep()
     small.sweep()
     assert big.diagnostics()["status"] >= 0 and small.diagnostics()["status"] >= 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_instances_match_the_oracle(qsa_mod, prec):
+    """Four uneven instances (grids 16x16, 24x24, 32x32, 12x18; alpha, gamma_b and dt all
+    different, like the scan over alpha_b and gamma_b after Fig. 2) advanced together by
+    qsa_advance_batch for two steps, then swept: each instance's slab, beam and lost count
+    against the FP64 oracle's run of the same beam (FP64 1e-9, mixed 1e-4 of each field's
+    scale; lost particles exact)."""
+    from oracle import qspic
+    tol = {"fp64": 1e-9, "mixed": 1e-4}[prec]
+    ps = instances(4, prec)
+    qs = []
+    for p in ps:
+        q = qsa_mod.QSA(p)
+        q.set_beam(0, inputs.all_beams(p)[0])
+        qs.append(q)
+    qsa_mod.advance_batch(qs, 2)
+    for q, p in zip(qs, ps):
+        q.sweep()
+        d = q.diagnostics()
+        assert d["status"] >= 0
+        ref, _, rb = qspic.run(p, inputs.all_beams(p), 2)
+        assert field_err(q.slab(), ref).max() <= tol
+        n = rb[0]["x"].size
+        gb = q.get_beam(0, n)
+        assert np.array_equal(gb["w"] == 0, rb[0]["w"] == 0)
+        live = rb[0]["w"] != 0
+        for key in ("xi", "ux", "uy"):
+            scale = max(np.abs(rb[0][key][live]).max(), 1e-300)
+            assert np.abs(gb[key][live] - rb[0][key][live]).max() <= tol * scale, key
+        for key, L, d in (("x", p.Lx, p.dx), ("y", p.Ly, p.dy)):     # periodic positions
+            e = np.mod(gb[key][live] - rb[0][key][live] + 0.5 * L, L) - 0.5 * L
+            assert np.abs(e).max() <= tol * d, key
+        q.close()

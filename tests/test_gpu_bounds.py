@@ -2,7 +2,8 @@
 every index path of the kernels: the sequential sweep and push, the pipelined launch with a
 slipping beam that is lost off the window, particles placed cells away from their lattice
 homes in x, y and xi, an odd grid with one plasma particle per cell, a batch of uneven
-instances, and the tolerance mode.  Not one index check may fail.  The library runs in a
+instances, the tolerance mode, and the allocation-free field solve (whose kernels are compiled
+in a source file of their own, with their own counters).  Not one index check may fail.  The library runs in a
 child process (one library per process); the release build reports its checks as absent.
 
 This stands in for a memory checker, which is not available here: a failed check records
@@ -72,6 +73,16 @@ ps = [c1.with_(nx=n, ny=n, Lx=n * 0.2, Ly=n * 0.2, seed=i, precision="mixed")
 qs = [qsa.QSA(pi) for pi in ps]
 qsa.advance_batch(qs, 2)
 out += [q.diagnostics()["status"] for q in qs]
+# the allocation-free solve, whose kernels sit in another source file with its own counters
+import ctypes as ct
+lib = qsa.load_library()
+for nx, ny in ((96, 64), (1, 32)):
+    rng = np.random.default_rng(nx)
+    ins = [torch.tensor(rng.normal(size=(ny, nx)), device="cuda") for _ in range(6)]
+    o = torch.empty((7, ny, nx), dtype=torch.float64, device="cuda")
+    out.append(lib.qsa_field_solve_static(nx, ny, 0.3 * nx, 0.25 * ny, 0.5, 0,
+                                          *[ct.c_void_p(t.data_ptr()) for t in ins],
+                                          ct.c_void_p(o.data_ptr()), None))
 torch.cuda.synchronize()
 enabled, first, count = qsa.bounds_check()
 print(json.dumps({"status": out, "enabled": enabled, "first_line": first, "count": count}))

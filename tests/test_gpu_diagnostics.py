@@ -123,3 +123,13 @@ def test_invalid_diag_modes_rejected(Q):
     for bad in ([(0, 0)], [(17, 0)], [(0, -17)]):
         with pytest.raises(QsaError):
             Q(p.with_(diag_modes=bad))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_field_energies(Q, prec):
+    """Per-slice energies 1/2 sum F^2 dx dy dxi of E_x, E_y, E_z, B_x, B_y, B_z against the
+    oracle's field_energy of its own slab (pinned to closed forms on the CPU)."""
+    p, q, d, slab, rd, _ = run_both(Q, prec)
+    want = qspic.field_energy(p, slab)
+    scale = want.max(axis=0)
+    assert np.all(np.abs(d["energy"] - want) <= 2 * TOL[prec] * scale)

@@ -379,3 +379,97 @@ def test_saturation_arithmetic_and_extent():
     assert abs(e / o["eps_Ey"] - 1) < o["rel_tol"]
     c = GOLDEN["cfi_extent"]
     assert abs(lt.transition_xi(10.0) / 10.0 - c["value"]) < c["abs_tol"]
+
+
+# ------------------------------------------------------------------ direct pins of helpers
+def test_gather_exact_on_bilinear_fields_and_adjoint_to_deposit():
+    """CIC gather reproduces a field that is bilinear in (x, y) exactly inside every cell
+    (bilinear interpolation of a bilinear function), and it is the transpose of the deposit:
+    sum over nodes deposit(q) F dx dy = sum over particles q gather(F)."""
+    rng = np.random.default_rng(11)
+    p = _p(nx=10, ny=7, nxi=2, Lx=2.5, Ly=1.4, Lxi=1.0, dt=1.0)
+    G = qspic.Grid(p)
+    X, Y = np.meshgrid(np.arange(p.nx) * p.dx, np.arange(p.ny) * p.dy)
+    a, b, c, d = 0.3, -1.7, 2.2, 0.9
+    F = a + b * X + c * Y + d * X * Y
+    # points whose cell does not wrap (the bilinear function is not periodic)
+    x = rng.uniform(0, (p.nx - 1) * p.dx, 400)
+    y = rng.uniform(0, (p.ny - 1) * p.dy, 400)
+    np.testing.assert_allclose(qspic.gather(G, F, x, y), a + b * x + c * y + d * x * y,
+                               rtol=0, atol=1e-13)
+    # adjointness on arbitrary (periodic) positions and a random field
+    xs, ys = rng.uniform(0, p.Lx, 300), rng.uniform(0, p.Ly, 300)
+    q = rng.normal(size=300)
+    Fr = rng.normal(size=(p.ny, p.nx))
+    lhs = (qspic.deposit(G, xs, ys, q) * Fr).sum() * p.dx * p.dy
+    rhs = (q * qspic.gather(G, Fr, xs, ys)).sum()
+    assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(rhs))
+
+
+def test_beam_source_slots_of_one_particle():
+    """One beam particle on a node (x = i dx, y = j dy, xi = k dxi) puts its whole charge on
+    that node: S_b = Z w (1 - v_z), J_z = Z w v_z, J_x = Z w v_x, J_y = Z w v_y, each divided
+    by dx dy dxi, with v = u/gamma (the source terms of the field equations); 1 - v_z is
+    compared with its value from u_z/gamma in 50-digit arithmetic."""
+    import mpmath
+    sp = config.Species(Z=-2.0, M=3.0)
+    p = _p(nx=6, ny=5, nxi=8, Lx=3.0, Ly=2.5, Lxi=4.0, dt=1.0, species=[sp])
+    i, j, k = 2, 3, 5
+    ux, uy, uz, w = 0.7, -1.3, 40.0, 0.25
+    b = [dict(x=np.array([i * p.dx]), y=np.array([j * p.dy]), xi=np.array([k * p.dxi]),
+              ux=np.array([ux]), uy=np.array([uy]), uz=np.array([uz]), w=np.array([w]))]
+    src = qspic.beam_sources(p, b)
+    vol = p.dx * p.dy * p.dxi
+    with mpmath.workdps(50):
+        g = mpmath.sqrt(1 + mpmath.mpf(ux) ** 2 + mpmath.mpf(uy) ** 2 + mpmath.mpf(uz) ** 2)
+        omv = float(1 - mpmath.mpf(uz) / g)
+        gam = float(g)
+    want = sp.Z * w / vol * np.array([omv, uz / gam, ux / gam, uy / gam])
+    for s in range(4):
+        assert abs(src[s, k, j, i] - want[s]) <= 1e-14 * abs(want[s]), s
+        rest = src[s].copy()
+        rest[k, j, i] = 0.0
+        assert not rest.any(), s
+    # a particle halfway between two xi nodes splits each slot evenly between them
+    b[0]["xi"] = np.array([(k + 0.5) * p.dxi])
+    src = qspic.beam_sources(p, b)
+    np.testing.assert_allclose(src[2, k:k + 2, j, i], 0.5 * want[2], rtol=1e-13)
+
+
+def test_gamma_otsi_is_the_maximum_temporal_rate():
+    """The temporal oblique-two-stream rate quoted after Eq. 6 is the largest growth rate of
+    the temporal dispersion relation of the beam-plasma system that Eq. 5 reduces: with the
+    plasma operator left without the quasistatic approximation (d_t = d_xi + d_tau), a mode
+    exp(-i k xi + sigma tau) obeys ((sigma - i k)^2 + 1) sigma^2 = Gamma^2.  Its roots are
+    found with numpy (companion matrix) and maximised over k near the plasma resonance; the
+    result tends to sqrt(3)/2^(4/3) Gamma^(2/3) as Gamma -> 0 (relative corrections
+    O(Gamma^(2/3)))."""
+    for G in (1e-6, 1e-5):
+        best = 0.0
+        for k in 1.0 + np.linspace(-0.05, 0.05, 2001) * G ** (2.0 / 3.0) * 20:
+            # sigma^4 - 2 i k sigma^3 + (1 - k^2) sigma^2 - Gamma^2 = 0
+            r = np.roots([1.0, -2j * k, 1.0 - k * k, 0.0, -G * G])
+            best = max(best, r.real.max())
+        assert abs(best / lt.gamma_otsi(G) - 1) < 3 * G ** (2.0 / 3.0) + 1e-4, (G, best)
+
+
+def test_field_energy_of_single_modes():
+    """Per-slice energies 1/2 sum F^2 dx dy dxi for fields whose energy is known in closed
+    form: B_x = A cos(k.x) gives A^2 Lx Ly dxi / 4; W_x = a, B_y = b (so E_x = a + b) gives
+    (a + b)^2 Lx Ly dxi / 2 in E_x and b^2 Lx Ly dxi / 2 in B_y; W_y = c, B_x = 0 gives E_y = c."""
+    p = _p(nx=12, ny=8, nxi=3, Lx=3.0, Ly=2.0, Lxi=1.5, dt=1.0)
+    X, Y = np.meshgrid(np.arange(p.nx) * p.dx, np.arange(p.ny) * p.dy)
+    slab = np.zeros((p.nxi + 1, 6, p.ny, p.nx))
+    A = 0.7
+    slab[1, 3] = A * np.cos(2 * math.pi * (2 * X / p.Lx + 3 * Y / p.Ly))
+    a, b, c = 0.2, -0.5, 0.3
+    slab[2, 0], slab[2, 4], slab[2, 1] = a, b, c
+    e = qspic.field_energy(p, slab)
+    area = p.Lx * p.Ly
+    want = np.zeros((p.nxi + 1, 6))
+    want[1, 3] = A * A * area * p.dxi / 4          # B_x (and E_y = W_y - B_x = -B_x)
+    want[1, 1] = A * A * area * p.dxi / 4
+    want[2, 0] = (a + b) ** 2 * area * p.dxi / 2   # E_x = W_x + B_y
+    want[2, 4] = b * b * area * p.dxi / 2
+    want[2, 1] = c * c * area * p.dxi / 2          # E_y = W_y - B_x
+    np.testing.assert_allclose(e, want, rtol=0, atol=1e-14)

@@ -15,7 +15,7 @@ from paper_2607_24214_b300 import config
 
 pytestmark = pytest.mark.gpu
 
-QSA_FP64, QSA_MIXED, QSA_ERR_ARG = 0, 1, -1
+QSA_FP64, QSA_MIXED, QSA_ERR_ARG, QSA_ERR_NONFINITE = 0, 1, -1, -5
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -70,3 +70,40 @@ def test_static_solve_rejects_large_grid(cuda_ok):
                                     ct.c_void_p(out.data_ptr()), None)
     assert rc == QSA_ERR_ARG
     assert b"128" in lib.qsa_last_error(None)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_static_solve_reports_non_finite_like_handle_solve(cuda_ok, prec):
+    """A NaN in one input makes the outputs non-finite: both entry points return
+    QSA_ERR_NONFINITE and say so, and the next call on clean inputs succeeds."""
+    import torch
+
+    from paper_2607_24214_b300.qsa import QSA, QsaError, load_library
+    lib = load_library()
+    nx, ny = 32, 24
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    p = config.Params(nx=nx, ny=ny, nxi=4, Lx=0.3 * nx, Ly=0.25 * ny, Lxi=1.0, dt=1.0,
+                      precision=prec)
+    rng = np.random.default_rng(5)
+    ins = [rng.normal(size=(ny, nx)) for _ in range(6)]
+    ins[3][4, 7] = np.nan                                        # J_z
+    q = QSA(p)
+    with pytest.raises(QsaError) as e:
+        q.field_solve(*ins, kappa2=0.5)
+    assert e.value.code == QSA_ERR_NONFINITE
+    q.close()
+    out = torch.empty((7, ny, nx), dtype=dtype, device="cuda")
+    stream = torch.cuda.current_stream()
+    code = QSA_FP64 if prec == "fp64" else QSA_MIXED
+
+    def call(arrs):
+        dev = [torch.tensor(a, dtype=dtype, device="cuda") for a in arrs]
+        return lib.qsa_field_solve_static(nx, ny, p.Lx, p.Ly, 0.5, code,
+                                          *[ct.c_void_p(t.data_ptr()) for t in dev],
+                                          ct.c_void_p(out.data_ptr()),
+                                          ct.c_void_p(stream.cuda_stream))
+    assert call(ins) == QSA_ERR_NONFINITE
+    assert b"non-finite" in lib.qsa_last_error(None)
+    ins[3][4, 7] = 0.0
+    assert call(ins) == 0, lib.qsa_last_error(None)
+    assert torch.isfinite(out).all()
