@@ -312,6 +312,35 @@ int qsa_field_solve_static(int32_t nx, int32_t ny, double Lx, double Ly, double 
                            const void* Jz, const void* Dx, const void* Dy, void* out,
                            void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Gradients of a run with respect to the seeded mode amplitudes and the beam density ratio
+ * (a discrete adjoint of the QS-PIC step).  The paper's linear theory (Eqs. 3-5) makes the
+ * growth of every transverse mode depend on alpha and on the seed the beam carries; these
+ * calls give d(loss)/d(amplitude of each qsa_mode) and d(loss)/d(alpha of each species) for
+ *   loss = 1/2 sum over the slices and cells of the final sweep of (B_x^2 + B_y^2) dx dy dxi,
+ * the transverse magnetic (filamentation) energy of the paper's Fig. 2 and Fig. 3d, after
+ * n_steps beam steps.  Both enter the run only through the initial macroparticle weights
+ * w = wbar (1 + noise) (1 + sum_m a_m cos(k_m . x0 + phi_m)) (wbar proportional to alpha).
+ *
+ * qsa_grad_forward runs n_steps x (qsa_plasma_sweep; qsa_beam_step) and the final sweep from
+ * the beam qsa_init built (the handle must be fresh: no sweep, push or qsa_set_beam before),
+ * keeps the beam state every step_ckpt steps (beam-step checkpoints), and writes the loss.
+ * qsa_grad_backward then recomputes each segment of step_ckpt steps from its checkpoint,
+ * recording every sweep slice by slice (particle state, fields of every field solve), and
+ * runs the adjoint backwards: sweep (slices in reverse), beam-source deposit, beam push.  It
+ * writes dloss * d(loss)/d(a_m) to dl_dmodes[n_modes] and dloss * d(loss)/d(alpha_s) to
+ * dl_dalpha[n_species] (either may be NULL), and leaves the handle as qsa_grad_forward left
+ * it.  The adjoint is exact for the discrete scheme (no approximation beyond rounding) when
+ * no plasma particle meets the psi floor; qsa_grad_forward returns QSA_ERR_STATE when one
+ * does.  Memory: step_ckpt + 1 beam copies and one segment's records (about
+ * (step_ckpt + 1) (7 np + 8 (n_pc_iter + 1) nx ny) (nxi + 1) doubles), allocated through
+ * the handle's allocator during qsa_grad_backward and released before it returns.
+ * Errors: QSA_ERR_ARG (not an FP64 handle, pc_tol > 0, n_steps < 0, step_ckpt < 1),
+ * QSA_ERR_STATE (handle not fresh, beam replaced, psi floor met, no recorded run),
+ * QSA_ERR_OOM, QSA_ERR_CUDA, and the device status of the sweeps.  Synchronise. */
+int qsa_grad_forward(qsa_handle* h, int32_t n_steps, int32_t step_ckpt, double* loss_out);
+int qsa_grad_backward(qsa_handle* h, double dloss, double* dl_dmodes, double* dl_dalpha);
+
 /* Tracing (the paper has no counterpart).
  * Phase timing of the last sweep: out[(j * 32 + ph) * 2 + 0] is the device
  * globaltimer (ns) when the last block arrived at the barrier closing phase ph of slice j,

@@ -16,6 +16,7 @@
 #include "qsa_pipe.cuh"
 #include "qsa_sweep.cuh"
 #include "qsa_tables.h"
+#include "qsa_adjoint.cuh"
 
 using namespace qsa;
 
@@ -60,6 +61,18 @@ struct qsa_handle {
   static constexpr int kLaunchEvents = 64;
   cudaEvent_t ev[2 * kLaunchEvents] = {};
   int n_timed = 0;
+  // the run recorded by qsa_grad_forward for qsa_grad_backward (null: none)
+  struct GradRun* grad = nullptr;
+  bool beam_replaced = false;  // qsa_set_beam replaced the beam qsa_init built
+};
+
+// State of a differentiable run between qsa_grad_forward and qsa_grad_backward.
+struct GradRun {
+  int n_steps = 0, ckpt = 10;
+  double loss = 0.0;
+  std::vector<double*> beam_ckpt;  // beam state after 0, ckpt, 2 ckpt, ... pushes
+  double* beam_end = nullptr;      // beam state after n_steps pushes
+  int64_t pushes = 0, sweeps = 0;  // the handle's counters after the forward run
 };
 
 namespace {
@@ -99,6 +112,19 @@ void* dalloc(qsa_handle* h, size_t bytes) {
     h->bytes += (int64_t)bytes;
   }
   return p;
+}
+
+// Release one allocation made through dalloc.
+void dfree(qsa_handle* h, void* p) {
+  for (size_t i = 0; i < h->allocs.size(); ++i)
+    if (h->allocs[i].first == p) {
+      const auto a = h->allocs[i];
+      h->allocs.erase(h->allocs.begin() + (long)i);
+      h->bytes -= (int64_t)a.second;
+      if (h->free_fn) h->free_fn(a.first, a.second, h->ctx, (void*)h->stream);
+      else cudaFreeAsync(a.first, h->stream);
+      return;
+    }
 }
 
 void dfree_all(qsa_handle* h) {
@@ -533,7 +559,15 @@ int launch_slots(qsa_handle* lead, PipeTable<R>& t, int nslots, int nbr, int nbc
   return QSA_OK;
 }
 
-constexpr int kPipeRowBatch = 2, kPipeColBatch = 1;  // FFT units of the chained launches
+// FFT units of the chained launches: grid rows and half-spectrum columns per unit (build
+// settings for tuning)
+#ifndef QSA_PIPE_ROW_BATCH
+#define QSA_PIPE_ROW_BATCH 2
+#endif
+#ifndef QSA_PIPE_COL_BATCH
+#define QSA_PIPE_COL_BATCH 1
+#endif
+constexpr int kPipeRowBatch = QSA_PIPE_ROW_BATCH, kPipeColBatch = QSA_PIPE_COL_BATCH;
 
 // n beam steps (sweep + push each) as wavefronts of up to S steps per persistent launch.
 template <typename R>
@@ -806,6 +840,7 @@ int beam_io(qsa_handle* h, int si, bool to_host, int64_t n, const double* const*
     if (bad) {
       rc = fail(h, QSA_ERR_ARG, "xi of a live particle outside [0, Lxi)");
     } else {
+      h->beam_replaced = true;
       beam_from_host_kernel<R><<<blocks, kThreads, 0, h->stream>>>(
           b, h->dp, s->species[si], (double*)tmp[0], (double*)tmp[1], (double*)tmp[2],
           (double*)tmp[3], (double*)tmp[4], (double*)tmp[5], (double*)tmp[6]);
@@ -913,6 +948,312 @@ int field_solve(qsa_handle* h, const double* const* in, double kappa2, double* o
       break;
     }
   rc = status_code(st);
+  return rc < 0 ? fail(h, rc, status_text(rc)) : QSA_OK;
+}
+
+// ---- the discrete adjoint (FP64 handles)
+
+// Doubles of one flat copy of every species' beam state (ox, oy, oxi, ux, uy, uz, dw).
+size_t beam_doubles(qsa_handle* h) {
+  size_t n = 0;
+  for (const auto& b : S<double>(h)->beams) n += 7 * (size_t)b.n;
+  return n;
+}
+// Views of species si's arrays inside a flat copy.
+BeamArrays<double> beam_view(qsa_handle* h, double* base, int si) {
+  State<double>* s = S<double>(h);
+  size_t off = 0;
+  for (int k = 0; k < si; ++k) off += 7 * (size_t)s->beams[k].n;
+  BeamArrays<double> v{};
+  const size_t n = (size_t)s->beams[si].n;
+  v.n = (long long)n;
+  double* q = base + off;
+  v.ox = q; v.oy = q + n; v.oxi = q + 2 * n; v.ux = q + 3 * n; v.uy = q + 4 * n;
+  v.uz = q + 5 * n; v.dw = q + 6 * n;
+  return v;
+}
+// Copy the handle's beam to a flat copy (to_copy) or back.
+int beam_copy(qsa_handle* h, double* flat, bool to_copy) {
+  State<double>* s = S<double>(h);
+  for (size_t si = 0; si < s->beams.size(); ++si) {
+    const BeamArrays<double>& b = s->beams[si];
+    const BeamArrays<double> v = beam_view(h, flat, (int)si);
+    const size_t by = (size_t)b.n * sizeof(double);
+    double* hs[7] = {b.ox, b.oy, b.oxi, b.ux, b.uy, b.uz, b.dw};
+    double* cs[7] = {v.ox, v.oy, v.oxi, v.ux, v.uy, v.uz, v.dw};
+    for (int k = 0; k < 7; ++k)
+      CK(cudaMemcpyAsync(to_copy ? cs[k] : hs[k], to_copy ? hs[k] : cs[k], by,
+                         cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return QSA_OK;
+}
+
+void grad_release(qsa_handle* h) {
+  if (!h->grad) return;
+  for (double* p : h->grad->beam_ckpt) dfree(h, p);
+  if (h->grad->beam_end) dfree(h, h->grad->beam_end);
+  delete h->grad;
+  h->grad = nullptr;
+}
+
+int grad_forward(qsa_handle* h, int n_steps, int ckpt, double* loss_out) {
+  State<double>* s = S<double>(h);
+  const DevParams& dp = h->dp;
+  grad_release(h);
+  h->grad = new GradRun();
+  GradRun& G = *h->grad;
+  G.n_steps = n_steps;
+  G.ckpt = ckpt;
+  const size_t nb = beam_doubles(h);
+  auto save = [&](std::vector<double*>& v) -> int {
+    double* c = (double*)dalloc(h, nb * sizeof(double));
+    if (!c) return fail(h, QSA_ERR_OOM, "beam checkpoint");
+    v.push_back(c);
+    return beam_copy(h, c, true);
+  };
+  if (int rc = save(G.beam_ckpt)) return rc;
+  for (int n = 0; n < n_steps; ++n) {
+    if (int rc = sweep<double>(h)) return rc;
+    if (int rc = beam_step<double>(h)) return rc;
+    if ((n + 1) % ckpt == 0 && n + 1 < n_steps)
+      if (int rc = save(G.beam_ckpt)) return rc;
+  }
+  if (!(G.beam_end = (double*)dalloc(h, nb * sizeof(double))))
+    return fail(h, QSA_ERR_OOM, "beam checkpoint");
+  if (int rc = beam_copy(h, G.beam_end, true)) return rc;
+  if (int rc = sweep<double>(h)) return rc;
+  // the loss of the final sweep, and the status of every sweep of the run
+  double* dl = (double*)dalloc(h, sizeof(double));
+  if (!dl) return fail(h, QSA_ERR_OOM, "loss");
+  CK(cudaMemsetAsync(dl, 0, sizeof(double), h->stream));
+  const size_t ncell = (size_t)dp.nk * dp.nx * dp.ny;
+  bperp_loss_kernel<<<std::min<size_t>((ncell + 255) / 256, 4096), 256, 0, h->stream>>>(
+      s->slots[0].slab, ncell, dp.dx * dp.dy * dp.dxi, 0.0, nullptr, dl);
+  ++h->launches;
+  CK(cudaGetLastError());
+  int st = 0;
+  CK(cudaMemcpyAsync(&G.loss, dl, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&st, s->slots[0].bar.status, sizeof(int), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  dfree(h, dl);
+  if (st & ST_FLOOR)
+    return fail(h, QSA_ERR_STATE, "the psi floor was met: the adjoint takes it as inactive");
+  const int rc = status_code(st);
+  if (rc < 0) return fail(h, rc, status_text(rc));
+  G.pushes = h->pushes;
+  G.sweeps = h->sweeps;
+  *loss_out = G.loss;
+  return QSA_OK;
+}
+
+int grad_backward(qsa_handle* h, double dloss, double* dmodes, double* dalpha) {
+  State<double>* s = S<double>(h);
+  const DevParams& dp = h->dp;
+  GradRun& G = *h->grad;
+  const int N = G.n_steps, K = G.ckpt, nk = dp.nk, n_pc = dp.n_pc;
+  const size_t g = (size_t)dp.nx * dp.ny, np = (size_t)dp.np, spec = (size_t)dp.nxh * dp.ny;
+  const size_t nb = beam_doubles(h);
+  const int seg = std::min(K, N) + 1;  // sweeps of the longest segment
+  std::vector<void*> mine;
+  bool oom = false;
+  auto A = [&](size_t bytes) -> double* {
+    void* p = dalloc(h, bytes);
+    if (!p) oom = true;
+    else mine.push_back(p);
+    return (double*)p;
+  };
+  auto release = [&]() {
+    for (auto it = mine.rbegin(); it != mine.rend(); ++it) dfree(h, *it);
+    mine.clear();
+  };
+  // segment store: tapes, slabs, beam states, per-sweep psi0 and kappa^2
+  const size_t tp = (size_t)nk * 5 * np, tf = (size_t)nk * (n_pc + 1) * g * kFG,
+               tj = (size_t)nk * 2 * spec;
+  std::vector<double*> tpart(seg), tfg(seg), slabs(seg), beams(seg), psi0s(seg), kaps(seg);
+  std::vector<C<double>*> tjp(seg);
+  for (int i = 0; i < seg; ++i) {
+    tpart[i] = A(tp * sizeof(double));
+    tfg[i] = A(tf * sizeof(double));
+    tjp[i] = (C<double>*)A(tj * sizeof(C<double>));
+    slabs[i] = A((size_t)nk * g * 8 * sizeof(double));
+    beams[i] = A(nb * sizeof(double));
+    psi0s[i] = A((size_t)nk * sizeof(double));
+    kaps[i] = A((size_t)nk * sizeof(double));
+  }
+  // adjoint buffers
+  AdjArgs a{};
+  a.p = dp;
+  a.w = dp.dx * dp.dy / dp.ppc;
+  a.idx = 1.0 / dp.dx;
+  a.idy = 1.0 / dp.dy;
+  a.dv = 1.0 / (dp.dx * dp.dy);
+  a.inv_LxLy = 1.0 / (dp.Lx * dp.Ly);
+  double* lslab = A((size_t)nk * g * 8 * sizeof(double));
+  a.lslab = lslab;
+  a.lsrc = A((size_t)nk * g * 4 * sizeof(double));
+  const size_t npart_adj = 9 * np, ngrid_adj = 22 * g;
+  double* pa = A(npart_adj * sizeof(double));
+  double* ga = A(ngrid_adj * sizeof(double));
+  a.zs = (C<double>*)A(8 * g * sizeof(C<double>));
+  a.zt = (C<double>*)A(8 * g * sizeof(C<double>));
+  // beam adjoints (positions, momenta, weight) of every species
+  double* lbeam = A(nb * sizeof(double));
+  double* gout = A(17 * (size_t)std::max(1, (int)s->species.size()) * sizeof(double));
+  if (oom) {
+    release();
+    return fail(h, QSA_ERR_OOM, "adjoint buffers");
+  }
+  if (pa) {
+    double** pp[9] = {&a.lx, &a.ly, &a.lux, &a.luy, &a.lpp, &a.lopp, &a.loph, &a.lgx, &a.lgy};
+    for (int k = 0; k < 9; ++k) *pp[k] = pa + (size_t)k * np;
+  }
+  {
+    double* q = ga;
+    for (int b = 0; b < 2; ++b)
+      for (int k = 0; k < 3; ++k) { a.lpsi[b][k] = q; q += g; }
+    for (int b = 0; b < 2; ++b)
+      for (int k = 0; k < 3; ++k) { a.lB[b][k] = q; q += g; }
+    for (int b = 0; b < 2; ++b)
+      for (int k = 0; k < 2; ++k) { a.ljp[b][k] = q; q += g; }
+    a.lS = q; q += g;
+    for (int k = 0; k < 5; ++k) { a.lJ[k] = q; q += g; }
+  }
+  a.twx = s->slots[0].twx;
+  a.twy = s->slots[0].twy;
+  a.ktab = s->slots[0].ktab;
+  a.bar = s->slots[0].bar;
+  const size_t asmem = adj_smem_bytes(dp.nx, dp.ny);
+  CK(raise_dyn_smem((const void*)adj_sweep_kernel, asmem));
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_sweep_kernel, kThreads, asmem));
+  if (per_sm < 1) {
+    release();
+    return fail(h, QSA_ERR_ARG, "adjoint kernel does not fit on an SM");
+  }
+  const int agrid = per_sm * h->num_sms;
+  double* part = A((size_t)agrid * 4 * sizeof(double));
+  if (oom) {
+    release();
+    return fail(h, QSA_ERR_OOM, "adjoint buffers");
+  }
+  a.part = part;
+  // the beam adjoint, as per-species views of lbeam
+  auto ladj = [&](int si) {
+    const BeamArrays<double> v = beam_view(h, lbeam, si);
+    return BeamAdj{v.ox, v.oy, v.oxi, v.ux, v.uy, v.uz, v.dw};
+  };
+  CK(cudaMemsetAsync(lbeam, 0, nb * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(gout, 0, 17 * std::max<size_t>(1, s->species.size()) * sizeof(double),
+                     h->stream));
+  const double npc = (double)dp.ppc * dp.nx * dp.ny;
+  std::vector<double> diag((size_t)D_COUNT * nk), kv(nk);
+  const int nseg = (N + K) / K;  // segments start at 0, K, 2K, ... <= N
+  for (int m = nseg - 1; m >= 0; --m) {
+    const int n0 = m * K, n1 = std::min(n0 + K, N + 1);
+    // recompute the segment from its checkpoint, recording every sweep
+    // the state a segment starts from: a checkpoint, or the end state for a segment that
+    // holds only the final sweep
+    double* ck = (n0 == N) ? G.beam_end : G.beam_ckpt[m];
+    if (int rc = beam_copy(h, ck, false)) { release(); return rc; }
+    h->src_valid = false;
+    for (int n = n0; n < n1; ++n) {
+      const int i = n - n0;
+      SweepArgs<double>& sa = s->slots[0];
+      sa.tape = Tape<double>{tpart[i], tfg[i], tjp[i]};
+      int rc = sweep<double>(h);
+      sa.tape = Tape<double>{nullptr, nullptr, nullptr};
+      if (rc) { release(); return rc; }
+      CK(cudaMemcpyAsync(slabs[i], sa.slab, (size_t)nk * g * 8 * sizeof(double),
+                         cudaMemcpyDeviceToDevice, h->stream));
+      if ((rc = beam_copy(h, beams[i], true))) { release(); return rc; }
+      CK(cudaMemcpyAsync(diag.data(), sa.diag, diag.size() * sizeof(double),
+                         cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      for (int j = 0; j < nk; ++j) kv[j] = diag[(size_t)D_KAPPA * nk + j] / npc;
+      CK(cudaMemcpyAsync(psi0s[i], diag.data() + (size_t)D_PSI0 * nk, nk * sizeof(double),
+                         cudaMemcpyHostToDevice, h->stream));
+      CK(cudaMemcpyAsync(kaps[i], kv.data(), nk * sizeof(double), cudaMemcpyHostToDevice,
+                         h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      if (n < N)
+        if ((rc = beam_step<double>(h))) { release(); return rc; }
+    }
+    // backwards through the segment
+    for (int n = n1 - 1; n >= n0; --n) {
+      const int i = n - n0;
+      if (n == N) {
+        const size_t ncell = (size_t)nk * g;
+        bperp_loss_kernel<<<std::min<size_t>((ncell + 255) / 256, 4096), 256, 0, h->stream>>>(
+            slabs[i], ncell, dp.dx * dp.dy * dp.dxi, dloss, lslab, nullptr);
+        ++h->launches;
+      } else {
+        // push n: beam state n through slab n gives beam state n + 1
+        CK(cudaMemsetAsync(lslab, 0, (size_t)nk * g * 8 * sizeof(double), h->stream));
+        for (size_t si = 0; si < s->beams.size(); ++si) {
+          const BeamArrays<double> b = beam_view(h, beams[i], (int)si);
+          if (b.n == 0) continue;
+          beam_push_adj_kernel<<<(unsigned)((b.n + kThreads - 1) / kThreads), kThreads, 0,
+                                 h->stream>>>(b, dp, s->species[si], slabs[i], lslab,
+                                              ladj((int)si));
+          ++h->launches;
+        }
+      }
+      CK(cudaGetLastError());
+      // the sweep of step n
+      CK(cudaMemsetAsync(a.lsrc, 0, (size_t)nk * g * 4 * sizeof(double), h->stream));
+      CK(cudaMemsetAsync(pa, 0, npart_adj * sizeof(double), h->stream));
+      CK(cudaMemsetAsync(ga, 0, ngrid_adj * sizeof(double), h->stream));
+      CK(cudaMemsetAsync(a.bar.count, 0, sizeof(unsigned), h->stream));
+      a.tape = Tape<double>{tpart[i], tfg[i], tjp[i]};
+      a.psi0 = psi0s[i];
+      a.kappa2 = kaps[i];
+      void* args[] = {&a};
+      CK(cudaLaunchCooperativeKernel((void*)adj_sweep_kernel, dim3(agrid), dim3(kThreads), args,
+                                     asmem, h->stream));
+      ++h->launches;
+      // the beam sources of step n, deposited from beam state n
+      for (size_t si = 0; si < s->beams.size(); ++si) {
+        const BeamArrays<double> b = beam_view(h, beams[i], (int)si);
+        if (b.n == 0) continue;
+        beam_src_adj_kernel<<<(unsigned)((b.n + kThreads - 1) / kThreads), kThreads, 0,
+                              h->stream>>>(b, dp, s->species[si], a.lsrc, ladj((int)si));
+        ++h->launches;
+      }
+      CK(cudaGetLastError());
+    }
+  }
+  // weights -> mode amplitudes and alpha, per species
+  for (size_t si = 0; si < s->beams.size(); ++si) {
+    const BeamArrays<double> b0 = beam_view(h, G.beam_ckpt[0], (int)si);
+    if (b0.n == 0) continue;
+    weight_grad_kernel<<<(unsigned)((b0.n + kThreads - 1) / kThreads), kThreads, 0,
+                         h->stream>>>(b0.dw, b0.n, dp, s->species[si], s->modes,
+                                      ladj((int)si).lw, gout + 17 * si);
+    ++h->launches;
+  }
+  CK(cudaGetLastError());
+  std::vector<double> go(17 * std::max<size_t>(1, s->species.size()));
+  int st = 0;
+  CK(cudaMemcpyAsync(go.data(), gout, go.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaMemcpyAsync(&st, a.bar.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  // leave the handle as the forward run left it
+  if (int rc = beam_copy(h, G.beam_end, false)) { release(); return rc; }
+  CK(cudaStreamSynchronize(h->stream));
+  release();
+  h->pushes = G.pushes;
+  h->sweeps = G.sweeps;
+  h->src_valid = false;
+  const int nm = s->modes.n;
+  if (dmodes)
+    for (int k = 0; k < nm; ++k) {
+      dmodes[k] = 0.0;
+      for (size_t si = 0; si < s->species.size(); ++si) dmodes[k] += go[17 * si + k];
+    }
+  if (dalpha)
+    for (size_t si = 0; si < s->species.size(); ++si) dalpha[si] = go[17 * si + nm];
+  const int rc = status_code(st);
   return rc < 0 ? fail(h, rc, status_text(rc)) : QSA_OK;
 }
 
@@ -1164,6 +1505,32 @@ int qsa_field_solve(qsa_handle* h, const double* S_, const double* Jx, const dou
   return h->fp64 ? field_solve<double>(h, in, kappa2, out) : field_solve<float>(h, in, kappa2, out);
 }
 
+int qsa_grad_forward(qsa_handle* h, int32_t n_steps, int32_t step_ckpt, double* loss_out) {
+  NvtxRange nvtx_range("qsa_grad_forward");
+  if (!h || !loss_out) return QSA_ERR_ARG;
+  if (!h->fp64) return fail(h, QSA_ERR_ARG, "the adjoint needs an FP64 handle");
+  if (n_steps < 0 || step_ckpt < 1) return fail(h, QSA_ERR_ARG, "n_steps >= 0, step_ckpt >= 1");
+  if (h->dp.pc_tol2 > 0.0)
+    return fail(h, QSA_ERR_ARG, "the adjoint needs a fixed predictor-corrector count (pc_tol 0)");
+  if (h->pushes != 0 || h->sweeps != 0)
+    return fail(h, QSA_ERR_STATE, "the run must start from the beam qsa_init built");
+  if (h->beam_replaced)
+    return fail(h, QSA_ERR_STATE, "the beam was replaced: the weights no longer follow the "
+                                  "mode amplitudes and alpha");
+  const int rc = grad_forward(h, n_steps, step_ckpt, loss_out);
+  if (rc) grad_release(h);
+  return rc;
+}
+
+int qsa_grad_backward(qsa_handle* h, double dloss, double* dl_dmodes, double* dl_dalpha) {
+  NvtxRange nvtx_range("qsa_grad_backward");
+  if (!h) return QSA_ERR_ARG;
+  if (!h->grad) return fail(h, QSA_ERR_STATE, "no run recorded by qsa_grad_forward");
+  const int rc = grad_backward(h, dloss, dl_dmodes, dl_dalpha);
+  grad_release(h);
+  return rc;
+}
+
 int qsa_phase_times(qsa_handle* h, int64_t* out, int cap) {
   if (!h || !out) return QSA_ERR_ARG;
   const int n = kTimedSlices * kTimedPhases * 2;
@@ -1218,6 +1585,8 @@ int qsa_bounds_check(int64_t* first_line, int64_t* count) {
 void qsa_destroy(qsa_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  delete h->grad;  // its buffers go with every other allocation below
+  h->grad = nullptr;
   dfree_all(h);
   cudaStreamSynchronize(h->stream);
   if (h->st) {

@@ -40,7 +40,11 @@ namespace qsa {
 
 constexpr int kMaxPipe = 16;
 constexpr int kMaxSpecies = 4;
-constexpr int kPipeBlocksPerSM = 4;  // resident blocks per SM the register budget is set for
+// resident blocks per SM the register budget is set for (a build setting for tuning)
+#ifndef QSA_PIPE_BLOCKS_PER_SM
+#define QSA_PIPE_BLOCKS_PER_SM 4
+#endif
+constexpr int kPipeBlocksPerSM = QSA_PIPE_BLOCKS_PER_SM;
 
 // The beam side of one slot: its push reads cmax_in and the slot's slab, and writes the
 // sources of the next sweep (src_next), the extents cmax_out and the beam moments mom_out.

@@ -106,6 +106,20 @@ inline SweepConst<R> sweep_consts(const DevParams& p) {
   return k;
 }
 
+// Record of one sweep for its adjoint (all pointers null: nothing recorded).  Per slice j:
+//   part[j][5][np]: x, y (absolute, in units of length, unwrapped), u_x, u_y (u^{j-1/2}) and
+//     the previous slice's psi_p of every plasma particle as the slice starts;
+//   fg[j][s][ny][nx][8]: the interleaved field grid as the slice starts (s = 0: psi, grad psi
+//     of slice j and the B guess, the previous slice's final fields) and after each of its
+//     n_pc field solves (s = 1..n_pc);
+//   jprev[j][2][nxh][ny]: the spectra of the total J_perp^{j-1/2}.
+template <typename R>
+struct Tape {
+  R* part;
+  R* fg;
+  C<R>* jprev;
+};
+
 template <typename R>
 struct SweepArgs {
   DevParams p;
@@ -131,6 +145,7 @@ struct SweepArgs {
   const double* bref;                       // [nk] beam J_z reference density per node
   unsigned long long* ptimes;               // [kTimedSlices][kTimedPhases][2] or null
   Barrier bar;
+  Tape<R> tape;                             // recording for the adjoint, or all null
 };
 
 // ------------------------------------------------------------------ particle helpers
@@ -1155,6 +1170,37 @@ __device__ bool pc_converged(const SweepArgs<R>& a, int j) {
   return s_conv != 0;
 }
 
+// Copies into the tape (see Tape): snap 0 at the start of slice j also takes the particle
+// state and the J_perp^{j-1/2} spectra.  All blocks share the copy (grid-stride); it only
+// reads buffers that no phase writes before the next grid barrier but one.
+template <typename R>
+__device__ void record_tape(const SweepArgs<R>& a, int j, int snap) {
+  const DevParams& p = a.p;
+  const size_t g = (size_t)p.nx * p.ny;
+  const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, st = (size_t)gridDim.x * blockDim.x;
+  R* fdst = a.tape.fg + ((size_t)j * (p.n_pc + 1) + snap) * g * kFG;
+  for (size_t e = t0; e < g * kFG; e += st) fdst[e] = a.fg[e];
+  if (snap != 0) return;
+  const size_t np = (size_t)p.np;
+  R* pd = a.tape.part + (size_t)j * 5 * np;
+  const int per_chunk = p.ppc * p.nx;
+  for (size_t i = t0; i < np; i += st) {
+    const int crow = (int)(i / per_chunk);
+    const int rem = (int)(i - (size_t)crow * per_chunk);
+    const int sub = rem / p.nx, ix = rem - sub * p.nx;
+    const int sy = sub / p.ppx, sx = sub - sy * p.ppx;
+    const R hx = (R(sx) + R(0.5)) * a.k.inv_ppx, hy = (R(sy) + R(0.5)) * a.k.inv_ppy;
+    pd[i] = (R(ix) + hx + a.pox[i]) * R(p.dx);
+    pd[np + i] = (R(crow) + hy + a.poy[i]) * R(p.dy);
+    pd[2 * np + i] = a.pux[i];
+    pd[3 * np + i] = a.puy[i];
+    pd[4 * np + i] = a.ppsi[i];
+  }
+  const size_t spec = (size_t)p.nxh * p.ny;
+  C<R>* jd = a.tape.jprev + (size_t)j * 2 * spec;
+  for (size_t e = t0; e < 2 * spec; e += st) jd[e] = a.jprev[e];
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256, 2) sweep_kernel(SweepArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1186,11 +1232,14 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(SweepArgs<R> a) {
   // tolerance mode: every solve may be the last, so each one completes the slice's outputs
   // (slab, diagnostics), and the loop stops after the first that has converged
   const bool tol = p.pc_tol2 > 0.0;
+  const bool rec = a.tape.part != nullptr;
   for (int j = 0; j < p.nk; ++j) {
     double ez0n = ez0h, ez0j = ez0h;
     int nsolve = p.n_pc;
+    if (rec) record_tape(a, j, 0);
     for (int it = 0; it < p.n_pc; ++it) {
       const bool first = (it == 0), last = tol || (it == p.n_pc - 1);
+      if (rec && it > 0) record_tape(a, j, it);
       dep_phase(a, tile, DEP_TRIAL, j, psi0, first, last, u0, G);
       if (!sync(j, 4 * it + 0)) return;
       row_phase(a, buf, tw, DEP_TRIAL, j, u0, G, 1);
@@ -1209,6 +1258,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(SweepArgs<R> a) {
         break;
       }
     }
+    if (rec) record_tape(a, j, p.n_pc);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.diag[D_PSI0 * p.nk + j] = psi0;
       a.diag[D_EZ0 * p.nk + j] = ez0j;

@@ -87,6 +87,70 @@ def dpy_rear(Gamma, xi, tau_sat, gamma_b, ky=1.0):
     return gamma_b * rate_rear(Gamma, xi, tau_sat) / ky
 
 
+def ex_wake_amplitude(rho_b, length, width):
+    """Longitudinal wake field behind a current filament (the paper's E_x, E_z here), from the
+    blazar paragraph: |2 rho_b sin(l/2)| (1 - exp(-w)), rho_b the filament's charge density,
+    l its length, w its transverse size.  The first factor is the linear plasma wake behind a
+    flat-top bunch of length l (Eq. 1 for a step-on, step-off source); the second is the
+    on-axis share of a transversely finite source under the screened operator of Eq. 2, whose
+    Green's function in the paper's 2D geometry is exp(-|y|)/2: a slab |y| < w keeps
+    1 - exp(-w) of the field of an unbounded one.  w is read as the half-width."""
+    return np.abs(2.0 * np.asarray(rho_b, dtype=float) * np.sin(0.5 * np.asarray(length))) \
+        * (1.0 - np.exp(-np.asarray(width, dtype=float)))
+
+
+def dpx_spread(rho_b, tau):
+    """Longitudinal momentum spread the filament wakes build up in the beam, Delta p_x ~
+    |rho_b| tau (blazar paragraph; Delta p_x is u_z here)."""
+    return np.abs(np.asarray(rho_b, dtype=float)) * np.asarray(tau, dtype=float)
+
+
+def filament_sizes(rho, dx, dy, dxi):
+    """Sizes of the current filaments in a block of beam charge density rho[k, iy, ix] (xi
+    slices k dxi of the front region, periodic transverse grid), from the fluctuation
+    d = rho - <rho>_(x, y) of each slice and its transverse power spectrum P(k) summed over
+    the slices, averaged over shells of |k| one box wavenumber wide:
+      spacing: 2 pi / |k| at the peak of P (the distance between neighbouring filaments);
+      width: the filament's full width at half maximum 2 sqrt(2 ln 2) s, with s from the
+        roll-off of P above its peak: a Gaussian filament of standard deviation s has
+        |F(k)|^2 ~ exp(-k^2 s^2), and the filaments' positions only multiply that by a
+        structure factor that tends to 1 at large k (fitted where P is above 1e-4 of its
+        peak, up to the grid's Nyquist wavenumber);
+      length: twice the xi lag at which the longitudinal autocorrelation
+        sum_k d_k d_(k+m) / sum_k d_k^2 (over the grid) first falls below 1/2; for filaments of
+        a flat-top profile of length l it falls as 1 - m dxi / l, to 1/2 at l/2.
+    Returns dict(spacing, width, length, rho_rms) with rho_rms the rms of d."""
+    rho = np.asarray(rho, dtype=float)
+    nk, ny, nx = rho.shape
+    d = rho - rho.mean(axis=(1, 2), keepdims=True)
+    P = (np.abs(np.fft.fft2(d, axes=(1, 2))) ** 2).sum(axis=0)
+    P[0, 0] = 0.0
+    KX, KY = np.meshgrid(2 * np.pi * np.fft.fftfreq(nx, d=dx), 2 * np.pi * np.fft.fftfreq(ny, d=dy))
+    dk = 2 * np.pi / max(nx * dx, ny * dy)
+    shell = np.rint(np.hypot(KX, KY) / dk).astype(int)
+    cnt = np.bincount(shell.ravel())
+    avg = np.bincount(shell.ravel(), weights=P.ravel()) / np.maximum(cnt, 1)
+    kp = int(np.argmax(avg[1:])) + 1
+    spacing = 2 * np.pi / (kp * dk)
+    kk = np.arange(avg.size) * dk
+    sel = ((np.arange(avg.size) >= kp) & (avg > 1e-4 * avg[kp]) &
+           (kk <= np.pi / max(dx, dy)))
+    slope = np.polyfit(kk[sel] ** 2, np.log(avg[sel]), 1)[0] if sel.sum() >= 2 else 0.0
+    sd = math.sqrt(max(-slope, 0.0))
+
+    def half_crossing(r, h):
+        """Lag (in units of h) where the sequence r (r[0] = 1) first falls below 1/2."""
+        for i in range(1, r.size):
+            if r[i] < 0.5:
+                return (i - 1 + (r[i - 1] - 0.5) / (r[i - 1] - r[i])) * h
+        return r.size * h
+
+    s2 = np.sum(d * d)
+    r = np.array([1.0] + [np.sum(d[:-m] * d[m:]) / s2 for m in range(1, nk)])
+    return {"spacing": float(spacing), "width": float(2.0 * math.sqrt(2.0 * math.log(2.0)) * sd),
+            "length": float(2 * half_crossing(r, dxi)), "rho_rms": float(np.sqrt(s2 / d.size))}
+
+
 # ------------------------------------------------------------------ the run
 FIELD_NAMES = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")  # order of the rms columns of qsa_diag
 

@@ -6,6 +6,7 @@ own limits.  The paper rounds its results to one or two figures."""
 import math
 
 import numpy as np
+import pytest
 
 from paper_2607_24214_b300 import config, nonlinear as nl
 
@@ -102,3 +103,77 @@ def test_summary_reads_synthetic_growth():
     assert abs(s["front_Bperp"]["rate_ratio_end"] - (1 + xf / (4 * G * tm))) < 0.01
     assert abs(s["rear_Eperp"]["rate_ratio_end"] - 1) < 0.01
     assert abs(s["rear_Eperp"]["eps_end"] / nl.fractional_energy(er[-1] ** 2, 1e-4, 1e4) - 1) < 1e-12
+
+
+def _flat_top_bunch_wake(alpha, length, half_width=None):
+    """On-axis E_z oscillation amplitude behind an electron bunch of density alpha, flat-top
+    of length `length` from the front, in the FP64 oracle's QS-PIC (small alpha: the linear
+    regime).  Without half_width the bunch fills the transverse box; with it the bunch is a
+    slab |y - Ly/2| < half_width in the paper's 2D3V geometry (nx = 1)."""
+    from oracle import qspic
+    from paper_2607_24214_b300 import inputs
+    dxi = 0.0625
+    if half_width is None:
+        p = config.Params(nx=4, ny=4, nxi=int(16 / dxi), Lx=1.0, Ly=1.0, Lxi=16.0, dt=1.0,
+                          species=[config.Species(Z=-1, M=1, alpha=alpha, gamma_b=1e3,
+                                                  xi_back=length)])
+        slab, d = qspic.plasma_sweep(p, qspic.beam_sources(p, inputs.all_beams(p)))
+        ez = d["ez0"]
+    else:
+        ny, Ly = 256, 25.6
+        dy = Ly / ny
+        p = config.Params(nx=1, ny=ny, nxi=int(12 / dxi), Lx=dy, Ly=Ly, Lxi=12.0, dt=1.0,
+                          species=[config.Species(Z=-1, M=1, alpha=alpha, gamma_b=1e3)],
+                          ppc_plasma_x=1, ppc_plasma_y=2)
+        iy = np.arange(int(round((Ly / 2 - half_width) / dy)),
+                       int(round((Ly / 2 + half_width) / dy)))
+        ks = np.arange(int(round(length / dxi)))
+        Y, XI = np.meshgrid(np.concatenate([(iy + 0.25) * dy, (iy + 0.75) * dy]),
+                            np.concatenate([(ks + 0.25) * dxi, (ks + 0.75) * dxi]))
+        n = Y.size
+        b = dict(x=np.full(n, 0.5 * dy), y=Y.ravel(), xi=XI.ravel(), ux=np.zeros(n),
+                 uy=np.zeros(n), uz=np.full(n, math.sqrt(1e6 - 1.0)),
+                 w=np.full(n, alpha * dy * dy * dxi / 4))
+        slab, _ = qspic.plasma_sweep(p, qspic.beam_sources(p, [b]))
+        ez = slab[:, 2, int(round(Ly / 2 / dy)), 0]
+    xs = np.arange(p.nxi + 1) * dxi
+    return np.abs(ez[xs > length + 0.5]).max()
+
+
+def test_filament_wake_estimate_against_the_qspic_response():
+    """The filament wake estimate |2 rho_b sin(l/2)| (1 - exp(-w)) of the blazar paragraph
+    against the oracle's plasma response to a flat-top bunch of length l (Eq. 1 with a
+    step-on, step-off source): unbounded in the transverse plane (the first factor alone),
+    and a slab of half-width w in the 2D geometry (the width factor); both within 1 %."""
+    alpha = 1e-4
+    for length in (5.0, 2.0):
+        got = _flat_top_bunch_wake(alpha, length)
+        assert abs(got / nl.ex_wake_amplitude(alpha, length, np.inf) - 1) < 0.01, length
+    for w in (1.0, 0.5):
+        got = _flat_top_bunch_wake(alpha, 5.0, half_width=w)
+        assert abs(got / nl.ex_wake_amplitude(alpha, 5.0, w) - 1) < 0.01, w
+    # the longitudinal spread the wakes build: |rho_b| tau
+    assert nl.dpx_spread(-2e-10, 1e10) == pytest.approx(2.0)
+
+
+def test_filament_sizes_of_synthetic_filaments():
+    """filament_sizes on Gaussian filaments of known spacing, width and length (square and
+    jittered lattices): spacing exact, width within 6 %, length within one slice."""
+    rng = np.random.default_rng(0)
+    n, h, dxi, nk = 64, 0.125, 0.125, 80
+    X, Y = np.meshgrid(np.arange(n) * h, np.arange(n) * h)
+    B = n * h
+    for s, lam, length, jitter in ((0.25, 2.0, 5.0, 0.0), (0.4, 2.0, 3.0, 0.0),
+                                   (0.3, 1.6, 6.0, 0.0), (0.3, 2.0, 5.0, 0.3)):
+        f = np.zeros((n, n))
+        for cx in np.arange(0.3, B, lam):
+            for cy in np.arange(0.3, B, lam):
+                jx, jy = rng.uniform(-jitter, jitter, 2)
+                dx_ = np.mod(X - cx - jx + B / 2, B) - B / 2
+                dy_ = np.mod(Y - cy - jy + B / 2, B) - B / 2
+                f += np.exp(-(dx_ ** 2 + dy_ ** 2) / (2 * s * s))
+        rho = np.array([f if (k + 0.5) * dxi < length else 0 * f for k in range(nk)])
+        r = nl.filament_sizes(rho, h, h, dxi)
+        assert r["spacing"] == pytest.approx(lam)
+        assert abs(r["width"] / (2 * math.sqrt(2 * math.log(2)) * s) - 1) < 0.06, (s, r)
+        assert abs(r["length"] - length) <= dxi, (length, r)
