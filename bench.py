@@ -215,6 +215,48 @@ def cpu_baseline(p, slices=CPU_SAMPLE_SLICES):
     return p.plasma_per_slice() * slices / dt, dt
 
 
+def _cpu_sample(args):
+    """One oracle sample in a worker process (one thread): updates and seconds."""
+    import os as _os
+    _os.environ["OMP_NUM_THREADS"] = "1"
+    p, slices = args
+    return cpu_baseline(p, slices)
+
+
+def cpu_baseline_all_cores(p, slices=CPU_SAMPLE_SLICES, max_procs=16):
+    """The same oracle sample run in one process per core (spawned, one thread each, up to
+    max_procs), all at once: the aggregate updates/s of the host's cores on independent
+    samples (the slice loop of one sweep is sequential, so independent samples are how the
+    oracle uses more cores).  Returns (updates/s, processes, seconds)."""
+    import multiprocessing as mp
+    try:
+        ncore = len(os.sched_getaffinity(0))
+    except AttributeError:
+        ncore = os.cpu_count() or 1
+    nproc = max(1, min(ncore, max_procs))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(nproc) as pool:
+        pool.map(_cpu_sample, [(p, 1)] * nproc)  # start-up and imports outside the timing
+        t = time.perf_counter()
+        res = pool.map(_cpu_sample, [(p, slices)] * nproc)
+        dt = time.perf_counter() - t
+    ups = sum(p.plasma_per_slice() * slices for _ in res)
+    return ups / dt, nproc, dt, ncore
+
+
+def cpu_c1_full():
+    """The oracle on the whole C1 run (32 x 32, 64 slices, 10 beam steps and the final sweep),
+    one thread: updates/s and seconds."""
+    from oracle import qspic
+    from paper_2607_24214_b300 import inputs
+    p = config.c1_fp64_electron_beam()
+    beams = inputs.all_beams(p)
+    t = time.perf_counter()
+    qspic.run(p, beams, p.steps)
+    dt = time.perf_counter() - t
+    return p.plasma_per_slice() * p.nxi * p.steps / dt, dt
+
+
 def run_reference(args, p):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -258,8 +300,10 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-c3", action="store_true",
                     help="skip the full-size pair-beam workload (224 GB on the device)")
-    ap.add_argument("--batch-steps", type=int, default=4,
-                    help="timed steps of the batched C4 scan (after 8 untimed, autotuning)")
+    ap.add_argument("--batch-steps", type=int, default=42,
+                    help="timed steps of the batched C4 scan after its 8 untimed autotuning "
+                         "steps (42: the scan's 50 steps in all)")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--steps-ref", type=int, default=2)
     ap.add_argument("--ref-slices", type=int, default=CPU_SAMPLE_SLICES,
                     help="slices of the oracle sample per reference step")
@@ -379,16 +423,28 @@ def main():
         line["e2e"] = e2e(p, args.e2e_steps, torch, stream)
 
     if not args.no_batch:
-        line["batched"] = batched(args.batch_steps, torch, stream)
+        line["batched"] = batched(args.batch_steps, torch, stream, hbm_peak)
 
     if not args.no_c3:
         line["pair_beam"] = pair_beam(torch, stream)
+
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_cost(torch, stream)
 
     if rank == 0 and not args.no_cpu:
         v, dt = cpu_baseline(p)
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
                                 "sample": f"first {CPU_SAMPLE_SLICES} of {p.nxi + 1} slices of "
                                           f"one sweep of the same workload ({dt:.1f} s)"}
+        va, nproc, dta, ncore = cpu_baseline_all_cores(p)
+        line["cpu_baseline"]["all_cores"] = {
+            "value": va, "unit": "updates/s", "cores": nproc, "host_cores": ncore,
+            "sample": f"the same sample in {nproc} spawned one-thread processes at once "
+                      f"({dta:.1f} s)"}
+        vc, dtc = cpu_c1_full()
+        line["cpu_baseline"]["c1_full_run"] = {
+            "value": vc, "unit": "updates/s", "cores": 1,
+            "sample": f"the whole 32x32, 64-slice, 10-step FP64 run ({dtc:.1f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -427,10 +483,12 @@ def pair_beam(torch, stream, steps=6, depth=3):
             "status": st}
 
 
-def batched(steps, torch, stream):
+def batched(steps, torch, stream, hbm_peak):
     """The batched parameter scan (64 instances of uneven grids, qsa_advance_batch): 8 untimed
     steps (the first four time the FFT unit shapes), then `steps` timed steps of all
-    instances.  Same metric: plasma particle-slice updates of all instances per second."""
+    instances (8 + 42: the scan's 50).  Same metric: plasma particle-slice updates of all
+    instances per second.  Roofline of the batched launches: the algorithmic bytes of the
+    sweeps and pushes of their instances over the mean launch time (CUDA events)."""
     from paper_2607_24214_b300.qsa import QSA, advance_batch
     ps = config.c4_parameter_scan()
     qs = [QSA(pi) for pi in ps]
@@ -443,16 +501,67 @@ def batched(steps, torch, stream):
     t1.record(stream)
     t1.synchronize()
     ms = t0.elapsed_time(t1)
+    lt = qs[0].launch_times()   # the launches of the last call (up to 64)
     status = min(q.diagnostics()["status"] for q in qs)
     for q in qs:
         q.close()
     del qs
     torch.cuda.empty_cache()
     ups = sum(updates_per_step(pi) for pi in ps)
-    return {"workload": "c4_parameter_scan_64", "value": ups * steps / (ms * 1e-3),
-            "unit": "updates/s", "instances": len(ps), "steps": steps,
-            "ms_per_step": ms / steps, "grids": sorted({pi.nx for pi in ps}),
-            "status": status}
+    # launches per step: instances in groups of up to 16; the bytes of one step of all
+    # instances spread over those launches
+    per_step = (len(ps) + 15) // 16
+    step_bytes = sum(sweep_bytes(pi) + push_bytes(pi) for pi in ps)
+    out = {"workload": "c4_parameter_scan_64", "value": ups * steps / (ms * 1e-3),
+           "unit": "updates/s", "instances": len(ps), "steps": steps, "untimed_steps": 8,
+           "ms_per_step": ms / steps, "grids": sorted({pi.nx for pi in ps}),
+           "status": status}
+    if len(lt):
+        launch_ms = float(np.mean(lt))
+        achieved = step_bytes / per_step / (launch_ms * 1e-3) / 1e9
+        out["roofline"] = {"bound": "hbm", "kernel": "pipe_kernel (independent instances)",
+                           "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                           "frac": achieved / hbm_peak,
+                           "algorithmic_bytes_per_step": step_bytes,
+                           "launches_per_step": per_step, "launch_ms": launch_ms,
+                           "launches_timed": int(len(lt))}
+    return out
+
+
+def adjoint_cost(torch, stream, steps=None, ckpt=10):
+    """The seeded-mode workload (128 x 128, 256 slices, 16 modes, 50 beam steps): the forward
+    run as the library runs it (mixed precision, pipelined, one qsa_advance), the recorded
+    FP64 forward of the gradient (qsa_grad_forward) and its backward pass (qsa_grad_backward:
+    checkpoint segments recomputed and recorded, adjoint sweeps and beam pushes), wall times
+    with the device synchronised."""
+    from paper_2607_24214_b300.qsa import QSA
+    p = config.c5_seeded_modes()
+    steps = p.steps if steps is None else steps
+    q = QSA(p.with_(pipeline_depth=16))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    q.advance(steps)
+    q.sweep()
+    q.diagnostics()
+    t_mixed = time.perf_counter() - t
+    q.close()
+    q = QSA(p.with_(precision="fp64"))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    loss = q.grad_forward(steps, ckpt)
+    t_fwd = time.perf_counter() - t
+    t = time.perf_counter()
+    dm, da = q.grad_backward(1.0)
+    t_bwd = time.perf_counter() - t
+    q.close()
+    del q
+    torch.cuda.empty_cache()
+    return {"workload": "c5_seeded_modes_128x128_256slices_16modes", "steps": steps,
+            "step_checkpoints": ckpt, "loss": loss, "forward_mixed_s": t_mixed,
+            "forward_fp64_recorded_s": t_fwd, "backward_s": t_bwd,
+            "backward_over_forward_fp64": t_bwd / t_fwd,
+            "backward_over_forward_mixed": t_bwd / t_mixed,
+            "grad_alpha": float(da[0]), "grad_mode0": float(dm[0])}
 
 
 def e2e(p, steps, torch, stream):
