@@ -123,6 +123,19 @@ def c3_pair_beam(ppc_xi: int = 1) -> Params:
                   precision="mixed", steps=400)
 
 
+def pair_beam_filaments() -> Params:
+    """Pair beam driven far into its nonlinear stage at moderate cost: 256 x 256 (box 16 pi),
+    1024 slices over 64, electrons and positrons of alpha 1e-3 each, gamma_b 1e3, 1e-3 weight
+    noise, 8 ppc; dt 20, 1000 steps.  Gamma = 1e-3 at k_y = k_p, so Gamma tau reaches 20: past
+    saturation, into the stage of current filaments at the front whose wakes the blazar
+    paragraph estimates.  Mixed precision."""
+    L = 256 * DX_DEFAULT
+    sp = dict(alpha=1e-3, gamma_b=1e3, noise_rel=1e-3)
+    return Params(nx=256, ny=256, nxi=1024, Lx=L, Ly=L, Lxi=64.0, dt=20.0,
+                  species=[Species(Z=-1, M=1, **sp), Species(Z=+1, M=1, **sp)],
+                  precision="mixed", steps=1000)
+
+
 def c4_parameter_scan(n: int = 64, seed: int = 0) -> List[Params]:
     """Batched scan: n independent instances, transverse grids drawn uniformly from
     {64, 96, 128, 192, 256}^2 (box N 2 pi / 32), 256 slices over 32, 4 ppc plasma; cold

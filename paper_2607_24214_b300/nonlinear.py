@@ -155,13 +155,17 @@ def filament_sizes(rho, dx, dy, dxi):
 FIELD_NAMES = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")  # order of the rms columns of qsa_diag
 
 
-def run(p: config.Params, steps: int, every: int, seg_width: float = 2.0, log=None) -> dict:
+def run(p: config.Params, steps: int, every: int, seg_width: float = 2.0, log=None,
+        read=None, read_every: int = 0) -> dict:
     """Advance a fresh handle of `p` by `steps` beam steps, `every` at a time (one pipelined
     call each), and record after each call the diagnostics of its last sweep.  That sweep saw
-    the beam after (sweeps - 1) pushes, so its time is tau = (sweeps - 1) dt."""
+    the beam after (sweeps - 1) pushes, so its time is tau = (sweeps - 1) dt.  With `read`
+    (a function of the handle, p and the diagnostics), its result is recorded after every
+    read_every-th call and after the last, under "reads" with their times "read_tau"."""
     from .qsa import QSA
     q = QSA(p)
     rec = {k: [] for k in ("tau", "rms_seg", "energy", "beam_rms_seg", "beam_lost", "ms")}
+    reads, read_tau, calls = [], [], 0
     nseg = int(math.ceil(p.Lxi / seg_width - 1e-12))
     cell_seg = np.minimum((np.arange(p.nxi) * p.dxi / seg_width + 1e-12).astype(int), nseg - 1)
     done = 0
@@ -186,6 +190,12 @@ def run(p: config.Params, steps: int, every: int, seg_width: float = 2.0, log=No
         rec["beam_rms_seg"].append(bseg)
         rec["beam_lost"].append(d["beam_lost"])
         rec["ms"].append(ms)
+        calls += 1
+        if read is not None and ((read_every and calls % read_every == 0) or done >= steps):
+            reads.append(read(q, p, d))
+            read_tau.append(rec["tau"][-1])
+            if log:
+                log(f"  read at tau {read_tau[-1]:.0f}: {json.dumps(reads[-1])}")
         if log:
             r = d["rms_seg"]
             log(f"step {done}/{steps} tau {rec['tau'][-1]:.0f}  rms B_perp(xi=2) "
@@ -194,6 +204,9 @@ def run(p: config.Params, steps: int, every: int, seg_width: float = 2.0, log=No
     q.close()
     out = {k: np.asarray(v) for k, v in rec.items()}
     out["seg_width"] = np.float64(seg_width)
+    if read is not None:
+        out["reads"] = reads
+        out["read_tau"] = np.asarray(read_tau)
     return out
 
 
@@ -248,17 +261,66 @@ def summary(rec: dict, p: config.Params, k_ref: float = 1.0) -> dict:
     return out
 
 
+def filament_reading(q, p: config.Params, d: dict, front: float = 10.0,
+                     downstream=(12.0, 40.0)) -> dict:
+    """The filaments of the beam front and their wakes, read from handle q after a run (d: its
+    diagnostics).  The beam charge density rho_b = S_b + J_z (both species) on the slab nodes
+    of xi < front gives filament_sizes; the filament charge density is read as the mean |rho_b
+    - <rho_b>| over the cells where it exceeds half its maximum (the filament cores).  The
+    wake estimate ex_wake_amplitude(rho_fil, length, width/2) (w read as the half-width of a
+    filament of full width `width`) stands beside the measured E_z (the paper's E_x) downstream:
+    sqrt 2 times its rms over the slices of `downstream` (the amplitude of a wave of that rms)."""
+    n = int(round(front / p.dxi))
+    rho = q.source("Sb", 0, n) + q.source("Jz", 0, n)
+    sz = filament_sizes(rho, p.dx, p.dy, p.dxi)
+    dev = np.abs(rho - rho.mean(axis=(1, 2), keepdims=True))
+    core = dev > 0.5 * dev.max()
+    rho_fil = float(dev[core].mean())
+    est = float(ex_wake_amplitude(rho_fil, sz["length"], 0.5 * sz["width"]))
+    xi = np.arange(p.nxi + 1) * p.dxi
+    sel = (xi >= downstream[0]) & (xi < downstream[1])
+    ez_amp = float(np.sqrt(2.0 * np.mean(d["rms"][sel, 2] ** 2)))
+    return dict(sz, rho_fil=rho_fil, ex_wake_estimate=est, ez_downstream_amplitude=ez_amp,
+                ratio=ez_amp / est if est > 0 else float("nan"))
+
+
+def dpx_reading(rec: dict, p: config.Params, rho_fil: float, seg=(12.0, 40.0),
+                last: float = 0.3) -> dict:
+    """Growth of the beam's longitudinal momentum spread downstream over the last fraction
+    `last` of the run (rms u_z of the first species over the segments of `seg`, averaged),
+    as d(rms u_z)/d tau, beside |rho_fil| (the blazar paragraph's Delta p_x ~ |rho_b| tau)."""
+    w = float(rec["seg_width"])
+    s0, s1 = int(seg[0] / w), int(seg[1] / w)
+    uz = rec["beam_rms_seg"][:, 0, s0:s1, 2].mean(axis=1)
+    tau = rec["tau"]
+    sel = tau >= tau[-1] * (1.0 - last)
+    slope = float(np.polyfit(tau[sel], uz[sel], 1)[0]) if sel.sum() >= 3 else float("nan")
+    return {"duz_dtau": slope, "rho_fil": rho_fil, "ratio": slope / rho_fil if rho_fil else None}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--workload", default="c3", choices=["c3", "filaments"],
+                    help="c3: the 512^2 pair beam (400 steps); filaments: the 256^2 pair beam "
+                         "driven to Gamma tau = 20, with the filament and wake reading")
+    ap.add_argument("--steps", type=int, default=0, help="beam steps (0: the workload's)")
     ap.add_argument("--every", type=int, default=6)
     ap.add_argument("--depth", type=int, default=3, help="beam steps in flight per launch")
-    ap.add_argument("--out", default="nonlinear_c3.npz")
+    ap.add_argument("--read-every", type=int, default=10)
+    ap.add_argument("--out", default="nonlinear_run.npz")
     a = ap.parse_args()
-    p = config.c3_pair_beam().with_(pipeline_depth=a.depth)
-    rec = run(p, a.steps, a.every, log=lambda s: print(s, flush=True))
-    np.savez_compressed(a.out, **rec)
-    print(json.dumps(summary(rec, p)), flush=True)
+    p = (config.c3_pair_beam() if a.workload == "c3" else
+         config.pair_beam_filaments()).with_(pipeline_depth=a.depth)
+    steps = a.steps or p.steps
+    read = filament_reading if a.workload == "filaments" else None
+    rec = run(p, steps, a.every, log=lambda s: print(s, flush=True), read=read,
+              read_every=a.read_every)
+    np.savez_compressed(a.out, **{k: v for k, v in rec.items() if k != "reads"})
+    out = summary(rec, p)
+    if read is not None:
+        out["filaments"] = {"tau": rec["read_tau"].tolist(), "reads": rec["reads"]}
+        out["dpx"] = dpx_reading(rec, p, rec["reads"][-1]["rho_fil"])
+    print(json.dumps(out), flush=True)
 
 
 if __name__ == "__main__":
