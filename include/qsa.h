@@ -102,6 +102,13 @@ typedef struct {
                               ||B_perp(n) - B_perp(n-1)|| / ||B_perp(n)|| (2-norms over the
                               grid) is below pc_tol, after n_pc_iter solves at most; the
                               count per slice is reported in qsa_diag.pc_iters */
+  double rehome_frac;      /* qsa_advance with pipeline_depth >= 2: before a persistent launch,
+                              when more than this fraction of the beam sat outside its storage
+                              slots' cells after the previous launch's pushes, re-home the beam
+                              (move each particle into a slot of the cell it occupies, within
+                              its xi layer; each keeps its identity for qsa_get_beam).  The
+                              sources and fields are unchanged up to the order of the sums.
+                              0: never.  Storage only, not part of the method. */
 } qsa_params;
 
 /* Allocator callbacks: alloc returns a device pointer (NULL on failure) of at least `bytes`
@@ -311,6 +318,15 @@ int qsa_field_solve_static(int32_t nx, int32_t ny, double Lx, double Ly, double 
                            int32_t precision, const void* S, const void* Jx, const void* Jy,
                            const void* Jz, const void* Dx, const void* Dy, void* out,
                            void* stream);
+
+/* Storage only (the paper has no counterpart): re-home the beam now, moving every particle
+ * into a storage slot of the cell it occupies within its xi layer (the ones of a crowded
+ * cell fill free slots of other cells, in row-major order), each keeping its identity for
+ * qsa_get_beam.  Sources and fields are unchanged up to the order of the sums.  qsa_advance
+ * does it by itself when rehome_frac says so.  Uses about 1 GB of staging memory, allocated
+ * on first use.  Asynchronous.  qsa_rehome_count: re-homings done by the handle. */
+int qsa_rehome(qsa_handle* h);
+int64_t qsa_rehome_count(const qsa_handle* h);
 
 /* ---------------------------------------------------------------------------------------
  * Gradients of a run with respect to the seeded mode amplitudes and the beam density ratio

@@ -68,6 +68,7 @@ class Params:
     seed: int = 0
     spin_limit: int = 1 << 26
     pipeline_depth: int = 1          # beam steps in flight per qsa_advance launch (1: none)
+    rehome_frac: float = 0.0         # pipelined: re-home the beam when this fraction left its slots
     diag_modes: List[Tuple[int, int]] = field(default_factory=list)  # (mx, my) recorded per slice
     steps: int = 1                   # beam steps of the named workload (not part of the C struct)
 

@@ -17,6 +17,7 @@
 #include "qsa_sweep.cuh"
 #include "qsa_tables.h"
 #include "qsa_adjoint.cuh"
+#include "qsa_rehome.cuh"
 
 using namespace qsa;
 
@@ -64,6 +65,8 @@ struct qsa_handle {
   // the run recorded by qsa_grad_forward for qsa_grad_backward (null: none)
   struct GradRun* grad = nullptr;
   bool beam_replaced = false;  // qsa_set_beam replaced the beam qsa_init built
+  int64_t rehomes = 0;         // re-homings of the beam done (qsa_rehome, qsa_advance)
+  int last_pushes = 0;         // pushes of the last pipelined launch
 };
 
 // State of a differentiable run between qsa_grad_forward and qsa_grad_backward.
@@ -153,6 +156,13 @@ struct State {
   PipeTable<R>* ptab = nullptr;     // device table of the multi-slot launches (lazy)
   int tuned_nbr = 0, tuned_nbc = 0; // FFT units chosen by the batch autotuner (0: not yet)
   unsigned long long* lost = nullptr;
+  unsigned long long* away = nullptr;  // beam particles outside their slots' cells (pipelined)
+  // re-homing buffers (lazy): cell keys of a chunk of layers, per-cell counts, prefix sums and
+  // cursors, per-layer cursors of the lost particles, and staging arrays of the chunk
+  int rh_layers = 0;
+  int *rh_key = nullptr, *rh_cnt = nullptr, *rh_exc = nullptr, *rh_vac = nullptr,
+      *rh_cur = nullptr, *rh_dead = nullptr;
+  BeamArrays<R> rh_t{};
   unsigned* bar = nullptr;  // [0] count, [1] generation
   int* status = nullptr;
   C<R>* tw = nullptr;
@@ -224,9 +234,10 @@ int setup(qsa_handle* h) {
   unsigned* bar = (unsigned*)A(2 * sizeof(unsigned));
   int* status = (int*)A(sizeof(int));
   s->lost = (unsigned long long*)A(sizeof(unsigned long long));
+  s->away = (unsigned long long*)A(sizeof(unsigned long long));
   s->dmin = (int*)A(sizeof(int));
   s->chk = (int*)A(sizeof(int));
-  if (!ktab || !twp || !bref || !bar || !status || !s->lost || !s->dmin || !s->chk)
+  if (!ktab || !twp || !bref || !bar || !status || !s->lost || !s->dmin || !s->chk || !s->away)
     return fail(h, QSA_ERR_OOM, "sweep tables");
   {
     const std::vector<R> kt = wavenumber_table<R>(dp.nx, dp.ny, dp.Lx, dp.Ly);
@@ -349,7 +360,8 @@ int setup(qsa_handle* h) {
     if (!(b.ox = (R*)A(n * sizeof(R))) || !(b.oy = (R*)A(n * sizeof(R))) ||
         !(b.oxi = (R*)A(n * sizeof(R))) || !(b.ux = (R*)A(n * sizeof(R))) ||
         !(b.uy = (R*)A(n * sizeof(R))) || !(b.dw = (R*)A(n * sizeof(R))) ||
-        !(b.uz = (typename UzT<R>::T*)A(n * sizeof(typename UzT<R>::T))))
+        !(b.uz = (typename UzT<R>::T*)A(n * sizeof(typename UzT<R>::T))) ||
+        !(b.id = (unsigned*)A(n * sizeof(unsigned))))
       return fail(h, QSA_ERR_OOM, "beam arrays");
     s->species.push_back(sp);
     s->bconst.push_back(beam_consts<R>(dp, sp));
@@ -398,7 +410,7 @@ int deposit_sources(qsa_handle* h) {
     const unsigned groups = (unsigned)(s->species[si].nkb * dp.ny);
     beam_kernel<R, false><<<groups, kThreads, beam_smem_bytes<R>(dp.nx), h->stream>>>(
         b, dp, s->species[si], s->bconst[si], nullptr, src, nullptr,
-        Extent{cmax, s->dmin, mom + si * (size_t)dp.nxi * 7});
+        Extent{cmax, s->dmin, mom + si * (size_t)dp.nxi * 7, nullptr});
     ++h->launches;
     CK(cudaGetLastError());
   }
@@ -489,6 +501,7 @@ PipeSlot<R> make_slot(qsa_handle* h, int64_t pushes) {
   ps.mom_out = ring_mom<R>(h, pushes + 1);
   ps.dmin = s->dmin;
   ps.lost = s->lost;
+  ps.away = s->away;
   ps.nspecies = (int)s->species.size();
   for (int si = 0; si < ps.nspecies; ++si) {
     ps.beam[si] = s->beams[si];
@@ -569,6 +582,78 @@ int launch_slots(qsa_handle* lead, PipeTable<R>& t, int nslots, int nbr, int nbc
 #endif
 constexpr int kPipeRowBatch = QSA_PIPE_ROW_BATCH, kPipeColBatch = QSA_PIPE_COL_BATCH;
 
+// Re-home every species' beam (see qsa_rehome.cuh), a chunk of xi layers at a time.
+template <typename R>
+int rehome(qsa_handle* h) {
+  State<R>* s = S<R>(h);
+  const DevParams& dp = h->dp;
+  const int ncell = dp.nx * dp.ny;
+  int ppc_max = 1, nkb_max = 1;
+  for (const auto& sp : s->species) {
+    ppc_max = std::max(ppc_max, sp.ppc);
+    nkb_max = std::max(nkb_max, sp.nkb);
+  }
+  const size_t L = (size_t)ncell * ppc_max;
+  const size_t rec = 6 * sizeof(R) + sizeof(typename UzT<R>::T) + sizeof(unsigned) + sizeof(int);
+  if (!s->rh_layers) {
+    // staging of about 1 GB (at least one layer)
+    const int nl = (int)std::max<size_t>(1, std::min<size_t>(nkb_max, (size_t(1) << 30) / (L * rec)));
+    auto A = [&](size_t bytes) { return dalloc(h, bytes); };
+    BeamArrays<R>& t = s->rh_t;
+    const size_t m = (size_t)nl * L;
+    if (!(s->rh_key = (int*)A(m * sizeof(int))) ||
+        !(s->rh_cnt = (int*)A((size_t)nl * ncell * sizeof(int))) ||
+        !(s->rh_exc = (int*)A((size_t)nl * ncell * sizeof(int))) ||
+        !(s->rh_vac = (int*)A((size_t)nl * ncell * sizeof(int))) ||
+        !(s->rh_cur = (int*)A((size_t)nl * ncell * sizeof(int))) ||
+        !(s->rh_dead = (int*)A((size_t)nl * sizeof(int))) || !(t.ox = (R*)A(m * sizeof(R))) ||
+        !(t.oy = (R*)A(m * sizeof(R))) || !(t.oxi = (R*)A(m * sizeof(R))) ||
+        !(t.ux = (R*)A(m * sizeof(R))) || !(t.uy = (R*)A(m * sizeof(R))) ||
+        !(t.dw = (R*)A(m * sizeof(R))) ||
+        !(t.uz = (typename UzT<R>::T*)A(m * sizeof(typename UzT<R>::T))) ||
+        !(t.id = (unsigned*)A(m * sizeof(unsigned))))
+      return fail(h, QSA_ERR_OOM, "re-homing buffers");
+    s->rh_layers = nl;
+  }
+  for (size_t si = 0; si < s->beams.size(); ++si) {
+    const BeamArrays<R>& b = s->beams[si];
+    const SpeciesDev& sp = s->species[si];
+    if (b.n == 0) continue;
+    const long long Ls = (long long)ncell * sp.ppc;
+    for (int k0 = 0; k0 < sp.nkb; k0 += s->rh_layers) {
+      const int nl = std::min(s->rh_layers, sp.nkb - k0);
+      const long long m = (long long)nl * Ls;
+      const unsigned blocks = (unsigned)((m + kThreads - 1) / kThreads);
+      CK(cudaMemsetAsync(s->rh_cnt, 0, (size_t)nl * ncell * sizeof(int), h->stream));
+      CK(cudaMemsetAsync(s->rh_dead, 0, (size_t)nl * sizeof(int), h->stream));
+      rehome_count_kernel<R><<<blocks, kThreads, 0, h->stream>>>(b, dp, sp, k0, nl, s->rh_key,
+                                                                  s->rh_cnt);
+      rehome_scan_kernel<<<nl, kRehomeThreads, 0, h->stream>>>(dp, sp.ppc, s->rh_cnt, s->rh_exc,
+                                                               s->rh_vac, s->rh_cur);
+      rehome_scatter_kernel<R><<<blocks, kThreads, 0, h->stream>>>(
+          b, s->rh_t, dp, sp, k0, nl, s->rh_key, s->rh_cnt, s->rh_exc, s->rh_vac, s->rh_cur,
+          s->rh_dead);
+      h->launches += 3;
+      CK(cudaGetLastError());
+      const size_t off = (size_t)k0 * Ls;
+      const BeamArrays<R>& t = s->rh_t;
+      CK(cudaMemcpyAsync(b.ox + off, t.ox, m * sizeof(R), cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(b.oy + off, t.oy, m * sizeof(R), cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(b.oxi + off, t.oxi, m * sizeof(R), cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(b.ux + off, t.ux, m * sizeof(R), cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(b.uy + off, t.uy, m * sizeof(R), cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(b.dw + off, t.dw, m * sizeof(R), cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(b.uz + off, t.uz, m * sizeof(typename UzT<R>::T),
+                         cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(b.id + off, t.id, m * sizeof(unsigned), cudaMemcpyDeviceToDevice,
+                         h->stream));
+    }
+  }
+  ++h->rehomes;
+  h->last_pushes = 0;  // the away count no longer describes the beam
+  return QSA_OK;
+}
+
 // n beam steps (sweep + push each) as wavefronts of up to S steps per persistent launch.
 template <typename R>
 int advance_pipelined(qsa_handle* h, int n) {
@@ -581,8 +666,21 @@ int advance_pipelined(qsa_handle* h, int n) {
   }
   std::vector<PipeTable<R>> tv(1);  // ~30 KB: on the heap
   PipeTable<R>& t = tv[0];
+  int64_t nbeam = 0;
+  for (const auto& b : s->beams) nbeam += b.n;
   while (n > 0) {
     const int m = n < nslot ? n : nslot;
+    // the away counter holds the pushes of the last pipelined launch (last_pushes of them)
+    if (h->last_pushes > 0 && h->prm.rehome_frac > 0.0 && nbeam > 0) {
+      unsigned long long away = 0;
+      CK(cudaMemcpyAsync(&away, s->away, sizeof(away), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      // each of the last launch's pushes counted its particles that left their slots' cells
+      if ((double)away > h->prm.rehome_frac * (double)nbeam * h->last_pushes)
+        if (int rc = rehome<R>(h)) return rc;
+    }
+    CK(cudaMemsetAsync(s->away, 0, sizeof(unsigned long long), h->stream));
+    h->last_pushes = m;
     t = PipeTable<R>{};
     t.chained = 1;
     for (int i = 0; i < m; ++i) {
@@ -700,7 +798,7 @@ int beam_step(qsa_handle* h) {
     const unsigned groups = (unsigned)(s->species[si].nkb * dp.ny);
     beam_kernel<R, true><<<groups, kThreads, beam_smem_bytes<R>(dp.nx), h->stream>>>(
         b, dp, s->species[si], s->bconst[si], slab, src, s->lost,
-        Extent{cmax, nullptr, mom + si * (size_t)dp.nxi * 7});
+        Extent{cmax, nullptr, mom + si * (size_t)dp.nxi * 7, nullptr});
     ++h->launches;
     CK(cudaGetLastError());
   }
@@ -841,6 +939,7 @@ int beam_io(qsa_handle* h, int si, bool to_host, int64_t n, const double* const*
       rc = fail(h, QSA_ERR_ARG, "xi of a live particle outside [0, Lxi)");
     } else {
       h->beam_replaced = true;
+      h->last_pushes = 0;
       beam_from_host_kernel<R><<<blocks, kThreads, 0, h->stream>>>(
           b, h->dp, s->species[si], (double*)tmp[0], (double*)tmp[1], (double*)tmp[2],
           (double*)tmp[3], (double*)tmp[4], (double*)tmp[5], (double*)tmp[6]);
@@ -1270,6 +1369,7 @@ int validate(const qsa_params* p, std::string& why) {
   if (p->precision != QSA_FP64 && p->precision != QSA_MIXED) return bad("unknown precision");
   if (p->n_pc_iter < 1 || p->n_pc_iter > 64) return bad("n_pc_iter must be in 1..64");
   if (!(p->pc_tol >= 0.0 && p->pc_tol <= 1e100)) return bad("pc_tol must be finite and >= 0");
+  if (!(p->rehome_frac >= 0.0 && p->rehome_frac <= 1.0)) return bad("rehome_frac must be in [0, 1]");
   if (!(p->psi_floor > 0 && p->psi_floor < 1)) return bad("psi_floor must be in (0, 1)");
   if (p->spin_limit < 0) return bad("spin_limit must be >= 0");
   if (p->pipeline_depth < 0 || p->pipeline_depth > kMaxPipe)
@@ -1504,6 +1604,14 @@ int qsa_field_solve(qsa_handle* h, const double* S_, const double* Jx, const dou
   const double* in[6] = {S_, Jx, Jy, Jz, Dx, Dy};
   return h->fp64 ? field_solve<double>(h, in, kappa2, out) : field_solve<float>(h, in, kappa2, out);
 }
+
+int qsa_rehome(qsa_handle* h) {
+  NvtxRange nvtx_range("qsa_rehome");
+  if (!h) return QSA_ERR_ARG;
+  return h->fp64 ? rehome<double>(h) : rehome<float>(h);
+}
+
+int64_t qsa_rehome_count(const qsa_handle* h) { return h ? h->rehomes : 0; }
 
 int qsa_grad_forward(qsa_handle* h, int32_t n_steps, int32_t step_ckpt, double* loss_out) {
   NvtxRange nvtx_range("qsa_grad_forward");

@@ -41,10 +41,13 @@ __host__ __device__ __forceinline__ void uz_store(float2& d, double v) {
 __device__ __forceinline__ double uz_lead(double v) { return v; }
 __device__ __forceinline__ float uz_lead(float2 v) { return v.x; }
 
+// id[s]: the canonical id of the particle slot s holds (the slot's own id until the beam is
+// re-homed, see rehome_*), so that host copies keep every particle's identity.
 template <typename BR>
 struct BeamArrays {
   BR *ox, *oy, *oxi, *ux, *uy, *dw;
   typename UzT<BR>::T* uz;
+  unsigned* id;
   long long n;
 };
 
@@ -154,6 +157,7 @@ __global__ void beam_init_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp, M
   b.uy[s] = BR(uy);
   uz_store(b.uz[s], sqrt(gam * gam - 1.0 - ux * ux - uy * uy));
   b.dw[s] = BR(dw);
+  b.id[s] = (unsigned)h.id;
 }
 
 // ------------------------------------------------------------------ deposit and push
@@ -489,6 +493,7 @@ struct Extent {
   int* cmax;
   int* dmin;
   double* mom;  // [nxi][7] beam moments of the species per xi cell (see qsa_diag), or null
+  unsigned long long* away;  // live particles outside their slot's cell after the push, or null
 };
 
 // u_z - sqrt(gamma_b^2 - 1) without cancellation of the leading parts
@@ -535,7 +540,7 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
   const BR hdt = bc.hdt;
   const BR cdx = bc.cdx, cdy = bc.cdy, cdk = bc.cdk;
   const int kleft = p.nxi - g.kabs;  // lost when the local xi position reaches this
-  int my_lost = 0;
+  int my_lost = 0, my_away = 0;
   // two sub-lattice positions per thread per pass: particles (sub0, ix) and (sub0 + 1, ix);
   // the loads and gathers of both are issued before either particle's arithmetic
   for (int sub0 = 0; sub0 < sp.ppc; sub0 += 2) {
@@ -653,6 +658,8 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
         doy[u] = oy[u];
         doxi[u] = oxi[u];
         post_home = post_home && in_cell(hx[u] + ox[u], hy[u] + oy[u], hk[u] + oxi[u]);
+        // away from the slot's cell transversely (what re-homing within the layer can mend)
+        my_away += in_cell(hx[u] + ox[u], hy[u] + oy[u], BR(0)) ? 0 : 1;
       }
       if (lane_agg && __all_sync(0xffffffffu, post_home)) {
         // every particle of the warp's two sub-lattice positions is in its home cell: the two
@@ -771,6 +778,10 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
     }
   }
   if (my_lost && lost) atomicAdd(lost, (unsigned long long)my_lost);
+  if (ext.away) {
+    my_away = warp_sum(my_away);
+    if ((threadIdx.x & 31) == 0 && my_away) atomicAdd(ext.away, (unsigned long long)my_away);
+  }
   __syncthreads();  // the tile and s_ext are reused by the block's next group
 }
 
@@ -815,6 +826,7 @@ __global__ void beam_from_host_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev 
   b.uy[s] = BR(uy[id]);
   uz_store(b.uz[s], uz[id]);
   b.dw[s] = (w[id] == 0.0) ? BR(-1) : BR(w[id] / sp.wbar - 1.0);
+  b.id[s] = (unsigned)id;
 }
 
 template <typename BR>
@@ -824,7 +836,7 @@ __global__ void beam_to_host_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp
   const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= b.n) return;
   const Home h = home_of(s, p.nx, p.ny, sp);
-  const long long id = h.id;
+  const long long id = b.id[s];  // the particle in slot s (slot s's own id unless re-homed)
   const double hx = h.ix + (h.sx + 0.5) / sp.ppx, hy = h.iy + (h.sy + 0.5) / sp.ppy;
   const double hk = sp.k0 + h.kxi + (h.sxi + 0.5) / sp.ppxi;
   double xx = (hx + (double)b.ox[s]) * p.dx, yy = (hy + (double)b.oy[s]) * p.dy;

@@ -56,6 +56,7 @@ struct PipeSlot {
   double* mom_out;      // [nspecies][nxi][7]
   const int* dmin;      // min over live particles of (xi cell - home layer), <= 0
   unsigned long long* lost;
+  unsigned long long* away;  // live particles outside their slots' cells after the pushes
   int nspecies;
   BeamArrays<R> beam[kMaxSpecies];
   SpeciesDev sp[kMaxSpecies];
@@ -299,7 +300,8 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
           for (int q = unit0(base, G); q < p.ny; q += G)
             beam_group<R, true>(ps.beam[si], p, sp, ps.bc[si], sa[s].slab, ps.src_next,
                                 ps.lost,
-                                Extent{ps.cmax_out, nullptr, ps.mom_out + (size_t)si * p.nxi * 7},
+                                Extent{ps.cmax_out, nullptr, ps.mom_out + (size_t)si * p.nxi * 7,
+                                       ps.away},
                                 (c - sp.k0) * p.ny + q, tile);
           base += p.ny;
         }

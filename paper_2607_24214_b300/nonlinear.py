@@ -288,14 +288,17 @@ def dpx_reading(rec: dict, p: config.Params, rho_fil: float, seg=(12.0, 40.0),
                 last: float = 0.3) -> dict:
     """Growth of the beam's longitudinal momentum spread downstream over the last fraction
     `last` of the run (rms u_z of the first species over the segments of `seg`, averaged),
-    as d(rms u_z)/d tau, beside |rho_fil| (the blazar paragraph's Delta p_x ~ |rho_b| tau)."""
+    as d(rms u_z)/d tau, beside the blazar paragraph's Delta p_x ~ |rho_b| tau: against one
+    species' mean beam density alpha, and against the filament charge density rho_fil."""
     w = float(rec["seg_width"])
     s0, s1 = int(seg[0] / w), int(seg[1] / w)
     uz = rec["beam_rms_seg"][:, 0, s0:s1, 2].mean(axis=1)
     tau = rec["tau"]
     sel = tau >= tau[-1] * (1.0 - last)
     slope = float(np.polyfit(tau[sel], uz[sel], 1)[0]) if sel.sum() >= 3 else float("nan")
-    return {"duz_dtau": slope, "rho_fil": rho_fil, "ratio": slope / rho_fil if rho_fil else None}
+    alpha = p.species[0].alpha
+    return {"duz_dtau": slope, "alpha": alpha, "ratio_alpha": slope / alpha,
+            "rho_fil": rho_fil, "ratio_fil": slope / rho_fil if rho_fil else None}
 
 
 def main():

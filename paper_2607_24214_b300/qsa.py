@@ -35,7 +35,7 @@ EXPORTS = ("qsa_init", "qsa_set_beam", "qsa_get_beam", "qsa_plasma_sweep", "qsa_
            "qsa_phase_times", "qsa_launch_count", "qsa_device_bytes", "qsa_last_error",
            "qsa_destroy", "qsa_field_solve_static", "qsa_advance", "qsa_launch_times",
            "qsa_eq5_march", "qsa_advance_batch", "qsa_bounds_check", "qsa_grad_forward",
-           "qsa_grad_backward")
+           "qsa_grad_backward", "qsa_rehome", "qsa_rehome_count")
 
 
 class QsaError(RuntimeError):
@@ -70,7 +70,7 @@ class ParamsC(ct.Structure):
                 ("dt", ct.c_double), ("psi_floor", ct.c_double), ("seed", ct.c_uint64),
                 ("spin_limit", ct.c_int64), ("species", Species * 4), ("modes", Mode * 16),
                 ("n_diag_modes", ct.c_int32), ("_pad", ct.c_int32), ("diag_modes", KVec * 16),
-                ("pc_tol", ct.c_double)]
+                ("pc_tol", ct.c_double), ("rehome_frac", ct.c_double)]
 
 
 _DP = ct.POINTER(ct.c_double)
@@ -120,6 +120,10 @@ def load_library(path: str = None):
     lib.qsa_advance_batch.restype = ct.c_int
     lib.qsa_bounds_check.argtypes = [ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int64)]
     lib.qsa_bounds_check.restype = ct.c_int
+    lib.qsa_rehome.argtypes = [P]
+    lib.qsa_rehome.restype = ct.c_int
+    lib.qsa_rehome_count.argtypes = [P]
+    lib.qsa_rehome_count.restype = ct.c_int64
     lib.qsa_grad_forward.argtypes = [P, ct.c_int32, ct.c_int32, _DP]
     lib.qsa_grad_forward.restype = ct.c_int
     lib.qsa_grad_backward.argtypes = [P, ct.c_double, _DP, _DP]
@@ -164,6 +168,7 @@ def to_c_params(p: config.Params) -> ParamsC:
     c.precision = 0 if p.precision == "fp64" else 1
     c.n_pc_iter = p.n_pc_iter
     c.pc_tol = p.pc_tol
+    c.rehome_frac = p.rehome_frac
     c.pipeline_depth = p.pipeline_depth
     c.Lx, c.Ly, c.Lxi, c.dt = p.Lx, p.Ly, p.Lxi, p.dt
     c.psi_floor = p.psi_floor
@@ -295,6 +300,13 @@ class QSA:
     def advance(self, n_steps: int):
         """n_steps x (sweep, beam step); pipelined launches when p.pipeline_depth >= 2."""
         return self._check(self.lib.qsa_advance(self.h, int(n_steps)))
+
+    def rehome(self):
+        """Move every beam particle into a storage slot of the cell it occupies (qsa_rehome)."""
+        return self._check(self.lib.qsa_rehome(self.h))
+
+    def rehome_count(self) -> int:
+        return int(self.lib.qsa_rehome_count(self.h))
 
     def launch_times(self) -> np.ndarray:
         """Device ms of each persistent launch of the last pipelined advance()."""

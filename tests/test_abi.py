@@ -40,11 +40,12 @@ def test_struct_layout_matches_c():
 #include <stddef.h>
 #include "qsa.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(qsa_params),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(qsa_params),
          sizeof(qsa_species), sizeof(qsa_mode), sizeof(qsa_diag), offsetof(qsa_params, species),
          offsetof(qsa_params, modes), offsetof(qsa_params, diag_modes),
          offsetof(qsa_params, pc_tol), offsetof(qsa_diag, seg_width),
-         offsetof(qsa_diag, beam_moments), offsetof(qsa_diag, pc_iters));
+         offsetof(qsa_diag, beam_moments), offsetof(qsa_diag, pc_iters),
+         offsetof(qsa_params, rehome_frac));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -56,7 +57,8 @@ int main(void) {
     want = [ct.sizeof(qsa.ParamsC), ct.sizeof(qsa.Species), ct.sizeof(qsa.Mode),
             ct.sizeof(qsa.Diag), qsa.ParamsC.species.offset, qsa.ParamsC.modes.offset,
             qsa.ParamsC.diag_modes.offset, qsa.ParamsC.pc_tol.offset, qsa.Diag.seg_width.offset,
-            qsa.Diag.beam_moments.offset, qsa.Diag.pc_iters.offset]
+            qsa.Diag.beam_moments.offset, qsa.Diag.pc_iters.offset,
+            qsa.ParamsC.rehome_frac.offset]
     assert got == want
 
 

@@ -151,3 +151,51 @@ def test_advance_zero_steps_and_sequential_depth(Q):
     assert q.diagnostics()["sweeps"] == 0
     # depth 1: advance is the sequential loop
     compare(Q, p, beams, 3, 1, 1e-12)
+
+
+def scattered(p, seed=4):
+    """The C1-like beam with every particle moved up to 6 cells from its lattice home in x
+    and y (cells end up with uneven counts, some above the ppc slots a cell has), and 1 % of
+    the particles marked lost."""
+    rng = np.random.default_rng(seed)
+    beams = inputs.all_beams(p)
+    for b in beams:
+        m = b["x"].size
+        b["x"] = np.mod(b["x"] + rng.uniform(-6, 6, m) * p.dx, p.Lx)
+        b["y"] = np.mod(b["y"] + rng.uniform(-6, 6, m) * p.dy, p.Ly)
+        b["ux"] = b["ux"] + rng.normal(0, 0.05, m)
+        b["w"][rng.random(m) < 0.01] = 0.0
+    return beams
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_rehome_keeps_every_particle_and_the_fields(Q, prec):
+    """Re-homing moves particles between storage slots only: the host copy of the beam (each
+    particle by its id) and the next sweep's fields are unchanged, to rounding."""
+    p = config.c1_fp64_electron_beam().with_(nxi=24, Lxi=3.0, precision=prec)
+    beams = scattered(p)
+    a, b = make(Q, p, beams), make(Q, p, beams)
+    n = beams[0]["x"].size
+    before = b.get_beam(0, n)
+    b.rehome()
+    assert b.rehome_count() == 1
+    after = b.get_beam(0, n)
+    np.testing.assert_array_equal(before["w"], after["w"])
+    ptol = 1e-12 if prec == "fp64" else 1e-6
+    for key, L in (("x", p.Lx), ("y", p.Ly)):
+        e = np.mod(after[key] - before[key] + 0.5 * L, L) - 0.5 * L
+        assert np.abs(e).max() <= ptol * L, key
+    for key in ("xi", "ux", "uy", "uz"):
+        assert np.abs(after[key] - before[key]).max() <= ptol * np.abs(before[key]).max(), key
+    a.sweep()
+    b.sweep()
+    assert field_err(b.slab(), a.slab()).max() <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_pipelined_run_rehomes_and_matches_sequential(Q, prec):
+    """A pipelined run whose particles sit away from their homes re-homes the beam before
+    its second launch (rehome_frac) and still matches the steps run one after the other."""
+    p = config.c1_fp64_electron_beam().with_(nxi=24, Lxi=3.0, precision=prec, rehome_frac=0.05)
+    a, b = compare(Q, p, scattered(p), 4, 2, TOL[prec])
+    assert b.rehome_count() >= 1
