@@ -713,6 +713,283 @@ __device__ __forceinline__ void load_tw(C<R>* dst, const C<R>* src, int n) {
   for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
 }
 
+// ------------------------------------------------------------------ rows by warps
+// FP32 grids 256 points wide take the transforms along x one per warp (warp_fft256): a unit of
+// the row phases is kWarpRows grid rows, one per warp of the 256-thread block, and warp w keeps
+// its kWarpFftBuf values of the phase buffer at w * kWarpRowStride (a stride that puts the
+// block's reads across the rows on distinct banks).  Every kernel that runs these phases
+// launches blocks of 256 threads.
+constexpr int kWarpRows = 8, kWarpRowStride = kWarpFftBuf + 2;
+template <typename R>
+__host__ __device__ inline bool warp_rows(const DevParams& p) {
+  return sizeof(R) == 4 && p.nx == 256;
+}
+// Units of the row and inverse-row phases when the other path takes nb rows per unit.
+template <typename R>
+__host__ __device__ inline int row_units(const DevParams& p, int nb) {
+  return warp_rows<R>(p) ? (p.ny + kWarpRows - 1) / kWarpRows : (p.ny + nb - 1) / nb;
+}
+
+// One unit of the forward row phase by warps: rows qb .. qb + 7 (those below ny).  Warp w forms
+// the packed pairs of row qb + w (the same sums as row_phase), transforms them, and leaves each
+// spectrum in its buffer; the block then writes the half spectra of its rows, eight
+// consecutive k_y per (field, k_x).  k0: the first beam-source node read.
+template <typename R>
+__device__ void row_unit_w(const SweepArgs<R>& a, C<R>* buf, const C<R>* tw, int mode, int k0,
+                           int qb, R& charge) {
+  const DevParams& p = a.p;
+  constexpr int nx = 256;
+  const int ny = p.ny, nxh = p.nxh, nk = p.nk;
+  const int nf = (mode == DEP_TRIAL) ? kNF : 3;
+  const int npair = (nf + 1) / 2;
+  const int tile_elems = kTileRows * nx * nf;
+  const int nr = min(kWarpRows, ny - qb);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = qb + w;
+  const bool act = w < nr;
+  const R* __restrict__ part = a.part;
+  R* __restrict__ ovf = a.ovf;
+  const R* __restrict__ src = a.src;
+  C<R>* F = buf + w * kWarpRowStride;
+  const bool s0ok = src != nullptr && k0 >= 0 && k0 < nk;
+  const bool s1ok = src != nullptr && k0 + 1 < nk;
+  if (threadIdx.x == 0 && src != nullptr) {
+    // the unit's rows of the two beam-source nodes into L2 while the partials are read
+    const unsigned nbts = (unsigned)((size_t)nr * nx * 4 * sizeof(R));
+    if (s0ok) l2_prefetch(src + ((size_t)k0 * ny + qb) * nx * 4, nbts);
+    if (s1ok) l2_prefetch(src + ((size_t)(k0 + 1) * ny + qb) * nx * 4, nbts);
+  }
+  // grid row q collects tile row t of chunk q + 1 - t; rows 1, 2 always, rows 0, 3 and the
+  // overflow row only where a deposit landed
+  bool use0 = false, use3 = false, od = false;
+  const R *p0 = part, *p1 = part, *p2 = part, *p3 = part;
+  if (act) {
+    use0 = a.cflag[wrap(q + 1, ny)] & 1;
+    use3 = a.cflag[wrap(q - 2, ny)] & 2;
+    od = a.odirty[q] != 0;
+    p0 = part + (size_t)wrap(q + 1, ny) * tile_elems;
+    p1 = part + (size_t)q * tile_elems + nx;
+    p2 = part + (size_t)wrap(q - 1, ny) * tile_elems + 2 * nx;
+    p3 = part + (size_t)wrap(q - 2, ny) * tile_elems + 3 * nx;
+  }
+  for (int pr = 0; pr < npair; ++pr) {
+    const int f0 = 2 * pr, f1 = 2 * pr + 1;
+    if (act) {
+      C<R> z[8];
+      // the two home tile rows and the beam sources, four columns at a time with every load
+      // issued before the sums (the loads are independent; one at a time they would wait on
+      // L2 one after the other)
+      const size_t fo0 = (size_t)f0 * kTileRows * nx, fo1 = (size_t)f1 * kTileRows * nx;
+      const R* e0 = src + ((size_t)k0 * ny + q) * nx * 4;
+      const R* e1 = src + ((size_t)(k0 + 1) * ny + q) * nx * 4;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        R a0[4], a1[4], b0[4], b1[4], sa[4], sb[4], sc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int x = lane + 32 * (4 * h + i);
+          a0[i] = p1[fo0 + x];
+          b0[i] = p2[fo0 + x];
+          a1[i] = (f1 < nf) ? p1[fo1 + x] : R(0);
+          b1[i] = (f1 < nf) ? p2[fo1 + x] : R(0);
+          // the source components this pair adds (S_b 0, J_z 1, J_x 2, J_y 3 of nodes k0, k0+1)
+          sa[i] = sb[i] = sc[i] = R(0);
+          if (mode == DEP_TRIAL) {
+            if (pr == 0) {
+              if (s0ok) sa[i] = e0[4 * x + 2], sb[i] = e0[4 * x + 3];
+            } else if (pr == 1) {
+              if (s0ok) sa[i] = e0[4 * x + 1], sb[i] = e0[4 * x + 2];
+              if (s1ok) sc[i] = e1[4 * x + 2];
+            } else {
+              if (s0ok) sa[i] = e0[4 * x + 3];
+              if (s1ok) sb[i] = e1[4 * x + 3];
+            }
+          } else if (pr == 0) {
+            if (s1ok) sa[i] = e1[4 * x], sc[i] = e1[4 * x + 2];
+            if (s0ok) sb[i] = e0[4 * x + 2];
+          } else {
+            if (s0ok) sa[i] = e0[4 * x + 3];
+            if (s1ok) sb[i] = e1[4 * x + 3];
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          R v0 = a0[i] + b0[i], v1 = a1[i] + b1[i];
+          if (mode == DEP_TRIAL) {
+            if (pr == 0) {
+              v0 += sa[i];
+              v1 += sb[i];
+            } else if (pr == 1) {
+              v0 += sa[i];
+              v1 += R(0.5) * (sb[i] + sc[i]);
+            } else {
+              v0 += R(0.5) * (sa[i] + sb[i]);
+            }
+          } else if (pr == 0) {
+            charge += v0;  // the plasma charge (the rare rows below add to it too)
+            v0 += sa[i];
+            v1 += R(0.5) * (sb[i] + sc[i]);
+          } else {
+            v0 += R(0.5) * (sa[i] + sb[i]);
+          }
+          z[4 * h + i] = C<R>{v0, v1};
+        }
+      }
+      // rare: the outer tile rows and the overflow row, where a deposit landed
+      if (use0 || use3 || od) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int x = lane + 32 * m;
+          R v[2] = {0, 0};
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            const int f = f0 + t;
+            if (f >= nf) continue;
+            const size_t fo = (size_t)f * kTileRows * nx + x;
+            if (use0) v[t] += p0[fo];
+            if (use3) v[t] += p3[fo];
+            if (od) {
+              R* o = ovf + ((size_t)f * ny + q) * nx + x;
+              v[t] += *o;
+              *o = R(0);
+            }
+          }
+          if (mode != DEP_TRIAL && pr == 0) charge += v[0];
+          z[m].x += v[0];
+          z[m].y += v[1];
+        }
+      }
+      warp_fft256(z, F, tw, -1);
+#pragma unroll
+      for (int d = 0; d < 8; ++d) F[lane + 32 * d] = z[d];
+    }
+    __syncthreads();
+    // unpack two real transforms: A_k = (Z_k + conj Z_{-k})/2, B_k = -i (Z_k - conj Z_{-k})/2
+    for (int e = threadIdx.x; e < kWarpRows * nxh; e += blockDim.x) {
+      const int r = e & (kWarpRows - 1), k = e >> 3;
+      if (r >= nr) continue;
+      const C<R>* Zr = buf + r * kWarpRowStride;
+      const C<R> zk = Zr[k];
+      const C<R> zm = cconj(Zr[k == 0 ? 0 : nx - k]);
+      const C<R> fa = C<R>{R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y + zm.y)};
+      const C<R> fb = C<R>{R(0.5) * (zk.y - zm.y), R(-0.5) * (zk.x - zm.x)};
+      a.rspec[((size_t)f0 * nxh + k) * ny + qb + r] = fa;
+      if (f1 < nf) a.rspec[((size_t)f1 * nxh + k) * ny + qb + r] = fb;
+    }
+    __syncthreads();
+  }
+  if (act && lane == 0) a.odirty[q] = 0;  // consumed (every lane read it before the barriers)
+}
+
+// One unit of the inverse row phase by warps (see irow_phase): warp w transforms row qb + w
+// (two packed pairs of output fields, read row-contiguous from the column phase's spectra) and
+// writes the field grid, and on the last solve the slab, for the 8 columns x = lane + 32 d.
+template <typename R>
+__device__ void irow_unit_w(const SweepArgs<R>& a, C<R>* buf, const C<R>* tw, bool psi_mode,
+                            int j, bool last, R ez0r, int qb, R (&en)[6], bool& bad) {
+  const DevParams& p = a.p;
+  constexpr int nx = 256;
+  const int ny = p.ny, nxh = p.nxh;
+  const int nout = psi_mode ? 3 : 4;
+  const int nr = min(kWarpRows, ny - qb);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w >= nr) return;
+  const int q = qb + w;
+  const R scale = a.k.scale;
+  const C<R>* __restrict__ cspec = a.cspec;
+  R* __restrict__ fg = a.fg;
+  C<R>* F = buf + w * kWarpRowStride;
+  // the slab of the last solve adds W = -grad psi from the field grid, written one slice
+  // earlier and by now often out of L2: fetch the row while the transforms run
+  if (!psi_mode && last && lane == 0)
+    l2_prefetch(fg + (size_t)q * nx * kFG, (unsigned)((size_t)nx * kFG * sizeof(R)));
+  const C<R>* r0 = cspec + (size_t)q * nxh;  // field f's row: r0 + f * ny * nxh
+  const size_t fs = (size_t)ny * nxh;
+  for (int pr = 0; pr < 2; ++pr) {
+    const int f0 = 2 * pr, f1 = 2 * pr + 1;
+    C<R> z[8];
+    // full spectrum of z = a + i b from the half spectra of the real outputs a, b; four
+    // columns at a time with the loads issued first
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      C<R> fa[4], fb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k = lane + 32 * (4 * h + i);
+        const int kk = (k < nxh) ? k : nx - k;
+        fa[i] = r0[f0 * fs + kk];
+        fb[i] = (f1 < nout) ? r0[f1 * fs + kk] : C<R>{0, 0};
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k = lane + 32 * (4 * h + i);
+        const int kk = (k < nxh) ? k : nx - k;
+        if (kk == 0 || 2 * kk == nx) {  // self-conjugate columns
+          fa[i].y = R(0);
+          fb[i].y = R(0);
+        }
+        if (k >= nxh) {
+          fa[i] = cconj(fa[i]);
+          fb[i] = cconj(fb[i]);
+        }
+        z[4 * h + i] = cadd(fa[i], cmuli(fb[i]));
+      }
+    }
+    warp_fft256(z, F, tw, +1);
+    if (pr == 0 || psi_mode || !last) {
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        R* node = fg + ((size_t)q * nx + lane + 32 * d) * kFG;
+        const R va = z[d].x * scale, vb = z[d].y * scale;
+        if (pr == 0) {
+          node[psi_mode ? FG_PSI : FG_BX] = va;
+          node[psi_mode ? FG_GX : FG_BY] = vb;
+        } else if (psi_mode) {
+          node[FG_GY] = va;
+        } else {
+          node[FG_BZ] = va;
+          node[FG_EZ] = vb;
+        }
+      }
+      continue;
+    }
+    // the last solve: the slab node, its energies and the finiteness check; B_x, B_y are
+    // this thread's own stores of the first pair, W = -grad psi the field grid's; four
+    // columns at a time with the loads issued first
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      R bx[4], by[4], gx[4], gy[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const R* node = fg + ((size_t)q * nx + lane + 32 * (4 * h + i)) * kFG;
+        bx[i] = node[FG_BX];
+        by[i] = node[FG_BY];
+        gx[i] = node[FG_GX];
+        gy[i] = node[FG_GY];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int d = 4 * h + i, x = lane + 32 * d;
+        R* node = fg + ((size_t)q * nx + x) * kFG;
+        const R va = z[d].x * scale, vb = z[d].y * scale;
+        node[FG_BZ] = va;
+        node[FG_EZ] = vb;
+        const R wx = -gx[i], wy = -gy[i];
+        const R ez = ez0r + vb;
+        st8(a.slab + (((size_t)j * ny + q) * nx + x) * 8, wx, wy, ez, bx[i], by[i], va);
+        const R Ex = wx + by[i], Ey = wy - bx[i];
+        en[0] += Ex * Ex;
+        en[1] += Ey * Ey;
+        en[2] += ez * ez;
+        en[3] += bx[i] * bx[i];
+        en[4] += by[i] * by[i];
+        en[5] += va * va;
+        if (!(isfinite(Ex) && isfinite(Ey) && isfinite(ez) && isfinite(va))) bad = true;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ row phase (forward)
 // mode DEP_TRIAL: fields Jx^j, Jy^j, Jz^j, Jx^{j+1/2}, Jy^{j+1/2} of slice j = jj.
 // else: fields S, Jx^{jn-1/2}, Jy^{jn-1/2} of the new slice jn = jj.
@@ -733,14 +1010,20 @@ __device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, 
   R* __restrict__ ovf = a.ovf;
   const R* __restrict__ src = a.src;
   __shared__ double red[32];
-  if (u0 * nb >= ny) {  // no unit in this block
+  const bool wr = warp_rows<R>(p);
+  if (u0 * (wr ? kWarpRows : nb) >= ny) {  // no unit in this block
     if (threadIdx.x == 0 && mode != DEP_TRIAL) *pslot(a.dpart, jj, P_CHARGE) = 0.0;
     return;
   }
   R charge = R(0);
   load_tw(tw, a.twx, nx);
   const int k0 = (mode == DEP_TRIAL) ? jj : jj - 1;  // beam-source nodes k0, k0 + 1
-  for (int u = u0; u * nb < ny; u += G) {
+  if (wr) {
+    __syncthreads();
+    for (int u = u0; u * kWarpRows < ny; u += G)
+      row_unit_w(a, buf, tw, mode, k0, u * kWarpRows, charge);
+  }
+  for (int u = u0; !wr && u * nb < ny; u += G) {
     const int qb = u * nb, nr = min(nb, ny - qb);
     if (threadIdx.x == 0 && src != nullptr) {
       // the unit's rows of the two beam-source nodes into L2 while the partials are read
@@ -1048,7 +1331,7 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
   const C<R>* __restrict__ cspec = a.cspec;
   R* __restrict__ fg = a.fg;
   __shared__ double red[64];
-  if (u0 * nb >= ny) {  // no unit in this block
+  if (u0 * (warp_rows<R>(p) ? kWarpRows : nb) >= ny) {  // no unit in this block
     if (threadIdx.x == 0 && !psi_mode && last)
       for (int f = 0; f < 6; ++f) *pslot(a.dpart, j, P_E0 + f) = 0.0;
     return;
@@ -1056,7 +1339,14 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
   R en[6] = {0, 0, 0, 0, 0, 0};
   bool bad = false;
   load_tw(tw, a.twx, nx);
-  for (int u = u0; u * nb < ny; u += G) {
+  const bool wr = warp_rows<R>(p);
+  if (wr) {
+    __syncthreads();
+    for (int u = u0; u * kWarpRows < ny; u += G)
+      irow_unit_w(a, buf, tw, psi_mode, j, last, ez0r, u * kWarpRows, en, bad);
+    __syncthreads();  // the buffers and the table are reused by the block's next phase
+  }
+  for (int u = u0; !wr && u * nb < ny; u += G) {
     const int qb = u * nb, nr = min(nb, ny - qb);
     // the slab of the last solve adds W = -grad psi from the field grid, written one slice
     // earlier and by now often out of L2: fetch the unit's rows while the transforms run
@@ -1139,6 +1429,10 @@ __host__ __device__ inline size_t phase_smem_bytes(int nx, int ny, int nbr = 1, 
   size_t col = (size_t)2 * kNF * ny * nbc * sizeof(C<R>);
   size_t m = tile > row ? tile : row;
   m = m > col ? m : col;
+  if (sizeof(R) == 4 && nx == 256) {  // per-warp row transforms
+    const size_t wr = (size_t)kWarpRows * kWarpRowStride * sizeof(C<R>);
+    m = m > wr ? m : wr;
+  }
   return (m + 15) & ~size_t(15);
 }
 template <typename R>
