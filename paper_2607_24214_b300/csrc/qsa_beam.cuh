@@ -181,6 +181,7 @@ template <typename BR>
 struct Group {
   int kabs, iy;  // home xi node and row of the group
   BR* tile;      // [2][4][4][nx]: S_b, J_z, J_x, J_y deviations
+  int* outer;    // bit dk * 4 + r set when a deposit landed in the outer tile row r (0 or 3)
 };
 
 // Add weight * (s, z, jx, jy) at node k, unwrapped row gy, wrapped column x.
@@ -191,6 +192,7 @@ __device__ __forceinline__ void put(const Group<BR>& g, BR* src, const DevParams
   if (!QSA_IN(x >= 0 && x < p.nx)) return;
   if (dk >= 0 && dk < 2 && r >= 0 && r < 4) {
     const int nx = p.nx;
+    if (r == 0 || r == 3) atomicOr(g.outer, 1 << (dk * 4 + r));
     BR* t = g.tile + (size_t)(dk * 4 + r) * 4 * nx + x;
     atomicAdd(t, wt * s);
     atomicAdd(t + nx, wt * z);
@@ -516,9 +518,10 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
                            const BeamConst<BR> bc, const BR* __restrict__ slab, BR* src,
                            unsigned long long* lost, Extent ext, int grp, BR* tile) {
   using UZ = typename UzT<BR>::T;
-  __shared__ int s_ext[2];
+  __shared__ int s_ext[2], s_outer;
   Group<BR> g;
   g.tile = tile;
+  g.outer = &s_outer;
   g.iy = grp % p.ny;
   g.kabs = sp.k0 + grp / p.ny;
   const int nx = p.nx;
@@ -528,6 +531,7 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
   if (threadIdx.x == 0) {
     s_ext[0] = -1;
     s_ext[1] = 0;
+    s_outer = 0;
     for (int k = 0; k < 7; ++k) s_mom[k] = 0.0;
   }
   __syncthreads();
@@ -766,9 +770,12 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
       for (int k = 0; k < 7; ++k)
         if (s_mom[k] != 0.0) atomicAdd(ext.mom + (size_t)g.kabs * 7 + k, s_mom[k]);
   }
+  const int outer = s_outer;  // final: every deposit preceded the barrier above
   for (int row = 0; row < 2 * 4; ++row) {  // node kabs + row / 4, grid row iy - 1 + row % 4
     const int k = g.kabs + (row >> 2);
     if (k >= p.nk) continue;
+    // the outer rows hold something only where a deposit landed there
+    if (((row & 3) == 0 || (row & 3) == 3) && !((outer >> row) & 1)) continue;
     BR* dst = src + ((size_t)k * p.ny + wrap(g.iy - 1 + (row & 3), p.ny)) * nx * 4;
     for (int x = threadIdx.x; x < nx; x += blockDim.x) {
       const BR* t = g.tile + (size_t)row * 4 * nx + x;

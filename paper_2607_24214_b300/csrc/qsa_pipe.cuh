@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
       for (int s = 0; s < nslots; ++s) {
         const DevParams& p = sa[s].p;
         const int nk = p.nk, a = adv[s];
-        const int ur = row_units<R>(p, nbr), uc = (p.nxh + nbc - 1) / nbc;
+        const int ur = row_units<R>(p, nbr), uc = col_units<R>(p, nbc);
         if (a && js[s] >= 0) {
           ot_dep[nt] = udep;
           ot_row[nt] = urow;

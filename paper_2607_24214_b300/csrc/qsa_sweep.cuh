@@ -691,11 +691,25 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
     __syncthreads();
   }
   if (mode == DEP_TRIAL && first) {
-    double s = block_sum_lo(kap, red);
-    if (threadIdx.x == 0 && s != 0.0) atomicAdd(&a.diag[D_KAPPA * p.nk + j], s);
-    double m = block_min_lo(omin, red);
-    double nfl = block_sum_lo(nfloor, red);
+    // the three partials of the first solve in one block pass: the sums of 1/(1+psi) and of
+    // floored particles, and the minimum of 1 + psi (warps' values summed in warp order)
+    const R ks = warp_sum(kap), nfs = warp_sum(nfloor), om = warp_min(omin);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+      red[w] = (double)ks;
+      red[nw + w] = (double)nfs;
+      red[2 * nw + w] = (double)om;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
+      double sk = 0.0, nfl = 0.0, m = red[2 * nw];
+      for (int k = 0; k < nw; ++k) {
+        sk += red[k];
+        nfl += red[nw + k];
+        m = fmin(m, red[2 * nw + k]);
+      }
+      if (sk != 0.0) atomicAdd(&a.diag[D_KAPPA * p.nk + j], sk);
       *pslot(a.dpart, j, P_OPPMIN) = m;
       *pslot(a.dpart, j, P_NFLOOR) = nfl;
       if (nfl > 0) atomicOr(a.bar.status, ST_FLOOR);
@@ -728,6 +742,51 @@ __host__ __device__ inline bool warp_rows(const DevParams& p) {
 template <typename R>
 __host__ __device__ inline int row_units(const DevParams& p, int nb) {
   return warp_rows<R>(p) ? (p.ny + kWarpRows - 1) / kWarpRows : (p.ny + nb - 1) / nb;
+}
+
+// The same for the column phases of FP32 grids 256 points tall: a unit is one half-spectrum
+// column; the forward transforms along y of its fields run one per warp into the block's
+// column buffer ([field][k_y], in front of the warps' transform buffers), the k-space solve
+// runs one k_y per thread, and the inverse transforms again one per warp.
+template <typename R>
+__host__ __device__ inline bool warp_cols(const DevParams& p) {
+  return sizeof(R) == 4 && p.ny == 256;
+}
+template <typename R>
+__host__ __device__ inline int col_units(const DevParams& p, int nb) {
+  return warp_cols<R>(p) ? p.nxh : (p.nxh + nb - 1) / nb;
+}
+// Forward transform along y, by warp w, of column kx of field w of the row phase's spectra
+// into the column buffer.
+template <typename R>
+__device__ __forceinline__ void col_forward_w(const SweepArgs<R>& a, C<R>* buf, const C<R>* tw,
+                                              int kx) {
+  constexpr int ny = 256;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  C<R>* F = buf + kNF * ny + w * kWarpRowStride;
+  const C<R>* col = a.rspec + ((size_t)w * a.p.nxh + kx) * ny;
+  C<R> z[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) z[m] = col[lane + 32 * m];
+  warp_fft256(z, F, tw, -1);
+#pragma unroll
+  for (int d = 0; d < 8; ++d) buf[w * ny + lane + 32 * d] = z[d];
+}
+// Inverse transform along y, by warp w, of output field w of the column buffer into the
+// spectra the inverse row phase reads ([field][y][k_x]).
+template <typename R>
+__device__ __forceinline__ void col_inverse_w(const SweepArgs<R>& a, C<R>* buf, const C<R>* tw,
+                                              int kx) {
+  constexpr int ny = 256;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nxh = a.p.nxh;
+  C<R>* F = buf + kNF * ny + w * kWarpRowStride;
+  C<R> z[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) z[m] = buf[w * ny + lane + 32 * m];
+  warp_fft256(z, F, tw, +1);
+#pragma unroll
+  for (int d = 0; d < 8; ++d) a.cspec[((size_t)w * ny + lane + 32 * d) * nxh + kx] = z[d];
 }
 
 // One unit of the forward row phase by warps: rows qb .. qb + 7 (those below ny).  Warp w forms
@@ -1167,7 +1226,7 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
   C<R>* A = buf;
   C<R>* B = buf + kNF * ny * nb;
   __shared__ R s_kap;
-  if (u0 * nb >= nxh) {  // no unit in this block
+  if (u0 * (warp_cols<R>(p) ? 1 : nb) >= nxh) {  // no unit in this block
     if (threadIdx.x == 0 && last) {
       *pslot(a.dpart, j, P_PCNUM) = 0.0;
       *pslot(a.dpart, j, P_PCDEN) = 0.0;
@@ -1182,7 +1241,62 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
   __shared__ double red[32];
   R num = R(0), den = R(0);
   load_tw(tw, a.twy, ny);
-  for (int u = u0; u * nb < nxh; u += G) {
+  const bool wc = warp_cols<R>(p);
+  if (wc) __syncthreads();  // the table and s_kap
+  for (int kx = u0; wc && kx < nxh; kx += G) {
+    const int w = threadIdx.x >> 5;
+    if (w < kNF) col_forward_w(a, buf, tw, kx);
+    __syncthreads();
+    {
+      // the solve at k_y = threadIdx.x, in place: outputs B_x, B_y, B_z, E_z over fields 0..3
+      const int ky = threadIdx.x;
+      const R kap = s_kap;
+      const R pw = (kx == 0 || ((p.nx % 2 == 0) && 2 * kx == p.nx)) ? R(1) : R(2);
+      const size_t ix0 = (size_t)kx * ny + ky, ix1 = ((size_t)nxh + kx) * ny + ky;
+      const C<R> Jxp = jprev[ix0], Jyp = jprev[ix1];
+      const C<R> Bxo = bold[ix0], Byo = bold[ix1];
+      const C<R> Jx = buf[ky], Jy = buf[ny + ky], Jz = buf[2 * ny + ky];
+      const C<R> Jxh = buf[3 * ny + ky], Jyh = buf[4 * ny + ky];
+      if (kx == 0 && ky == 0) {
+        const double opp0 = 1.0 + psi0;
+        const double jz_ref =
+            psi0 * (2.0 + psi0) / (2.0 * opp0 * opp0) + (a.bref ? a.bref[j] : 0.0);
+        a.diag[D_JZ * p.nk + j] = (double)Jz.x / ((double)p.nx * p.ny) + jz_ref;
+      }
+      const Kv<R> k = kvec(a.ktab, nxh, ny, kx, ky);
+      C<R> obx{0, 0}, oby{0, 0}, obz{0, 0}, oez{0, 0};
+      if (k.k2 > R(0)) {
+        const R ik2 = R(1) / k.k2;
+        const R kxd = k.kxd, kyd = k.kyd;
+        const C<R> Dx = cscale(csub(Jxh, Jxp), rdxi), Dy = cscale(csub(Jyh, Jyp), rdxi);
+        obz = cscale(cmuli(csub(cscale(Jy, kxd), cscale(Jx, kyd))), ik2);
+        oez = cscale(cmuli(cadd(cscale(Jx, kxd), cscale(Jy, kyd))), -ik2);
+        const R ih = R(1) / (k.k2 + kap);
+        obx = cscale(cadd(cadd(cmuli(cscale(Jz, kyd)), Dy), cscale(Bxo, kap)), ih);
+        oby = cscale(csub(csub(cscale(Byo, kap), cmuli(cscale(Jz, kxd))), Dx), ih);
+        if (last) {
+          const R ex = obx.x - Bxo.x, ey = obx.y - Bxo.y;
+          const R fx = oby.x - Byo.x, fy = oby.y - Byo.y;
+          num += pw * (ex * ex + ey * ey + fx * fx + fy * fy);
+          den += pw * (obx.x * obx.x + obx.y * obx.y + oby.x * oby.x + oby.y * oby.y);
+        }
+      }
+      bold[ix0] = obx;
+      bold[ix1] = oby;
+      buf[ky] = obx;
+      buf[ny + ky] = oby;
+      buf[2 * ny + ky] = obz;
+      buf[3 * ny + ky] = oez;
+    }
+    __syncthreads();
+    if (last) {
+      const int fields[4] = {2, 3, 4, 1};  // B_x, B_y, B_z, E_z
+      record_modes(a, buf, kx, 1, 4, fields, j);
+    }
+    if (w < 4) col_inverse_w(a, buf, tw, kx);
+    __syncthreads();  // the column buffer is the next unit's
+  }
+  for (int u = u0; !wc && u * nb < nxh; u += G) {
     const int kb = u * nb, nc = min(nb, nxh - kb);
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
       const int c = div_by(e, p.fd_ny), ky = e - c * ny, kx = kb + c;
@@ -1271,9 +1385,37 @@ __device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int u0
   C<R>* A = buf;
   C<R>* B = buf + kNF * ny * nb;
   const C<R>* __restrict__ rspec = a.rspec;
-  if (u0 * nb >= nxh) return;  // no unit in this block
+  const bool wc = warp_cols<R>(p);
+  if (u0 * (wc ? 1 : nb) >= nxh) return;  // no unit in this block
   load_tw(tw, a.twy, ny);
-  for (int u = u0; u * nb < nxh; u += G) {
+  if (wc) __syncthreads();  // the table
+  for (int kx = u0; wc && kx < nxh; kx += G) {
+    const int w = threadIdx.x >> 5;
+    if (w < 3) col_forward_w(a, buf, tw, kx);
+    __syncthreads();
+    {
+      // psi and its gradient at k_y = threadIdx.x, in place over fields 0..2; the spectra of
+      // J_perp^{j-1/2} are kept for the next slice's B_perp solves
+      const int ky = threadIdx.x;
+      const size_t ix0 = (size_t)kx * ny + ky, ix1 = ((size_t)nxh + kx) * ny + ky;
+      a.jprev[ix0] = buf[ny + ky];
+      a.jprev[ix1] = buf[2 * ny + ky];
+      const Kv<R> k = kvec(a.ktab, nxh, ny, kx, ky);
+      C<R> ps{0, 0};
+      if (k.k2 > R(0)) ps = cscale(buf[ky], R(1) / k.k2);
+      buf[ky] = ps;
+      buf[ny + ky] = cmuli(cscale(ps, k.kxd));
+      buf[2 * ny + ky] = cmuli(cscale(ps, k.kyd));
+    }
+    __syncthreads();
+    {
+      const int fields[3] = {0, -1, -1};  // psi
+      record_modes(a, buf, kx, 1, 3, fields, jn);
+    }
+    if (w < 3) col_inverse_w(a, buf, tw, kx);
+    __syncthreads();  // the column buffer is the next unit's
+  }
+  for (int u = u0; !wc && u * nb < nxh; u += G) {
     const int kb = u * nb, nc = min(nb, nxh - kb);
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
       const int c = div_by(e, p.fd_ny), ky = e - c * ny, kx = kb + c;
@@ -1429,9 +1571,15 @@ __host__ __device__ inline size_t phase_smem_bytes(int nx, int ny, int nbr = 1, 
   size_t col = (size_t)2 * kNF * ny * nbc * sizeof(C<R>);
   size_t m = tile > row ? tile : row;
   m = m > col ? m : col;
-  if (sizeof(R) == 4 && nx == 256) {  // per-warp row transforms
+  // the per-warp paths (grids 256 wide or tall); a multi-slot launch sizes its buffer for
+  // its largest grid, so every size from 256 up covers them
+  if (sizeof(R) == 4 && nx >= 256) {  // per-warp row transforms
     const size_t wr = (size_t)kWarpRows * kWarpRowStride * sizeof(C<R>);
     m = m > wr ? m : wr;
+  }
+  if (sizeof(R) == 4 && ny >= 256) {  // column buffer and five per-warp transform buffers
+    const size_t wc = ((size_t)kNF * 256 + kNF * kWarpRowStride) * sizeof(C<R>);
+    m = m > wc ? m : wc;
   }
   return (m + 15) & ~size_t(15);
 }
