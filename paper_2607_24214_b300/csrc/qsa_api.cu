@@ -688,6 +688,10 @@ int advance_pipelined(qsa_handle* h, int n) {
       t.st[i] = s->slots[i];
       t.st[i].src = ring_src<R>(h, h->pushes + i);
       t.slot[i] = make_slot<R>(h, h->pushes + i);
+      // only the last step's beam moments are ever read (qsa_diagnostics reports the state
+      // after the last push); the away count only feeds re-homing
+      if (i + 1 < m) t.slot[i].mom_out = nullptr;
+      if (!(h->prm.rehome_frac > 0.0)) t.slot[i].away = nullptr;
     }
     int grid = 0;
     if (int rc = launch_slots<R>(h, t, m, kPipeRowBatch, kPipeColBatch, &grid)) return rc;

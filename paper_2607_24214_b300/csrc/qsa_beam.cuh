@@ -645,15 +645,17 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
           const int cell = min((int)floor(hk[u] + oxi[u]), kleft - 1);
           cmax_t = max(cmax_t, g.kabs + cell);
           dmin_t = min(dmin_t, cell);
-          const BR wr = BR(1) + dw[u], duz = uz_dev(uz[u], bc);
-          const BR mv[7] = {wr, wr * ux[u], wr * uy[u], wr * duz, wr * ux[u] * ux[u],
-                            wr * uy[u] * uy[u], wr * duz * duz};
-          if (cell == 0) {
+          if (ext.mom) {  // the moments, where asked for
+            const BR wr = BR(1) + dw[u], duz = uz_dev(uz[u], bc);
+            const BR mv[7] = {wr, wr * ux[u], wr * uy[u], wr * duz, wr * ux[u] * ux[u],
+                              wr * uy[u] * uy[u], wr * duz * duz};
+            if (cell == 0) {
 #pragma unroll
-            for (int k = 0; k < 7; ++k) mom_t[k] += mv[k];
-          } else if (ext.mom && g.kabs + cell >= 0 && g.kabs + cell < p.nxi) {
-            for (int k = 0; k < 7; ++k)
-              atomicAdd(ext.mom + (size_t)(g.kabs + cell) * 7 + k, (double)mv[k]);
+              for (int k = 0; k < 7; ++k) mom_t[k] += mv[k];
+            } else if (g.kabs + cell >= 0 && g.kabs + cell < p.nxi) {
+              for (int k = 0; k < 7; ++k)
+                atomicAdd(ext.mom + (size_t)(g.kabs + cell) * 7 + k, (double)mv[k]);
+            }
           }
         }
         beam_sources(ux[u], uy[u], uz_lead(uz[u]), uz_dev(uz[u], bc), dw[u], bc, dv[u][0],
@@ -663,7 +665,7 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
         doxi[u] = oxi[u];
         post_home = post_home && in_cell(hx[u] + ox[u], hy[u] + oy[u], hk[u] + oxi[u]);
         // away from the slot's cell transversely (what re-homing within the layer can mend)
-        my_away += in_cell(hx[u] + ox[u], hy[u] + oy[u], BR(0)) ? 0 : 1;
+        if (ext.away) my_away += in_cell(hx[u] + ox[u], hy[u] + oy[u], BR(0)) ? 0 : 1;
       }
       if (lane_agg && __all_sync(0xffffffffu, post_home)) {
         // every particle of the warp's two sub-lattice positions is in its home cell: the two
@@ -754,8 +756,9 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
   }
   cmax_t = warp_max(cmax_t);
   dmin_t = warp_min(dmin_t);
+  if (ext.mom)
 #pragma unroll
-  for (int k = 0; k < 7; ++k) mom_t[k] = warp_sum(mom_t[k]);
+    for (int k = 0; k < 7; ++k) mom_t[k] = warp_sum(mom_t[k]);
   if ((threadIdx.x & 31) == 0) {
     if (cmax_t > s_ext[0]) atomicMax(&s_ext[0], cmax_t);
     if (dmin_t < 0) atomicMin(&s_ext[1], dmin_t);

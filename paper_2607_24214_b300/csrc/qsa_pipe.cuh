@@ -53,10 +53,10 @@ struct PipeSlot {
   R* src_next;
   const int* cmax_in;   // [nxi]
   int* cmax_out;        // [nxi]
-  double* mom_out;      // [nspecies][nxi][7]
+  double* mom_out;      // [nspecies][nxi][7], or null (moments not needed)
   const int* dmin;      // min over live particles of (xi cell - home layer), <= 0
   unsigned long long* lost;
-  unsigned long long* away;  // live particles outside their slots' cells after the pushes
+  unsigned long long* away;  // live particles outside their slots' cells after the pushes, or null
   int nspecies;
   BeamArrays<R> beam[kMaxSpecies];
   SpeciesDev sp[kMaxSpecies];
@@ -300,7 +300,9 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
           for (int q = unit0(base, G); q < p.ny; q += G)
             beam_group<R, true>(ps.beam[si], p, sp, ps.bc[si], sa[s].slab, ps.src_next,
                                 ps.lost,
-                                Extent{ps.cmax_out, nullptr, ps.mom_out + (size_t)si * p.nxi * 7,
+                                Extent{ps.cmax_out, nullptr,
+                                       ps.mom_out ? ps.mom_out + (size_t)si * p.nxi * 7
+                                                  : nullptr,
                                        ps.away},
                                 (c - sp.k0) * p.ny + q, tile);
           base += p.ny;
