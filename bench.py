@@ -35,6 +35,8 @@ import numpy as np  # noqa: E402
 from paper_2607_24214_b300 import config  # noqa: E402
 
 METRIC = "plasma particle-slice updates/s (push+deposit+field solve), mixed vs FP64"
+# ncu summary holding the DRAM bytes of one full pipelined launch of the workload
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pipe_kernel_c2_linear_launch_dram.md")
 WORKLOAD = "c2_mixed_electron_beam_256x256_1024slices"
 CPU_SAMPLE_SLICES = 12
 
@@ -283,6 +285,42 @@ def run_reference(args, p):
     print(json.dumps(line), flush=True)
 
 
+def kernel_sources_sha256() -> str:
+    """SHA-256 over the library's CUDA sources (csrc/*.cu, *.cuh, *.h, in name order)."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2607_24214_b300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(p, steps_per_launch):
+    """DRAM bytes (read + write) of one full pipelined launch, from the committed ncu summary,
+    when that capture was taken on these kernel sources, this grid and this launch length;
+    else None (the counters no longer describe the kernel that ran)."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            lines = f.read().splitlines()
+    except OSError:
+        return None
+    kv = {}
+    for ln in lines:
+        if ln.startswith("- ") and ": " in ln:
+            k, v = ln[2:].split(": ", 1)
+            kv[k.strip()] = v.strip()
+    want = f"nx {p.nx}, ny {p.ny}, nxi {p.nxi}, steps per launch {steps_per_launch}"
+    if kv.get("kernel sources sha256") != kernel_sources_sha256() or kv.get("workload") != want:
+        return None
+    try:
+        return float(kv["dram bytes per launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -350,9 +388,12 @@ def main():
         dom_ms = float(np.mean(full if full else lt))
         dom_steps = args.depth if full else args.steps
         achieved = pipe_bytes(p, dom_steps) / (dom_ms * 1e-3) / 1e9
+        traffic = measured_traffic(p, dom_steps)
         roof = {"bound": "hbm", "kernel": "pipe_kernel", "achieved": achieved,
                 "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": None,
+                "traffic": traffic,
+                "traffic_launch": ("the first timed launch (linear stage), one ncu capture of "
+                                   "these kernel sources" if traffic is not None else None),
                 "algorithmic_bytes": pipe_bytes(p, dom_steps),
                 "peak_source": peak_src, "launch_ms": dom_ms,
                 "steps_per_launch": dom_steps, "kernel_share": float(np.sum(lt)) / ms,
