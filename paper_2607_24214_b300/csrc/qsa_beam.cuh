@@ -184,26 +184,6 @@ struct Group {
   int* outer;    // bit dk * 4 + r set when a deposit landed in the outer tile row r (0 or 3)
 };
 
-// Add weight * (s, z, jx, jy) at node k, unwrapped row gy, wrapped column x.
-template <typename BR>
-__device__ __forceinline__ void put(const Group<BR>& g, BR* src, const DevParams& p, int k, int gy,
-                                    int x, BR wt, BR s, BR z, BR jx, BR jy) {
-  const int dk = k - g.kabs, r = gy - (g.iy - 1);
-  if (!QSA_IN(x >= 0 && x < p.nx)) return;
-  if (dk >= 0 && dk < 2 && r >= 0 && r < 4) {
-    const int nx = p.nx;
-    if (r == 0 || r == 3) atomicOr(g.outer, 1 << (dk * 4 + r));
-    BR* t = g.tile + (size_t)(dk * 4 + r) * 4 * nx + x;
-    atomicAdd(t, wt * s);
-    atomicAdd(t + nx, wt * z);
-    atomicAdd(t + 2 * nx, wt * jx);
-    atomicAdd(t + 3 * nx, wt * jy);
-  } else if (k >= 0 && k < p.nk) {
-    red4(src + (((size_t)k * p.ny + wrap(gy, p.ny)) * p.nx + x) * 4, wt * s, wt * z, wt * jx,
-         wt * jy);
-  }
-}
-
 // Trilinear weights W of the eight corners of the home cell at (h + d) and their differences
 // dW = W - W(h) from the reference position h, both separable by axis: with a = h or 1 - h and
 // d = +-offset per axis, W = (a1 + d1)(a2 + d2)(a3 + d3) and the difference telescopes as
@@ -262,25 +242,44 @@ __device__ __forceinline__ void deposit_particle(const Group<BR>& g, BR* src, co
     }
     return;
   }
-  // left the home cell: full weights at the new corners, minus the reference at home
+  // left the home cell: full weights at the new corners, minus the reference at home.  The
+  // destination (tile row or global row) is settled once per (node, row); the row's two
+  // corners share it
 #pragma unroll 1
   for (int pass = 0; pass < (home_ref ? 2 : 1); ++pass) {
     const BR mx = pass ? hx : lx, my = pass ? hy : ly, mk = pass ? hk : lk;
     const BR fx = floor(mx), fy = floor(my), fk = floor(mk);
     const BR ex = mx - fx, ey = my - fy, ek = mk - fk;
-    const int gx = ix + (int)fx, gy = g.iy + (int)fy, gk = g.kabs + (int)fk;
+    const int gx0 = wrap(ix + (int)fx, nx), gx1 = (gx0 + 1 == nx) ? 0 : gx0 + 1;
+    const int gy = g.iy + (int)fy, gk = g.kabs + (int)fk;
+    (void)QSA_IN(gx0 >= 0 && gx0 < nx && gx1 < nx);
     const BR s0 = pass ? -refS : dS + refS, z0 = pass ? -refJz : dJz + refJz;
     const BR x0v = pass ? BR(0) : jx, y0v = pass ? BR(0) : jy;
 #pragma unroll
     for (int ck = 0; ck < 2; ++ck) {
+      const int k = gk + ck, dk = k - g.kabs;
+      if (k < 0 || k >= p.nk) continue;
       const BR wk = ck ? ek : BR(1) - ek;
 #pragma unroll
       for (int cy = 0; cy < 2; ++cy) {
         const BR wy = wk * (cy ? ey : BR(1) - ey);
-#pragma unroll
-        for (int cx = 0; cx < 2; ++cx) {
-          const BR wt = wy * (cx ? ex : BR(1) - ex);
-          put(g, src, p, gk + ck, gy + cy, wrap(gx + cx, nx), wt, s0, z0, x0v, y0v);
+        const BR w0 = wy * (BR(1) - ex), w1 = wy * ex;
+        const int r = gy + cy - (g.iy - 1);
+        if (dk >= 0 && dk < 2 && r >= 0 && r < 4) {
+          if (r == 0 || r == 3) atomicOr(g.outer, 1 << (dk * 4 + r));
+          BR* t = g.tile + (size_t)(dk * 4 + r) * 4 * nx;
+          atomicAdd(t + gx0, w0 * s0);
+          atomicAdd(t + nx + gx0, w0 * z0);
+          atomicAdd(t + 2 * nx + gx0, w0 * x0v);
+          atomicAdd(t + 3 * nx + gx0, w0 * y0v);
+          atomicAdd(t + gx1, w1 * s0);
+          atomicAdd(t + nx + gx1, w1 * z0);
+          atomicAdd(t + 2 * nx + gx1, w1 * x0v);
+          atomicAdd(t + 3 * nx + gx1, w1 * y0v);
+        } else {
+          BR* e = src + ((size_t)k * p.ny + wrap(gy + cy, p.ny)) * nx * 4;
+          red4(e + (size_t)gx0 * 4, w0 * s0, w0 * z0, w0 * x0v, w0 * y0v);
+          red4(e + (size_t)gx1 * 4, w1 * s0, w1 * z0, w1 * x0v, w1 * y0v);
         }
       }
     }
