@@ -894,28 +894,42 @@ __device__ void row_unit_w(const SweepArgs<R>& a, C<R>* buf, const C<R>* tw, int
           z[4 * h + i] = C<R>{v0, v1};
         }
       }
-      // rare: the outer tile rows and the overflow row, where a deposit landed
+      // rare: the outer tile rows and the overflow row, where a deposit landed; four
+      // columns at a time, loads first, then the overflow entries zeroed
       if (use0 || use3 || od) {
+        R* o0 = ovf + ((size_t)f0 * ny + q) * nx;
+        R* o1 = ovf + ((size_t)f1 * ny + q) * nx;
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const int x = lane + 32 * m;
-          R v[2] = {0, 0};
+        for (int h = 0; h < 2; ++h) {
+          R v0[4], v1[4];
 #pragma unroll
-          for (int t = 0; t < 2; ++t) {
-            const int f = f0 + t;
-            if (f >= nf) continue;
-            const size_t fo = (size_t)f * kTileRows * nx + x;
-            if (use0) v[t] += p0[fo];
-            if (use3) v[t] += p3[fo];
+          for (int i = 0; i < 4; ++i) {
+            const int x = lane + 32 * (4 * h + i);
+            v0[i] = v1[i] = R(0);
+            if (use0) {
+              v0[i] += p0[fo0 + x];
+              if (f1 < nf) v1[i] += p0[fo1 + x];
+            }
+            if (use3) {
+              v0[i] += p3[fo0 + x];
+              if (f1 < nf) v1[i] += p3[fo1 + x];
+            }
             if (od) {
-              R* o = ovf + ((size_t)f * ny + q) * nx + x;
-              v[t] += *o;
-              *o = R(0);
+              v0[i] += o0[x];
+              if (f1 < nf) v1[i] += o1[x];
             }
           }
-          if (mode != DEP_TRIAL && pr == 0) charge += v[0];
-          z[m].x += v[0];
-          z[m].y += v[1];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int m = 4 * h + i, x = lane + 32 * m;
+            if (od) {
+              o0[x] = R(0);
+              if (f1 < nf) o1[x] = R(0);
+            }
+            if (mode != DEP_TRIAL && pr == 0) charge += v0[i];
+            z[m].x += v0[i];
+            z[m].y += v1[i];
+          }
         }
       }
       warp_fft256(z, F, tw, -1);
