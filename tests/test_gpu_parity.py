@@ -45,7 +45,8 @@ def gpu(Q, p, beams=None):
 
 # ------------------------------------------------------------------ transverse solves
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("nx,ny", [(32, 32), (9, 12), (1, 64), (96, 48), (256, 256)])
+@pytest.mark.parametrize("nx,ny", [(32, 32), (9, 12), (1, 64), (96, 48), (256, 256), (256, 36),
+                                   (36, 256)])
 def test_field_solve(Q, prec, nx, ny):
     p = config.Params(nx=nx, ny=ny, nxi=4, Lx=0.3 * nx, Ly=0.25 * ny, Lxi=1.0, dt=1.0,
                       precision=prec)
@@ -162,6 +163,38 @@ def test_sweep_without_beam(Q):
     q.sweep()
     assert np.abs(q.slab()).max() == 0.0
     assert q.diagnostics()["charge"].max() < 1e-12
+
+
+# ------------------------------------------------------------------ per-warp transforms
+# FP32 rows of 256 points and FP32 columns of 256 points take the per-warp transforms, each on
+# its own: grids 256 wide but 36 tall (the last 8-row unit of the row phases holds 4 rows),
+# and the reverse.
+WARP_GRIDS = {"rows256": (256, 36), "cols256": (36, 256)}
+
+
+def _warp_grid(geom, **kw):
+    nx, ny = WARP_GRIDS[geom]
+    return config.c1_fp64_electron_beam().with_(nx=nx, ny=ny, Lx=nx * 0.2, Ly=ny * 0.2, nxi=8,
+                                                Lxi=1.0, precision="mixed", **kw)
+
+
+@pytest.mark.parametrize("geom", sorted(WARP_GRIDS))
+def test_sweep_warp_paths_mixed(Q, geom):
+    _sweep_parity(Q, _warp_grid(geom), TOL["mixed"])
+
+
+@pytest.mark.parametrize("geom", sorted(WARP_GRIDS))
+def test_pipelined_warp_paths_mixed(Q, geom):
+    """Two beam steps as one pipelined launch of two slots, then a sweep, against the
+    oracle's run."""
+    p = _warp_grid(geom, pipeline_depth=2)
+    beams = inputs.all_beams(p)
+    q = gpu(Q, p, beams)
+    q.advance(2)
+    q.sweep()
+    ref_slab, _, _ = qspic.run(p, beams, 2)
+    err = field_err(q.slab(), ref_slab)
+    assert err.max() <= TOL["mixed"], err
 
 
 # ------------------------------------------------------------------ beam step parity
