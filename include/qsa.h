@@ -227,6 +227,19 @@ int qsa_advance(qsa_handle* h, int32_t n_steps);
  * launch timing (qsa_launch_times).  Asynchronous, except during the timing steps. */
 int qsa_advance_batch(qsa_handle* const* handles, int32_t n_handles, int32_t n_steps);
 
+/* CUDA graphs of the batched steps (the paper has no counterpart).
+ * qsa_advance_batch led by `lead` runs each step after the autotuner's timing steps as a
+ * CUDA graph: the step's stream work (slot preparation, the table uploads from pinned host
+ * copies, the persistent launches, the diagnostic reductions) is captured once per distinct
+ * step (the same handles, FFT unit shape and ring phase of each handle's sources) and
+ * replayed; a step whose capture fails runs directly, and so do the later ones.  The
+ * results are those of the direct launches.  enable: 1 on (the default; also retries after
+ * a failed capture), 0 off, < 0 unchanged.  replays (optional): the number of steps run as
+ * graphs so far, or -1 - that number when graphs are off or a capture failed.  With graphs,
+ * qsa_launch_times reports the launches of the last direct step and of the captured steps'
+ * latest replays. */
+int qsa_batch_graphs(qsa_handle* lead, int32_t enable, int64_t* replays);
+
 /* Tracing (the paper has no counterpart).
  * Device time, in ms, of each persistent launch of the last pipelined qsa_advance or
  * qsa_advance_batch call led by h (CUDA events recorded around the launches on the handle's

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <atomic>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -67,6 +68,28 @@ struct qsa_handle {
   bool beam_replaced = false;  // qsa_set_beam replaced the beam qsa_init built
   int64_t rehomes = 0;         // re-homings of the beam done (qsa_rehome, qsa_advance)
   int last_pushes = 0;         // pushes of the last pipelined launch
+  uint64_t serial = 0;         // unique over the process's handles, never reused
+  // CUDA graphs of the batched steps this handle leads (qsa_advance_batch)
+  std::vector<struct BatchGraph*> graphs;
+  bool batch_graphs = true;    // capture and replay the batched steps
+  bool graphs_failed = false;  // a capture failed: launch directly from then on
+  int64_t graph_replays = 0;
+  cudaStream_t cap_stream = nullptr;  // the stream the batched steps are captured on
+};
+
+// One batched step as a CUDA graph: the same stream work for the same handles, FFT unit
+// shape and ring phases (every pointer the step touches is fixed by them).  The slot tables
+// it uploads live in pinned host memory of its own.
+struct BatchGraph {
+  std::vector<uint64_t> serials;
+  std::vector<int64_t> phases;
+  int nbr = 0, nbc = 0;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<void*> tables;
+  ~BatchGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (void* t : tables) cudaFreeHost(t);
+  }
 };
 
 // State of a differentiable run between qsa_grad_forward and qsa_grad_backward.
@@ -712,9 +735,139 @@ int advance_pipelined(qsa_handle* h, int n) {
 // FFT unit shapes the batch autotuner tries (rows x half-spectrum columns per unit).
 constexpr int kTuneShapes[4][2] = {{2, 1}, {1, 1}, {4, 1}, {2, 2}};
 
+// The stream work of one batched step (every handle by one step, kMaxPipe per launch): slot
+// preparation, the launches and the diagnostic reductions, for the handles' current push
+// counts; tables[c] (one per launch) holds the slot table the launch uploads.  The host-side
+// counters are advanced by finish_batch_step.
+template <typename R>
+int issue_batch_step(qsa_handle* const* hs, int nh, int nbr, int nbc,
+                     PipeTable<R>* const* tables, int* failed) {
+  qsa_handle* lead = hs[0];
+  for (int c0 = 0, c = 0; c0 < nh; c0 += kMaxPipe, ++c) {
+    const int m = std::min(kMaxPipe, nh - c0);
+    PipeTable<R>& t = *tables[c];
+    t = PipeTable<R>{};
+    t.chained = 0;
+    for (int i = 0; i < m; ++i) {
+      qsa_handle* h = hs[c0 + i];
+      SweepArgs<R>& a = S<R>(h)->slots[0];
+      if (int rc = prepare_slot<R>(h, a, h->pushes)) {
+        *failed = c0 + i;
+        return rc;
+      }
+      t.st[i] = a;
+      t.st[i].src = ring_src<R>(h, h->pushes);
+      t.slot[i] = make_slot<R>(h, h->pushes);
+    }
+    int grid = 0;
+    if (int rc = launch_slots<R>(lead, t, m, nbr, nbc, &grid)) {
+      *failed = 0;
+      return rc;
+    }
+    for (int i = 0; i < m; ++i) {
+      qsa_handle* h = hs[c0 + i];
+      SweepArgs<R>& a = S<R>(h)->slots[0];
+      diag_reduce_kernel<<<h->dp.nk, 256, 0, h->stream>>>(a.dpart, grid, a.diag, h->dp.nk);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        *failed = c0 + i;
+        return cuda_fail(h, e, "diag_reduce_kernel");
+      }
+    }
+  }
+  return QSA_OK;
+}
+
+template <typename R>
+void finish_batch_step(qsa_handle* const* hs, int nh) {
+  for (int i = 0; i < nh; ++i) {
+    qsa_handle* h = hs[i];
+    h->launches += 2;  // the diagnostic initialisation and reduction
+    h->pushes += 1;
+    h->sweeps += 1;
+    S<R>(h)->last_slot = 0;
+    h->src_valid = true;
+  }
+  hs[0]->launches += (nh + kMaxPipe - 1) / kMaxPipe;
+}
+
+// The graph of this step of the batch (captured on first use), or null when the step cannot
+// be captured (then it runs directly, and so does every later step of this lead).
+template <typename R>
+BatchGraph* batch_graph(qsa_handle* const* hs, int nh, int nbr, int nbc) {
+  qsa_handle* lead = hs[0];
+  std::vector<uint64_t> serials(nh);
+  std::vector<int64_t> phases(nh);
+  for (int i = 0; i < nh; ++i) {
+    serials[i] = hs[i]->serial;
+    phases[i] = hs[i]->pushes % (int64_t)S<R>(hs[i])->srcs.size();
+  }
+  for (BatchGraph* g : lead->graphs)
+    if (g->nbr == nbr && g->nbc == nbc && g->serials == serials && g->phases == phases) return g;
+  if (lead->graphs.size() >= 64) {  // keyed by serials: stale entries only cost memory
+    for (BatchGraph* g : lead->graphs) delete g;
+    lead->graphs.clear();
+  }
+  auto* g = new BatchGraph;
+  g->serials = serials;
+  g->phases = phases;
+  g->nbr = nbr;
+  g->nbc = nbc;
+  const int nl = (nh + kMaxPipe - 1) / kMaxPipe;
+  for (int c = 0; c < nl; ++c) {
+    void* t = nullptr;
+    if (cudaMallocHost(&t, sizeof(PipeTable<R>)) != cudaSuccess) {
+      delete g;
+      cudaGetLastError();
+      return nullptr;
+    }
+    g->tables.push_back(t);
+  }
+  // Capture on the lead's own capture stream (the handles' stream may be the legacy default
+  // stream, which cannot be captured): the handles issue to it for the capture's duration,
+  // and the graph is then launched on their stream.  Each launch uploads its table from its
+  // pinned buffer, which the graph reads at every replay.
+  if (!lead->cap_stream &&
+      cudaStreamCreateWithFlags(&lead->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete g;
+    return nullptr;
+  }
+  std::vector<PipeTable<R>*> pins(nl);
+  for (int c = 0; c < nl; ++c) pins[c] = static_cast<PipeTable<R>*>(g->tables[c]);
+  std::vector<cudaStream_t> saved(nh);
+  for (int i = 0; i < nh; ++i) {
+    saved[i] = hs[i]->stream;
+    hs[i]->stream = lead->cap_stream;
+  }
+  cudaGraph_t graph = nullptr;
+  int failed = 0;
+  bool ok = cudaStreamBeginCapture(lead->cap_stream, cudaStreamCaptureModeThreadLocal) ==
+            cudaSuccess;
+  if (ok) {
+    ok = issue_batch_step<R>(hs, nh, nbr, nbc, pins.data(), &failed) == QSA_OK;
+    const cudaError_t e = cudaStreamEndCapture(lead->cap_stream, &graph);
+    ok = ok && e == cudaSuccess && graph != nullptr;
+  }
+  for (int i = 0; i < nh; ++i) hs[i]->stream = saved[i];
+  if (ok) ok = cudaGraphInstantiate(&g->exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {
+    cudaGetLastError();  // a capture that failed leaves no error behind for later calls
+    for (int i = 0; i < nh; ++i) hs[i]->err.clear();
+    delete g;
+    return nullptr;
+  }
+  lead->graphs.push_back(g);
+  return g;
+}
+
+
 // n_steps steps of every handle, each launch advancing up to kMaxPipe handles by one step.
 // With n_steps >= 2 x (shapes) and no earlier choice, the first steps time each FFT unit
 // shape on the real work (every shape computes the same steps) and the rest use the fastest.
+// After those, each step runs as a CUDA graph (captured once per distinct step, see
+// batch_graph) unless graphs are off for the lead or a capture failed.
 template <typename R>
 int advance_batch(qsa_handle* const* hs, int nh, int n_steps) {
   qsa_handle* lead = hs[0];
@@ -727,45 +880,39 @@ int advance_batch(qsa_handle* const* hs, int nh, int n_steps) {
   for (int i = 0; i < nh; ++i)
     if (!hs[i]->src_valid)
       if (int rc = deposit_sources<R>(hs[i])) return relay(rc, i);
-  std::vector<PipeTable<R>> tv(1);
-  PipeTable<R>& t = tv[0];
+  const int nl = (nh + kMaxPipe - 1) / kMaxPipe;
+  std::vector<PipeTable<R>> tv(nl);  // ~33 KB each: on the heap
   const int nshape = 4;
   const bool tune = ls->tuned_nbr == 0 && n_steps >= 2 * nshape;
   std::vector<float> shape_ms(nshape, 0.f);
   for (int step = 0; step < n_steps; ++step) {
     int nbr = ls->tuned_nbr ? ls->tuned_nbr : kPipeRowBatch;
     int nbc = ls->tuned_nbc ? ls->tuned_nbc : kPipeColBatch;
-    if (tune && step < nshape) {
+    const bool timing = tune && step < nshape;
+    if (timing) {
       nbr = kTuneShapes[step][0];
       nbc = kTuneShapes[step][1];
       lead->n_timed = 0;
     }
-    for (int c0 = 0; c0 < nh; c0 += kMaxPipe) {
-      const int m = std::min(kMaxPipe, nh - c0);
-      t = PipeTable<R>{};
-      t.chained = 0;
-      for (int i = 0; i < m; ++i) {
-        qsa_handle* h = hs[c0 + i];
-        SweepArgs<R>& a = S<R>(h)->slots[0];
-        if (int rc = prepare_slot<R>(h, a, h->pushes)) return relay(rc, c0 + i);
-        t.st[i] = a;
-        t.st[i].src = ring_src<R>(h, h->pushes);
-        t.slot[i] = make_slot<R>(h, h->pushes);
-      }
-      int grid = 0;
-      if (int rc = launch_slots<R>(lead, t, m, nbr, nbc, &grid)) return rc;
-      for (int i = 0; i < m; ++i) {
-        qsa_handle* h = hs[c0 + i];
-        SweepArgs<R>& a = S<R>(h)->slots[0];
-        diag_reduce_kernel<<<h->dp.nk, 256, 0, h->stream>>>(a.dpart, grid, a.diag, h->dp.nk);
-        ++h->launches;
-        h->pushes += 1;
-        h->sweeps += 1;
-        S<R>(h)->last_slot = 0;
-        h->src_valid = true;
-      }
+    // graphs once the lazy set-up of the launches (slot table, events) exists
+    BatchGraph* g = nullptr;
+    if (!timing && lead->batch_graphs && !lead->graphs_failed && ls->ptab && lead->ev[0]) {
+      g = batch_graph<R>(hs, nh, nbr, nbc);
+      if (!g) lead->graphs_failed = true;
     }
-    if (tune && step < nshape) {
+    if (g) {
+      qsa_handle* h = lead;  // error reporting of CK
+      CK(cudaGraphLaunch(g->exec, lead->stream));
+      ++lead->graph_replays;
+    } else {
+      std::vector<PipeTable<R>*> tp(nl);
+      for (int c = 0; c < nl; ++c) tp[c] = &tv[c];
+      int failed = 0;
+      if (int rc = issue_batch_step<R>(hs, nh, nbr, nbc, tp.data(), &failed))
+        return relay(rc, failed);
+    }
+    finish_batch_step<R>(hs, nh);
+    if (timing) {
       qsa_handle* h = lead;  // error reporting of CK
       float tot = 0.f, ms = 0.f;
       for (int i = 0; i < lead->n_timed; ++i) {
@@ -1429,6 +1576,8 @@ int qsa_init(const qsa_params* params, void* stream, qsa_alloc_fn alloc, qsa_fre
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(nullptr, QSA_ERR_CUDA, cudaGetErrorString(e));
   qsa_handle* h = new qsa_handle();
+  static std::atomic<uint64_t> next_serial{1};
+  h->serial = next_serial++;
   h->prm = *params;
   h->stream = (cudaStream_t)stream;
   h->alloc = alloc;
@@ -1571,6 +1720,20 @@ int qsa_advance_batch(qsa_handle* const* handles, int32_t n_handles, int32_t n_s
                     : advance_batch<float>(handles, n_handles, n_steps);
 }
 
+int qsa_batch_graphs(qsa_handle* lead, int32_t enable, int64_t* replays) {
+  NvtxRange nvtx_range("qsa_batch_graphs");
+  if (!lead) return fail(nullptr, QSA_ERR_ARG, "NULL handle");
+  if (enable > 0) {
+    lead->batch_graphs = true;
+    lead->graphs_failed = false;
+  } else if (enable == 0) {
+    lead->batch_graphs = false;
+  }
+  if (replays) *replays = lead->batch_graphs && !lead->graphs_failed ? lead->graph_replays
+                                                                      : -1 - lead->graph_replays;
+  return QSA_OK;
+}
+
 int qsa_diagnostics(qsa_handle* h, qsa_diag* out) {
   NvtxRange nvtx_range("qsa_diagnostics");
   if (!h || !out) return QSA_ERR_ARG;
@@ -1707,6 +1870,8 @@ void qsa_destroy(qsa_handle* h) {
   }
   for (int i = 0; i < 2 * qsa_handle::kLaunchEvents; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  for (BatchGraph* g : h->graphs) delete g;
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
 

@@ -35,7 +35,7 @@ EXPORTS = ("qsa_init", "qsa_set_beam", "qsa_get_beam", "qsa_plasma_sweep", "qsa_
            "qsa_phase_times", "qsa_launch_count", "qsa_device_bytes", "qsa_last_error",
            "qsa_destroy", "qsa_field_solve_static", "qsa_advance", "qsa_launch_times",
            "qsa_eq5_march", "qsa_advance_batch", "qsa_bounds_check", "qsa_grad_forward",
-           "qsa_grad_backward", "qsa_rehome", "qsa_rehome_count")
+           "qsa_grad_backward", "qsa_rehome", "qsa_rehome_count", "qsa_batch_graphs")
 
 
 class QsaError(RuntimeError):
@@ -118,6 +118,8 @@ def load_library(path: str = None):
     lib.qsa_advance.restype = ct.c_int
     lib.qsa_advance_batch.argtypes = [ct.POINTER(P), ct.c_int32, ct.c_int32]
     lib.qsa_advance_batch.restype = ct.c_int
+    lib.qsa_batch_graphs.argtypes = [P, ct.c_int32, ct.POINTER(ct.c_int64)]
+    lib.qsa_batch_graphs.restype = ct.c_int
     lib.qsa_bounds_check.argtypes = [ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int64)]
     lib.qsa_bounds_check.restype = ct.c_int
     lib.qsa_rehome.argtypes = [P]
@@ -233,6 +235,19 @@ def advance_batch(instances, n_steps: int):
     if rc < 0:
         raise QsaError(rc, lib.qsa_last_error(instances[0].h if instances else None).decode())
     return rc
+
+
+def batch_graphs(lead, enable=None) -> int:
+    """CUDA graphs of the batched steps led by QSA instance `lead` (qsa_batch_graphs):
+    enable True/False switches them, None leaves them; returns the steps run as graphs so far
+    (negative, -1 - that number, when graphs are off or a capture failed)."""
+    lib = load_library()
+    n = ct.c_int64(0)
+    e = -1 if enable is None else (1 if enable else 0)
+    rc = lib.qsa_batch_graphs(lead.h, e, ct.byref(n))
+    if rc < 0:
+        raise QsaError(rc, lib.qsa_last_error(lead.h).decode())
+    return int(n.value)
 
 
 class QSA:

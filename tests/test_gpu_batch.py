@@ -154,3 +154,44 @@ def test_batch_instances_match_the_oracle(qsa_mod, prec):
             e = np.mod(gb[key][live] - rb[0][key][live] + 0.5 * L, L) - 0.5 * L
             assert np.abs(e).max() <= tol * d, key
         q.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_graphs_match_direct_launches(qsa_mod, prec):
+    """The batched steps replayed as CUDA graphs (qsa_batch_graphs; 18 instances, so two
+    launches per step, over five steps, so both ring phases of the sources are captured and
+    replayed) against the same steps launched directly: the same fields, beams and
+    diagnostics to rounding, and the graphs really ran.  The same kernels run in the same
+    order; only the order of the atomic sums differs between any two runs: FP64 keeps that
+    below 1e-12 of a field's scale over these steps (the check of the graph machinery),
+    while FP32 sums, amplified by the growing modes, reach ~1e-5 after the last sweep and
+    are held to the mixed path's tolerance."""
+    ps = instances(18, prec)
+    runs = []
+    for graphs in (False, True):
+        qs = []
+        for p in ps:
+            q = qsa_mod.QSA(p)
+            q.set_beam(0, inputs.all_beams(p)[0])
+            qs.append(q)
+        qsa_mod.batch_graphs(qs[0], graphs)
+        qsa_mod.advance_batch(qs, 5)
+        n = qsa_mod.batch_graphs(qs[0])
+        if graphs:
+            assert n == 4, n  # the first step launches directly (it sets the launches up)
+        else:
+            assert n == -1, n
+        runs.append(qs)
+    tol = 1e-12 if prec == "fp64" else TOL["mixed"]
+    for a, b, p in zip(runs[0], runs[1], ps):
+        da, db = a.diagnostics(), b.diagnostics()
+        assert da["sweeps"] == db["sweeps"] == 5 and da["beam_lost"] == db["beam_lost"]
+        assert field_err(b.slab(), a.slab()).max() <= tol
+        n = inputs.all_beams(p)[0]["x"].size
+        ga, gb = a.get_beam(0, n), b.get_beam(0, n)
+        for key in ("x", "y", "xi", "ux", "uy", "uz"):
+            scale = max(np.abs(ga[key]).max(), 1e-300)
+            assert np.abs(ga[key] - gb[key]).max() <= tol * scale, key
+        a.sweep()
+        b.sweep()
+        assert field_err(b.slab(), a.slab()).max() <= tol
