@@ -530,7 +530,7 @@ def batched(steps, torch, stream, hbm_peak):
     instances (8 + 42: the scan's 50).  Same metric: plasma particle-slice updates of all
     instances per second.  Roofline of the batched launches: the algorithmic bytes of the
     sweeps and pushes of their instances over the mean launch time (CUDA events)."""
-    from paper_2607_24214_b300.qsa import QSA, advance_batch
+    from paper_2607_24214_b300.qsa import QSA, advance_batch, batch_graphs
     ps = config.c4_parameter_scan()
     qs = [QSA(pi) for pi in ps]
     advance_batch(qs, 8)
@@ -543,6 +543,7 @@ def batched(steps, torch, stream, hbm_peak):
     t1.synchronize()
     ms = t0.elapsed_time(t1)
     lt = qs[0].launch_times()   # the launches of the last call (up to 64)
+    replays = batch_graphs(qs[0])  # steps run as CUDA graphs so far
     status = min(q.diagnostics()["status"] for q in qs)
     for q in qs:
         q.close()
@@ -556,7 +557,7 @@ def batched(steps, torch, stream, hbm_peak):
     out = {"workload": "c4_parameter_scan_64", "value": ups * steps / (ms * 1e-3),
            "unit": "updates/s", "instances": len(ps), "steps": steps, "untimed_steps": 8,
            "ms_per_step": ms / steps, "grids": sorted({pi.nx for pi in ps}),
-           "status": status}
+           "graph_replays": replays, "status": status}
     if len(lt):
         launch_ms = float(np.mean(lt))
         achieved = step_bytes / per_step / (launch_ms * 1e-3) / 1e9

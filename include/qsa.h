@@ -236,8 +236,8 @@ int qsa_advance_batch(qsa_handle* const* handles, int32_t n_handles, int32_t n_s
  * results are those of the direct launches.  enable: 1 on (the default; also retries after
  * a failed capture), 0 off, < 0 unchanged.  replays (optional): the number of steps run as
  * graphs so far, or -1 - that number when graphs are off or a capture failed.  With graphs,
- * qsa_launch_times reports the launches of the last direct step and of the captured steps'
- * latest replays. */
+ * qsa_launch_times reports the launches of the captured steps' latest replays (and of the
+ * call's direct steps). */
 int qsa_batch_graphs(qsa_handle* lead, int32_t enable, int64_t* replays);
 
 /* Tracing (the paper has no counterpart).

@@ -84,6 +84,7 @@ struct BatchGraph {
   std::vector<uint64_t> serials;
   std::vector<int64_t> phases;
   int nbr = 0, nbc = 0;
+  int ev_end = 0;  // the launch events it records: the lead's ev[0 .. 2 ev_end) at most
   cudaGraphExec_t exec = nullptr;
   std::vector<void*> tables;
   ~BatchGraph() {
@@ -584,13 +585,18 @@ int launch_slots(qsa_handle* lead, PipeTable<R>& t, int nslots, int nbr, int nbc
   Barrier bar = s->slots[0].bar;
   CK(cudaMemsetAsync(bar.count, 0, sizeof(unsigned), h->stream));
   const int ti = h->n_timed < qsa_handle::kLaunchEvents ? h->n_timed++ : -1;
-  if (ti >= 0) CK(cudaEventRecord(h->ev[2 * ti], h->stream));
+  // under stream capture (a batched step becoming a CUDA graph) the events become event-record
+  // nodes of the graph, re-recorded at every replay
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(h->stream, &cap));
+  const unsigned evf = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+  if (ti >= 0) CK(cudaEventRecordWithFlags(h->ev[2 * ti], h->stream, evf));
   const PipeTable<R>* tab = s->ptab;
   void* args[] = {&tab, &nslots, &bar};
   CK(cudaLaunchCooperativeKernel((void*)pipe_kernel<R>, dim3(grid), dim3(kThreads), args, smem,
                                  h->stream));
   ++h->launches;
-  if (ti >= 0) CK(cudaEventRecord(h->ev[2 * ti + 1], h->stream));
+  if (ti >= 0) CK(cudaEventRecordWithFlags(h->ev[2 * ti + 1], h->stream, evf));
   *grid_out = grid;
   return QSA_OK;
 }
@@ -846,6 +852,7 @@ BatchGraph* batch_graph(qsa_handle* const* hs, int nh, int nbr, int nbc) {
             cudaSuccess;
   if (ok) {
     ok = issue_batch_step<R>(hs, nh, nbr, nbc, pins.data(), &failed) == QSA_OK;
+    g->ev_end = lead->n_timed;
     const cudaError_t e = cudaStreamEndCapture(lead->cap_stream, &graph);
     ok = ok && e == cudaSuccess && graph != nullptr;
   }
@@ -904,6 +911,8 @@ int advance_batch(qsa_handle* const* hs, int nh, int n_steps) {
       qsa_handle* h = lead;  // error reporting of CK
       CK(cudaGraphLaunch(g->exec, lead->stream));
       ++lead->graph_replays;
+      // its launch events, re-recorded by this replay, count for qsa_launch_times
+      lead->n_timed = std::max(lead->n_timed, g->ev_end);
     } else {
       std::vector<PipeTable<R>*> tp(nl);
       for (int c = 0; c < nl; ++c) tp[c] = &tv[c];

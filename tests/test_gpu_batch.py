@@ -179,6 +179,8 @@ def test_batch_graphs_match_direct_launches(qsa_mod, prec):
         n = qsa_mod.batch_graphs(qs[0])
         if graphs:
             assert n == 4, n  # the first step launches directly (it sets the launches up)
+            lt = qs[0].launch_times()  # the replays' launches, timed by their own events
+            assert len(lt) >= 2 and np.all(np.asarray(lt) > 0), lt
         else:
             assert n == -1, n
         runs.append(qs)
