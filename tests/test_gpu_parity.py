@@ -46,7 +46,7 @@ def gpu(Q, p, beams=None):
 # ------------------------------------------------------------------ transverse solves
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("nx,ny", [(32, 32), (9, 12), (1, 64), (96, 48), (256, 256), (256, 36),
-                                   (36, 256)])
+                                   (36, 256), (1, 256)])
 def test_field_solve(Q, prec, nx, ny):
     p = config.Params(nx=nx, ny=ny, nxi=4, Lx=0.3 * nx, Ly=0.25 * ny, Lxi=1.0, dt=1.0,
                       precision=prec)
@@ -181,6 +181,13 @@ def _warp_grid(geom, **kw):
 @pytest.mark.parametrize("geom", sorted(WARP_GRIDS))
 def test_sweep_warp_paths_mixed(Q, geom):
     _sweep_parity(Q, _warp_grid(geom), TOL["mixed"])
+
+
+def test_sweep_2d3v_256_mixed(Q):
+    """The paper's 2D3V geometry (nx = 1) on 256 rows: per-warp column transforms of a single
+    half-spectrum column, block row transforms of one point."""
+    _sweep_parity(Q, config.v_pair_single_mode(ny=256, Lxi=4.0, precision="mixed"),
+                  TOL["mixed"])
 
 
 @pytest.mark.parametrize("geom", sorted(WARP_GRIDS))
