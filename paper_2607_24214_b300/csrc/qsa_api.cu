@@ -377,6 +377,7 @@ int setup(qsa_handle* h) {
     {
       const double uzb = std::sqrt(q.gamma_b * q.gamma_b - 1.0);
       sp.omvbar = 1.0 / (q.gamma_b * (q.gamma_b + uzb));
+      sp.uzb = uzb;
     }
     BeamArrays<R> b{};
     b.n = (long long)dp.nx * dp.ny * sp.nkb * sp.ppc;
@@ -384,9 +385,8 @@ int setup(qsa_handle* h) {
     if (!(b.ox = (R*)A(n * sizeof(R))) || !(b.oy = (R*)A(n * sizeof(R))) ||
         !(b.oxi = (R*)A(n * sizeof(R))) || !(b.ux = (R*)A(n * sizeof(R))) ||
         !(b.uy = (R*)A(n * sizeof(R))) || !(b.dw = (R*)A(n * sizeof(R))) ||
-        !(b.uz = (typename UzT<R>::T*)A(n * sizeof(typename UzT<R>::T))) ||
-        !(b.id = (unsigned*)A(n * sizeof(unsigned))))
-      return fail(h, QSA_ERR_OOM, "beam arrays");
+        !(b.uz = (typename UzT<R>::T*)A(n * sizeof(typename UzT<R>::T))))
+      return fail(h, QSA_ERR_OOM, "beam arrays");  // the ids come with the first re-homing
     s->species.push_back(sp);
     s->bconst.push_back(beam_consts<R>(dp, sp));
     s->beams.push_back(b);
@@ -645,9 +645,17 @@ int rehome(qsa_handle* h) {
     s->rh_layers = nl;
   }
   for (size_t si = 0; si < s->beams.size(); ++si) {
-    const BeamArrays<R>& b = s->beams[si];
+    BeamArrays<R>& b = s->beams[si];
     const SpeciesDev& sp = s->species[si];
     if (b.n == 0) continue;
+    if (!b.id) {  // every slot holds its own particle until now
+      if (!(b.id = (unsigned*)dalloc(h, (size_t)b.n * sizeof(unsigned))))
+        return fail(h, QSA_ERR_OOM, "beam ids");
+      const unsigned blocks = (unsigned)((b.n + kThreads - 1) / kThreads);
+      beam_id_init_kernel<R><<<blocks, kThreads, 0, h->stream>>>(b, dp, sp);
+      ++h->launches;
+      CK(cudaGetLastError());
+    }
     const long long Ls = (long long)ncell * sp.ppc;
     for (int k0 = 0; k0 < sp.nkb; k0 += s->rh_layers) {
       const int nl = std::min(s->rh_layers, sp.nkb - k0);

@@ -6,9 +6,12 @@
 // neighbouring cells of one sub-lattice position).  Positions are offsets, in cells, from
 // the particle's lattice home; this keeps the slow transverse and longitudinal drifts of an
 // ultrarelativistic beam (1e-6 cells per step) exact in FP32.  u_z is FP64 in the FP64 path
-// and a double-float pair (leading float + trailing float, about 48 significant bits) in the
-// mixed path: the per-step increments of u_z are 1e-6 of it, too small for one float, and the
-// pair keeps them with FP32 instructions only.
+// and, in the mixed path, one float holding its deviation u_z - u_zb from the species'
+// reference momentum u_zb = sqrt(gamma_b^2 - 1): the per-step increments of u_z are ~1e-6 of
+// it, too small for a float of u_z itself, but the deviation is the energy spread (a few
+// percent of u_zb at most), whose float resolves them.  A mixed-path particle is 28 bytes:
+// three offsets, u_x, u_y, the u_z deviation and the weight deviation; the slot's canonical
+// id (4 bytes more) is only kept once the beam has been re-homed.
 // The weight is stored as its relative deviation dw = w / wbar - 1 from the species' nominal
 // weight wbar = alpha dx dy dxi / ppc (dw = -1 marks a lost particle), and the beam sources
 // are deposited as deviations from the reference beam (nominal weight, at home, u = (0, 0,
@@ -21,28 +24,28 @@
 
 namespace qsa {
 
-// Storage type of u_z: FP64, or a (leading, trailing) float pair in the mixed path.
+// Storage type of u_z: FP64 (u_z itself), or in the mixed path a float of u_z - u_zb.
 template <typename BR>
 struct UzT {
   using T = double;
 };
 template <>
 struct UzT<float> {
-  using T = float2;
+  using T = float;
 };
-__host__ __device__ __forceinline__ double uz_value(double v) { return v; }
-__host__ __device__ __forceinline__ double uz_value(float2 v) { return (double)v.x + (double)v.y; }
-__host__ __device__ __forceinline__ void uz_store(double& d, double v) { d = v; }
-__host__ __device__ __forceinline__ void uz_store(float2& d, double v) {
-  const float hi = (float)v;
-  d = make_float2(hi, (float)(v - (double)hi));
+// Stored u_z <-> its value, with uzb = sqrt(gamma_b^2 - 1) of the species (FP64).
+__host__ __device__ __forceinline__ double uz_value(double v, double) { return v; }
+__host__ __device__ __forceinline__ double uz_value(float v, double uzb) {
+  return uzb + (double)v;
 }
-// Leading part (the value for the derived quantities gamma, 1 - v_z).
-__device__ __forceinline__ double uz_lead(double v) { return v; }
-__device__ __forceinline__ float uz_lead(float2 v) { return v.x; }
+__host__ __device__ __forceinline__ void uz_store(double& d, double v, double) { d = v; }
+__host__ __device__ __forceinline__ void uz_store(float& d, double v, double uzb) {
+  d = (float)(v - uzb);
+}
 
-// id[s]: the canonical id of the particle slot s holds (the slot's own id until the beam is
-// re-homed, see rehome_*), so that host copies keep every particle's identity.
+// id[s]: the canonical id of the particle slot s holds (see rehome_*), so that host copies
+// keep every particle's identity; null until the beam is first re-homed (every slot then
+// holds its own particle).
 template <typename BR>
 struct BeamArrays {
   BR *ox, *oy, *oxi, *ux, *uy, *dw;
@@ -56,6 +59,7 @@ struct SpeciesDev {
   double wbar;   // nominal weight alpha dx dy dxi / ppc
   double qbar;   // Z wbar / (dx dy dxi): reference density per particle
   double omvbar; // 1 - v_z of the reference momentum
+  double uzb;    // reference momentum sqrt(gamma_b^2 - 1)
   int ppx, ppy, ppxi, ppc;
   int k0, nkb;  // first xi cell and number of xi cells
   int seeded, index;
@@ -155,9 +159,9 @@ __global__ void beam_init_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp, M
   b.oxi[s] = BR(0);
   b.ux[s] = BR(ux);
   b.uy[s] = BR(uy);
-  uz_store(b.uz[s], sqrt(gam * gam - 1.0 - ux * ux - uy * uy));
+  uz_store(b.uz[s], sqrt(gam * gam - 1.0 - ux * ux - uy * uy), sp.uzb);
   b.dw[s] = BR(dw);
-  b.id[s] = (unsigned)h.id;
+  if (b.id) b.id[s] = (unsigned)h.id;
 }
 
 // ------------------------------------------------------------------ deposit and push
@@ -405,15 +409,16 @@ __device__ __forceinline__ void boris(double& ux, double& uy, double& uz, const 
   uz = mz + (px * sy - py * sx) + h * Ez;
 }
 
-// The same Boris step with FP32 arithmetic and double-float u_z accumulation, written so that
-// no step subtracts nearly equal terms: with W = E_perp - z x B (the slab's first two fields),
-// E_x - v_z B_y = W_x + (1 - v_z) B_y, and 1 - v_z is formed from gamma - u_z =
-// (1 + u_perp^2)/(gamma + u_z).
-__device__ __forceinline__ void boris(float& ux, float& uy, float2& uz, const float F[6],
-                                      float h) {
+// The same Boris step with FP32 arithmetic, u_z kept as its deviation duz = u_z - u_zb (a
+// float of the energy spread resolves the small per-step increments that a float of u_z
+// would round away), written so that no step subtracts nearly equal terms: with W = E_perp -
+// z x B (the slab's first two fields), E_x - v_z B_y = W_x + (1 - v_z) B_y, and 1 - v_z is
+// formed from gamma - u_z = (1 + u_perp^2)/(gamma + u_z).  uzb: u_zb in FP32.
+__device__ __forceinline__ void boris(float& ux, float& uy, float& duz, const float F[6],
+                                      float h, float uzb) {
   const float Wx = F[0], Wy = F[1], Ez = F[2], Bx = F[3], By = F[4], Bz = F[5];
   const float mx = ux + h * (Wx + By), my = uy + h * (Wy - Bx);
-  const float mzf = uz.x + h * Ez;
+  const float mzf = (uzb + duz) + h * Ez;
   const float mp2 = mx * mx + my * my;
   const float gm = fast_sqrt(1.0f + mp2 + mzf * mzf);
   const float dm = fast_div(1.0f + mp2, gm + mzf);  // gamma^- - m_z
@@ -430,15 +435,7 @@ __device__ __forceinline__ void boris(float& ux, float& uy, float2& uz, const fl
   const float eps = (dm + gm * t2 - (mx * ty - my * tx)) * ig * i1t2;
   ux = ux + 2.0f * h * Wx + 2.0f * h * By * eps + pyp * sz;
   uy = uy + 2.0f * h * Wy - 2.0f * h * Bx * eps - pxp * sz;
-  // u_z += du in double-float: Knuth's two-sum of the leading part and du, its rounding error
-  // carried into the trailing part, then renormalised (|trailing| <= ulp(leading) / 2)
-  const float du = 2.0f * h * Ez + pxp * sy - pyp * sx;
-  const float sum = uz.x + du;
-  const float bv = sum - uz.x;
-  const float err = (uz.x - (sum - bv)) + (du - bv);
-  const float lo = uz.y + err;
-  const float hi = sum + lo;
-  uz = make_float2(hi, lo - (hi - sum));
+  duz += 2.0f * h * Ez + pxp * sy - pyp * sx;
 }
 
 template <typename BR>
@@ -497,12 +494,24 @@ struct Extent {
   unsigned long long* away;  // live particles outside their slot's cell after the push, or null
 };
 
-// u_z - sqrt(gamma_b^2 - 1) without cancellation of the leading parts
+// u_z - sqrt(gamma_b^2 - 1) (the stored deviation in the mixed path), and u_z (in FP32 there,
+// for the derived quantities gamma and 1 - v_z)
 __device__ __forceinline__ double uz_dev(double uz, const BeamConst<double>& c) {
   return uz - c.uzb_hi;
 }
-__device__ __forceinline__ float uz_dev(float2 uz, const BeamConst<float>& c) {
-  return (uz.x - c.uzb_hi) + (uz.y - c.uzb_lo);
+__device__ __forceinline__ float uz_dev(float duz, const BeamConst<float>&) { return duz; }
+__device__ __forceinline__ double uz_lead(double uz, const BeamConst<double>&) { return uz; }
+__device__ __forceinline__ float uz_lead(float duz, const BeamConst<float>& c) {
+  return c.uzb_hi + duz;
+}
+// the Boris step of either precision with the stored u_z
+__device__ __forceinline__ void boris_st(double& ux, double& uy, double& uz, const double F[6],
+                                         const BeamConst<double>& c) {
+  boris(ux, uy, uz, F, c.hdt);
+}
+__device__ __forceinline__ void boris_st(float& ux, float& uy, float& duz, const float F[6],
+                                         const BeamConst<float>& c) {
+  boris(ux, uy, duz, F, c.hdt, c.uzb_hi);
 }
 
 // One group of a species: the ppc * nx particles whose home is xi cell (layer) k and row iy.
@@ -540,7 +549,6 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
   const bool lane_agg = (nx % 32 == 0) && (blockDim.x % 32 == 0);
   const size_t base = (size_t)grp * sp.ppc * nx;
   const BR refS = bc.refS, refJz = bc.refJz;
-  const BR hdt = bc.hdt;
   const BR cdx = bc.cdx, cdy = bc.cdy, cdk = bc.cdk;
   const int kleft = p.nxi - g.kabs;  // lost when the local xi position reaches this
   int my_lost = 0, my_away = 0;
@@ -614,10 +622,10 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
           continue;
         }
         if (PUSH) {
-          boris(ux[u], uy[u], uz[u], F[u], hdt);
+          boris_st(ux[u], uy[u], uz[u], F[u], bc);
           // dx/dt = u/gamma, dxi/dt = 1 - v_z = (1 + u_perp^2)/(gamma (gamma + u_z))
           BR ig, omv;
-          drift_rates(ux[u], uy[u], uz_lead(uz[u]), ig, omv);
+          drift_rates(ux[u], uy[u], uz_lead(uz[u], bc), ig, omv);
           ox[u] += cdx * ux[u] * ig;
           oy[u] += cdy * uy[u] * ig;
           oxi[u] += cdk * omv;
@@ -657,7 +665,7 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
             }
           }
         }
-        beam_sources(ux[u], uy[u], uz_lead(uz[u]), uz_dev(uz[u], bc), dw[u], bc, dv[u][0],
+        beam_sources(ux[u], uy[u], uz_lead(uz[u], bc), uz_dev(uz[u], bc), dw[u], bc, dv[u][0],
                      dv[u][1], dv[u][2], dv[u][3]);
         dox[u] = ox[u];
         doy[u] = oy[u];
@@ -833,9 +841,9 @@ __global__ void beam_from_host_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev 
   b.oxi[s] = live ? BR(xi[id] / p.dxi - hk) : BR(0);
   b.ux[s] = BR(ux[id]);
   b.uy[s] = BR(uy[id]);
-  uz_store(b.uz[s], uz[id]);
+  uz_store(b.uz[s], uz[id], sp.uzb);
   b.dw[s] = (w[id] == 0.0) ? BR(-1) : BR(w[id] / sp.wbar - 1.0);
-  b.id[s] = (unsigned)id;
+  if (b.id) b.id[s] = (unsigned)id;
 }
 
 template <typename BR>
@@ -845,7 +853,8 @@ __global__ void beam_to_host_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp
   const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= b.n) return;
   const Home h = home_of(s, p.nx, p.ny, sp);
-  const long long id = b.id[s];  // the particle in slot s (slot s's own id unless re-homed)
+  // the particle in slot s (slot s's own until the beam has been re-homed)
+  const long long id = b.id ? (long long)b.id[s] : h.id;
   const double hx = h.ix + (h.sx + 0.5) / sp.ppx, hy = h.iy + (h.sy + 0.5) / sp.ppy;
   const double hk = sp.k0 + h.kxi + (h.sxi + 0.5) / sp.ppxi;
   double xx = (hx + (double)b.ox[s]) * p.dx, yy = (hy + (double)b.oy[s]) * p.dy;
@@ -856,7 +865,7 @@ __global__ void beam_to_host_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp
   xi[id] = (hk + (double)b.oxi[s]) * p.dxi;
   ux[id] = (double)b.ux[s];
   uy[id] = (double)b.uy[s];
-  uz[id] = uz_value(b.uz[s]);
+  uz[id] = uz_value(b.uz[s], sp.uzb);
   w[id] = (b.dw[s] == BR(-1)) ? 0.0 : sp.wbar * (1.0 + (double)b.dw[s]);
 }
 

@@ -25,6 +25,14 @@ namespace qsa {
 
 constexpr int kRehomeThreads = 1024;
 
+// Canonical ids of a beam that has not been re-homed yet: every slot its own particle.
+template <typename BR>
+__global__ void beam_id_init_kernel(BeamArrays<BR> b, DevParams p, SpeciesDev sp) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= b.n) return;
+  b.id[s] = (unsigned)home_of(s, p.nx, p.ny, sp).id;
+}
+
 // Cell (within the layer) of every particle of layers [k0, k0 + nl), and the particle count of
 // each cell; lost particles are counted apart (key -1).
 template <typename BR>
