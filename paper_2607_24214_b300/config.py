@@ -115,8 +115,10 @@ def c2_mixed_electron_beam() -> Params:
 
 def c3_pair_beam(ppc_xi: int = 1) -> Params:
     """Pair beam, 512x512 (box 32 pi), 2048 slices over 128; alpha 1e-4 per species, gamma_b
-    1e4 with 1% energy spread; dt 200, 400 steps.  8 beam ppc per species do not fit next to
-    the slabs in one GPU's memory with 32 B per particle, so the default is 2x2x1 = 4 ppc."""
+    1e4 with 1% energy spread; dt 200, 400 steps.  ppc_xi = 2 gives the workload's 2x2x2 = 8
+    beam ppc per species (8.6e9 particles at 28 B: 275 GB on the device, which fits at
+    pipeline depth 1 only); the default 2x2x1 = 4 leaves room for deeper pipelines and the
+    diagnostics of the long run."""
     L = 512 * DX_DEFAULT
     sp = dict(alpha=1e-4, gamma_b=1e4, gamma_spread_rel=1e-2, noise_rel=1e-4, ppc_xi=ppc_xi)
     return Params(nx=512, ny=512, nxi=2048, Lx=L, Ly=L, Lxi=128.0, dt=200.0,
