@@ -437,7 +437,7 @@ def main():
                        "ppc_plasma": 4, "ppc_beam": 8, "beam_particles": 8 * p.nx * p.ny * p.nxi,
                        "n_pc_iter": p.n_pc_iter, "precision": "mixed",
                        "pipeline_depth": args.depth,
-                       "l2": "inputs larger than L2 (17 GB beam state)",
+                       "l2": "inputs larger than L2 (15 GB beam state)",
                        "parallelism": f"replicas{world}"},
             "gpu_launches": launches, "roofline": roof,
             "clocks": clk.summary(), "status": d["status"]}
