@@ -468,7 +468,7 @@ def main():
 
     if not args.no_c3:
         line["pair_beam"] = pair_beam(torch, stream)
-        line["pair_beam_8ppc"] = pair_beam(torch, stream, steps=3, depth=1, ppc_xi=2)
+        line["pair_beam_8ppc"] = pair_beam(torch, stream, steps=3, ppc_xi=2)
 
     if not args.no_adjoint:
         line["adjoint"] = adjoint_cost(torch, stream)
@@ -494,12 +494,13 @@ def main():
         dist.destroy_process_group()
 
 
-def pair_beam(torch, stream, steps=6, depth=3, ppc_xi=1):
+def pair_beam(torch, stream, steps=6, depth=1, ppc_xi=1, warmup=3):
     """The full-size pair-beam workload (512 x 512, 2048 slices, electrons and positrons):
-    `steps` timed beam steps after `depth` untimed ones (the linear stage).  Same metric.
-    ppc_xi = 1: 4 beam ppc per species (4.3e9 beam particles, 224 GB on the device at depth
-    3); ppc_xi = 2: the workload's 8 per species (8.6e9 particles, 28 bytes each, 275 GB at
-    depth 1, the depth that fits)."""
+    `steps` timed beam steps after `warmup` untimed ones (the linear stage).  Same metric.
+    ppc_xi = 1: 4 beam ppc per species (4.3e9 beam particles, 155 GB on the device); ppc_xi =
+    2: the workload's 8 per species (8.6e9 particles, 28 bytes each, 275 GB).  Depth 1: a
+    512^2 slice fills the GPU by itself, and deeper pipelines were slower (1.12-1.15 against
+    0.93 s per step at 4 ppc)."""
     from paper_2607_24214_b300.qsa import QSA
     p = config.c3_pair_beam(ppc_xi=ppc_xi).with_(pipeline_depth=depth)
     name = "c3_pair_beam_512x512_2048slices" + ("_8ppc" if ppc_xi == 2 else "")
@@ -509,7 +510,7 @@ def pair_beam(torch, stream, steps=6, depth=3, ppc_xi=1):
     except Exception as e:  # a device with less free memory than the workload needs
         return {"workload": name, "unavailable": str(e)[:200]}
     dev = q.device_bytes()
-    q.advance(depth)
+    q.advance(warmup)
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -524,7 +525,7 @@ def pair_beam(torch, stream, steps=6, depth=3, ppc_xi=1):
     torch.cuda.empty_cache()
     nb = sum(p.nx * p.ny * sp.ppc_x * sp.ppc_y * sp.ppc_xi * p.nxi for sp in p.species)
     return {"workload": name, "value": updates_per_step(p) * steps / (ms * 1e-3),
-            "unit": "updates/s", "steps": steps, "warmup": depth, "pipeline_depth": depth,
+            "unit": "updates/s", "steps": steps, "warmup": warmup, "pipeline_depth": depth,
             "ms_per_step": ms / steps, "beam_particles": nb, "device_bytes": dev,
             "status": st}
 

@@ -13,7 +13,7 @@ asymptotic exponents of Eqs. 7 and 6, the growth rate at the end of the run agai
 spatiotemporal rate, and the fractional field energy and transverse momentum spread beside
 the trapping estimates.
 
-    python -m paper_2607_24214_b300.nonlinear --steps 400 --every 6 --depth 3 --out run.npz
+    python -m paper_2607_24214_b300.nonlinear --steps 400 --every 6 --out run.npz
 """
 from __future__ import annotations
 
@@ -308,12 +308,15 @@ def main():
                          "driven to Gamma tau = 20, with the filament and wake reading")
     ap.add_argument("--steps", type=int, default=0, help="beam steps (0: the workload's)")
     ap.add_argument("--every", type=int, default=6)
-    ap.add_argument("--depth", type=int, default=3, help="beam steps in flight per launch")
+    ap.add_argument("--depth", type=int, default=0,
+                    help="beam steps in flight per launch (0: 1 for the 512^2 pair beam, whose "
+                         "slices fill the GPU alone, 16 for the 256^2 one)")
     ap.add_argument("--read-every", type=int, default=10)
     ap.add_argument("--out", default="nonlinear_run.npz")
     a = ap.parse_args()
+    depth = a.depth or (1 if a.workload == "c3" else 16)
     p = (config.c3_pair_beam() if a.workload == "c3" else
-         config.pair_beam_filaments()).with_(pipeline_depth=a.depth)
+         config.pair_beam_filaments()).with_(pipeline_depth=depth)
     steps = a.steps or p.steps
     read = filament_reading if a.workload == "filaments" else None
     rec = run(p, steps, a.every, log=lambda s: print(s, flush=True), read=read,
