@@ -244,6 +244,41 @@ def test_ten_steps_c1_fp64(Q):
     assert err.max() <= TOL["fp64"], err
 
 
+def test_mixed_uz_deviation_tracks_fp64(Q):
+    """The mixed path keeps u_z as one float of its deviation from u_zb.  A pair-beam-like
+    beam (gamma_b = 1e4, 1 % energy spread, dt = 200: a float of u_z itself has a spacing of
+    1e-3 there) over ten steps: the change of every live particle's u_z over the run agrees
+    with the FP64 path's to 1e-3 of the changes' scale (the mixed fields' 1e-4 acting on the
+    increments, not the storage), and that scale is hundreds of float spacings of u_z; u_x,
+    u_y within 1e-4 of their scale."""
+    base = config.c1_fp64_electron_beam().with_(nx=16, ny=16, Lx=3.2, Ly=3.2, nxi=16,
+                                                Lxi=2.0, dt=200.0)
+    base.species[0].gamma_b = 1e4
+    base.species[0].gamma_spread_rel = 1e-2
+    base.species[0].alpha = 1e-2
+    out = {}
+    for prec in ("fp64", "mixed"):
+        p = base.with_(precision=prec)
+        beams = inputs.all_beams(p)
+        q = gpu(Q, p, beams)
+        for _ in range(10):
+            q.sweep()
+            q.beam_step()
+        out[prec] = q.get_beam(0, beams[0]["x"].size)
+        q.close()
+    uz0 = inputs.all_beams(base)[0]["uz"]
+    a, b = out["fp64"], out["mixed"]
+    live = a["w"] != 0
+    assert np.array_equal(live, b["w"] != 0)
+    da, db = a["uz"][live] - uz0[live], b["uz"][live] - uz0[live]
+    scale = np.abs(da).max()
+    assert scale > 100 * np.spacing(np.float32(1e4)), scale
+    assert np.abs(db - da).max() <= 1e-3 * scale, (np.abs(db - da).max(), scale)
+    for k in ("ux", "uy"):
+        scale = np.abs(a[k][live]).max()
+        assert np.abs(b[k][live] - a[k][live]).max() <= 1e-4 * scale, k
+
+
 def test_lost_particles_exact(Q):
     """A slow beam (gamma_b = 2) slips back by dt/(2 gamma^2) per step: the particles that
     cross xi = Lxi are removed, the same ones as in the oracle."""
