@@ -73,7 +73,7 @@ struct BeamConst {
   BR cdx, cdy, cdk;  // dt/dx, dt/dy, dt/dxi
   BR refS, refJz;    // reference source weights qbar omvbar, qbar (1 - omvbar)
   BR qb, omvbar;     // qbar, 1 - v_z of the reference momentum
-  BR uzb_hi, uzb_lo; // sqrt(gamma_b^2 - 1) as a (leading, trailing) pair (trailing 0 in FP64)
+  BR uzb;            // sqrt(gamma_b^2 - 1), the reference momentum
   BR gamb, Db;       // gamma_b and gamma_b (gamma_b + u_zb) = 1 / omvbar
   BR inv_ppx, inv_ppy, inv_ppxi;  // 1 / sub-lattice counts
 };
@@ -91,8 +91,7 @@ inline BeamConst<BR> beam_consts(const DevParams& p, const SpeciesDev& sp) {
   c.gamb = BR(sp.gamma_b);
   c.Db = BR(1.0 / sp.omvbar);
   const double uzb = std::sqrt(sp.gamma_b * sp.gamma_b - 1.0);
-  c.uzb_hi = BR(uzb);
-  c.uzb_lo = BR(uzb - (double)c.uzb_hi);
+  c.uzb = BR(uzb);
   c.inv_ppx = BR(1.0 / sp.ppx);
   c.inv_ppy = BR(1.0 / sp.ppy);
   c.inv_ppxi = BR(1.0 / sp.ppxi);
@@ -323,7 +322,7 @@ __device__ __forceinline__ void beam_sources(float ux, float uy, float uzf, floa
   const float g = uzf + d;
   const float ig = fast_div(1.0f, g);
   const float omv = d * ig;                                              // 1 - v_z
-  const float s2 = up2 + duz * (uzf + c.uzb_hi);
+  const float s2 = up2 + duz * (uzf + c.uzb);
   const float dg = fast_div(s2, g + c.gamb);
   const float num = up2 * c.Db - s2 - dg * uzf - c.gamb * duz;
   const float domv = num * fast_div(1.0f, g * (g + uzf)) * c.omvbar;
@@ -497,12 +496,12 @@ struct Extent {
 // u_z - sqrt(gamma_b^2 - 1) (the stored deviation in the mixed path), and u_z (in FP32 there,
 // for the derived quantities gamma and 1 - v_z)
 __device__ __forceinline__ double uz_dev(double uz, const BeamConst<double>& c) {
-  return uz - c.uzb_hi;
+  return uz - c.uzb;
 }
 __device__ __forceinline__ float uz_dev(float duz, const BeamConst<float>&) { return duz; }
 __device__ __forceinline__ double uz_lead(double uz, const BeamConst<double>&) { return uz; }
 __device__ __forceinline__ float uz_lead(float duz, const BeamConst<float>& c) {
-  return c.uzb_hi + duz;
+  return c.uzb + duz;
 }
 // the Boris step of either precision with the stored u_z
 __device__ __forceinline__ void boris_st(double& ux, double& uy, double& uz, const double F[6],
@@ -511,7 +510,7 @@ __device__ __forceinline__ void boris_st(double& ux, double& uy, double& uz, con
 }
 __device__ __forceinline__ void boris_st(float& ux, float& uy, float& duz, const float F[6],
                                          const BeamConst<float>& c) {
-  boris(ux, uy, duz, F, c.hdt, c.uzb_hi);
+  boris(ux, uy, duz, F, c.hdt, c.uzb);
 }
 
 // One group of a species: the ppc * nx particles whose home is xi cell (layer) k and row iy.
