@@ -342,6 +342,19 @@ __device__ __forceinline__ void push_xi(R& ux, R& uy, R opp, R iopp, R gx, R gy,
 
 enum DepMode : int { DEP_INIT = 0, DEP_TRIAL = 1, DEP_COMMIT = 2 };
 
+// Shared-memory reduction *addr += v by the lanes whose pred holds, as one predicated
+// instruction (no branch around it).
+__device__ __forceinline__ void red_shared_if(bool pred, float* addr, float v) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(addr);
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.shared.add.f32 [%1], %2;\n\t}"
+               ::"r"((int)pred), "r"(sa), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_shared_if(bool pred, double* addr, double v) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(addr);
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.shared.add.f64 [%1], %2;\n\t}"
+               ::"r"((int)pred), "r"(sa), "d"(v) : "memory");
+}
+
 
 template <typename R>
 struct W4 {
@@ -404,6 +417,12 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
   // carries rho - J_z = -w and u_z/(1+psi) = c0 = -psi0 (2 + psi0) / (2 (1+psi0)^2); formed
   // in the working precision (psi0 is O(alpha), no cancellation)
   const DevParams& p = a.p;
+  // the fields the particle loop reads, held in registers (a reference into shared or global
+  // memory would be re-read after every store the compiler cannot separate from it)
+  const int ppc = p.ppc, ppx = p.ppx, np = p.np;
+  const R inv_ppx = a.k.inv_ppx, inv_ppy = a.k.inv_ppy;
+  const R* __restrict__ fgp = a.fg;
+  R* const ovf = a.ovf;
   const R psi0r = R(psi0);
   const R opp0 = R(1) + psi0r;
   const R iopp02 = R(1) / (opp0 * opp0);
@@ -412,7 +431,7 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
   const R dfloor = floor_ - opp0;  // psi fluctuation of a floored particle
   const int nx = p.nx, ny = p.ny;
   const int nf = (mode == DEP_TRIAL) ? kNF : 3;
-  const int per_chunk = p.ppc * nx;
+  const int per_chunk = ppc * nx;
   const R wn = a.k.wn;
   const R dxi = a.k.dxi;
   const R idx = a.k.idx, idy = a.k.idy;
@@ -458,10 +477,10 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
     for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) tile[e] = R(0);
     if (threadIdx.x == 0) s_flag = 0;
     __syncthreads();
-    const size_t base = (size_t)crow * per_chunk;
+    const int base = crow * per_chunk;  // particle indices fit in int (np < 2^31)
     if (mode == DEP_INIT) {  // at home: rho - J_z equals its reference, nothing to add
       for (int t = threadIdx.x; t < per_chunk; t += blockDim.x) {
-        const size_t i = base + t;
+        const int i = base + t;
         pox[i] = R(0);
         poy[i] = R(0);
         pux[i] = R(0);
@@ -471,27 +490,27 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
     } else {
       // two sub-lattice positions per thread per pass, (sub0, ix) and (sub0 + 1, ix): the
       // loads and gathers of both are issued before either particle's arithmetic
-      for (int sub0 = 0; sub0 < p.ppc; sub0 += 2) {
+      for (int sub0 = 0; sub0 < ppc; sub0 += 2) {
         R hx[2], hy[2];
         bool ok[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-          ok[u] = sub0 + u < p.ppc;
+          ok[u] = sub0 + u < ppc;
           const int sub = ok[u] ? sub0 + u : sub0;
           // sub = sy ppx + sx, split with an exact float quotient of small integers
-          const int sy = (int)((float(sub) + 0.5f) * float(a.k.inv_ppx));
-          hx[u] = (R(sub - sy * p.ppx) + R(0.5)) * a.k.inv_ppx;
-          hy[u] = (R(sy) + R(0.5)) * a.k.inv_ppy;
+          const int sy = (int)((float(sub) + 0.5f) * float(inv_ppx));
+          hx[u] = (R(sub - sy * ppx) + R(0.5)) * inv_ppx;
+          hy[u] = (R(sy) + R(0.5)) * inv_ppy;
         }
         for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
-          size_t ii[2];
+          int ii[2];
           R ox[2], oy[2], uxs[2], uys[2], pprev[2];
           Cic<R> c[2];
           R F[2][8];
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            ii[u] = base + (size_t)(ok[u] ? sub0 + u : sub0) * nx + ix;
-            if (!QSA_IN(ii[u] < (size_t)p.np)) ii[u] = 0;
+            ii[u] = base + (ok[u] ? sub0 + u : sub0) * nx + ix;
+            if (!QSA_IN(ii[u] >= 0 && ii[u] < np)) ii[u] = 0;
             ox[u] = pox[ii[u]];
             oy[u] = poy[ii[u]];
             uxs[u] = pux[ii[u]];
@@ -510,23 +529,23 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
 #pragma unroll
             for (int u = 0; u < 2; ++u)
               c[u] = Cic<R>{ix, gx1, crow, gy1, 1, hx[u] + ox[u], hy[u] + oy[u]};
-            gather8_pair(a.fg, ix, gx1, crow, gy1, nx, c, F);
+            gather8_pair(fgp, ix, gx1, crow, gy1, nx, c, F);
           } else {
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
               c[u] = cic<R>(ix, crow, hx[u] + ox[u], hy[u] + oy[u], nx, ny, crow);
-              gather8(a.fg, c[u], nx, F[u]);
+              gather8(fgp, c[u], nx, F[u]);
             }
           }
           // arithmetic of both particles; their deposit values are kept for the deposit step
           bool home[2] = {false, false}, homeh[2] = {false, false};
           R vx[2] = {0, 0}, vy[2] = {0, 0}, vdev[2] = {0, 0};
           R jhx[2] = {0, 0}, jhy[2] = {0, 0}, nox[2] = {0, 0}, noy[2] = {0, 0};
-          Cic<R> ch[2];
+          R lxh[2] = {0, 0}, lyh[2] = {0, 0};  // sub-cell position at x^{j+1/2}
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             if (!ok[u]) continue;
-            const size_t i = ii[u];
+            const int i = ii[u];
             R ux = uxs[u], uy = uys[u];
             const R psi_fl = F[u][FG_PSI];
             const R psi_p = psi0r + psi_fl;
@@ -540,9 +559,9 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
             push_xi(ux, uy, opp, iopp, F[u][FG_GX], F[u][FG_GY], F[u][FG_BX], F[u][FG_BY],
                     F[u][FG_BZ], dxi);
             const R sh = R(0.5) * dxi * ioph;
-            const R lxh = hx[u] + ox[u] + sh * ux * idx, lyh = hy[u] + oy[u] + sh * uy * idy;
-            ch[u] = cic<R>(ix, crow, lxh, lyh, nx, ny, crow);
-            homeh[u] = lxh >= R(0) && lxh < R(1) && lyh >= R(0) && lyh < R(1);
+            lxh[u] = hx[u] + ox[u] + sh * ux * idx;
+            lyh[u] = hy[u] + oy[u] + sh * uy * idy;
+            homeh[u] = lxh[u] >= R(0) && lxh[u] < R(1) && lyh[u] >= R(0) && lyh[u] < R(1);
             jhx[u] = -wn * ux * ioph;
             jhy[u] = -wn * uy * ioph;
             if (mode == DEP_TRIAL) {
@@ -601,8 +620,8 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
               for (int r = 0; r < 2; ++r) {
                 const R lft = r ? a10 : a00, rgt = r ? a11 : a01;
                 const R from = __shfl_up_sync(0xffffffffu, rgt, 1);
-                atomicAdd(r0 + (size_t)r * nx + ix, lft + (lane ? from : R(0)));
-                if (lane == 31) atomicAdd(r0 + (size_t)r * nx + x1, rgt);
+                atomicAdd(r0 + r * nx + ix, lft + (lane ? from : R(0)));
+                red_shared_if(lane == 31, r0 + r * nx + x1, rgt);
               }
             };
             W4<R> w[2], d[2], wh[2];
@@ -612,7 +631,7 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
                                   hy[u] + (mode == DEP_TRIAL ? oy[u] : noy[u])});
               d[u] = (mode == DEP_TRIAL) ? cic_dw(hx[u], hy[u], ox[u], oy[u])
                                          : cic_dw(hx[u], hy[u], nox[u], noy[u]);
-              wh[u] = cic_w(ch[u]);
+              wh[u] = cic_w(Cic<R>{0, 0, 0, 0, 0, lxh[u], lyh[u]});
             }
             const int fh = (mode == DEP_TRIAL) ? 3 : 1;
             if (mode == DEP_TRIAL) {
@@ -659,15 +678,17 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
                   atomicAdd(t0 + 2 * fs + nx + x1, w.w11 * vdev[u] + d.w11 * vref);
                 } else {
                   const R v3[3] = {vx[u], vy[u], vdev[u] + vref};
-                  deposit_n(tile, a.ovf, fl, c[u], w, 0, nx, ny, v3);
+                  deposit_n(tile, ovf, fl, c[u], w, 0, nx, ny, v3);
                   const Cic<R> hc = cic<R>(ix, crow, hx[u], hy[u], nx, ny, crow);
-                  deposit(tile, a.ovf, fl, hc, 2, nx, ny, -vref);
+                  deposit(tile, ovf, fl, hc, 2, nx, ny, -vref);
                 }
-                deposit_n(tile, a.ovf, fl, ch[u], cic_w(ch[u]), 3, nx, ny, jh);
+                const Cic<R> ch = cic<R>(ix, crow, lxh[u], lyh[u], nx, ny, crow);
+                deposit_n(tile, ovf, fl, ch, cic_w(ch), 3, nx, ny, jh);
               } else {
-                deposit_ref(tile, a.ovf, fl, ix, crow, hx[u], hy[u], nox[u], noy[u], 0, nx, ny,
+                deposit_ref(tile, ovf, fl, ix, crow, hx[u], hy[u], nox[u], noy[u], 0, nx, ny,
                             R(0), vref);
-                deposit_n(tile, a.ovf, fl, ch[u], cic_w(ch[u]), 1, nx, ny, jh);
+                const Cic<R> ch = cic<R>(ix, crow, lxh[u], lyh[u], nx, ny, crow);
+                deposit_n(tile, ovf, fl, ch, cic_w(ch), 1, nx, ny, jh);
               }
             }
           }
