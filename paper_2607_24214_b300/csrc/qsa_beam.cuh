@@ -533,7 +533,7 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
   g.kabs = sp.k0 + grp / p.ny;
   const int nx = p.nx;
   const int tn = 2 * 4 * nx * 4;
-  for (int e = threadIdx.x; e < tn; e += blockDim.x) g.tile[e] = BR(0);
+  zero_block(g.tile, tn);
   __shared__ double s_mom[7];
   if (threadIdx.x == 0) {
     s_ext[0] = -1;
@@ -708,7 +708,7 @@ __device__ void beam_group(const BeamArrays<BR> b, const DevParams& p, const Spe
             for (int q = 0; q < 4; ++q) {
               const BR from = __shfl_up_sync(0xffffffffu, acc[1][q], 1);
               atomicAdd(row + (size_t)q * nx + ix, acc[0][q] + (lane ? from : BR(0)));
-              if (lane == 31) atomicAdd(row + (size_t)q * nx + x1, acc[1][q]);
+              red_shared_if(lane == 31, row + (size_t)q * nx + x1, acc[1][q]);
             }
           }
         }

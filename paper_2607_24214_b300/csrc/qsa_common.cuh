@@ -343,6 +343,29 @@ __device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
   }
 }
 
+// Shared-memory reduction *addr += v by the lanes whose pred holds, as one predicated
+// instruction (no branch around it).
+__device__ __forceinline__ void red_shared_if(bool pred, float* addr, float v) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(addr);
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.shared.add.f32 [%1], %2;\n\t}"
+               ::"r"((int)pred), "r"(sa), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_shared_if(bool pred, double* addr, double v) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(addr);
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.shared.add.f64 [%1], %2;\n\t}"
+               ::"r"((int)pred), "r"(sa), "d"(v) : "memory");
+}
+
+// Zero n values at p (shared memory, 16-byte aligned) with 16-byte stores where they fit.
+// Called by all threads of the block.
+template <typename T>
+__device__ __forceinline__ void zero_block(T* p, int n) {
+  const int n4 = (int)((size_t)n * sizeof(T) / 16);
+  float4* q = reinterpret_cast<float4*>(p);
+  for (int e = threadIdx.x; e < n4; e += blockDim.x) q[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int e = (int)(n4 * 16 / sizeof(T)) + threadIdx.x; e < n; e += blockDim.x) p[e] = T(0);
+}
+
 // Periodic index: i mod n in [0, n), without a division when i is within one period.
 // Bounds checks of the debug build (-DQSA_DEBUG_BOUNDS, libqsa_bounds.so): QSA_IN(cond)
 // records the source line of the first failed check and the number of failures, and is

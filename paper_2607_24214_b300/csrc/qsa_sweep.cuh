@@ -342,18 +342,6 @@ __device__ __forceinline__ void push_xi(R& ux, R& uy, R opp, R iopp, R gx, R gy,
 
 enum DepMode : int { DEP_INIT = 0, DEP_TRIAL = 1, DEP_COMMIT = 2 };
 
-// Shared-memory reduction *addr += v by the lanes whose pred holds, as one predicated
-// instruction (no branch around it).
-__device__ __forceinline__ void red_shared_if(bool pred, float* addr, float v) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(addr);
-  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.shared.add.f32 [%1], %2;\n\t}"
-               ::"r"((int)pred), "r"(sa), "f"(v) : "memory");
-}
-__device__ __forceinline__ void red_shared_if(bool pred, double* addr, double v) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(addr);
-  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.shared.add.f64 [%1], %2;\n\t}"
-               ::"r"((int)pred), "r"(sa), "d"(v) : "memory");
-}
 
 
 template <typename R>
@@ -438,6 +426,13 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
   const int tile_elems = kTileRows * nx * nf;
   // the aggregated deposit needs whole warps over consecutive columns
   const bool lane_agg = (nx % 32 == 0) && (blockDim.x % 32 == 0);
+  // the tile goes out in 16-byte pieces when rows are whole quads (FP32) and the block's
+  // threads cover whole rows of quads
+  const int nx4 = nx >> 2;
+  const bool cp4 = sizeof(R) == 4 && (nx & 3) == 0 && nx4 <= (int)blockDim.x &&
+                   blockDim.x % nx4 == 0;
+  const int r0_t = cp4 ? (int)threadIdx.x / nx4 : 0, x4_t = cp4 ? (int)threadIdx.x % nx4 : 0;
+  const int rstep = cp4 ? (int)blockDim.x / nx4 : 1;
   // per-thread diagnostics accumulate in R; the block reductions below finish in FP64
   R kap = R(0), inv = R(0), omin = R(1e30), nfloor = R(0);
   __shared__ double red[32];
@@ -474,7 +469,7 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
         l2_prefetch(pps + b2, nbts);
       }
     }
-    for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) tile[e] = R(0);
+    zero_block(tile, tile_elems);
     if (threadIdx.x == 0) s_flag = 0;
     __syncthreads();
     const int base = crow * per_chunk;  // particle indices fit in int (np < 2^31)
@@ -701,11 +696,22 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
       // the outer tile rows go out only when a deposit landed there (the row phase reads
       // them only then)
       const int fl = s_flag;
-      for (int row = 0; row < nf * kTileRows; ++row) {
-        const int r = row & (kTileRows - 1);
-        if ((r == 0 && !(fl & 1)) || (r == kTileRows - 1 && !(fl & 2))) continue;
-        for (int x = threadIdx.x; x < nx; x += blockDim.x)
-          dst[(size_t)row * nx + x] = tile[(size_t)row * nx + x];
+      if (cp4) {
+        // 16-byte copies: thread t moves column quad t % nx4 of rows t / nx4 + k rstep
+        const float4* t4 = reinterpret_cast<const float4*>(tile);
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        for (int row = r0_t; row < nf * kTileRows; row += rstep) {
+          const int r = row & (kTileRows - 1);
+          if ((r == 0 && !(fl & 1)) || (r == kTileRows - 1 && !(fl & 2))) continue;
+          d4[row * nx4 + x4_t] = t4[row * nx4 + x4_t];
+        }
+      } else {
+        for (int row = 0; row < nf * kTileRows; ++row) {
+          const int r = row & (kTileRows - 1);
+          if ((r == 0 && !(fl & 1)) || (r == kTileRows - 1 && !(fl & 2))) continue;
+          for (int x = threadIdx.x; x < nx; x += blockDim.x)
+            dst[(size_t)row * nx + x] = tile[(size_t)row * nx + x];
+        }
       }
     }
     if (threadIdx.x == 0) a.cflag[crow] = s_flag;
