@@ -172,16 +172,6 @@ __device__ __forceinline__ Cic<R> cic(int ix, int iy, R lx, R ly, int nx, int ny
   return c;
 }
 
-// Bilinear gather of all components of the interleaved field grid.
-__device__ __forceinline__ void ld4(const float* p, float v[4]) {
-  const float4 q = *reinterpret_cast<const float4*>(p);
-  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-}
-__device__ __forceinline__ void ld4(const double* p, double v[4]) {
-  const double2 a = *reinterpret_cast<const double2*>(p);
-  const double2 b = *reinterpret_cast<const double2*>(p + 2);
-  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-}
 // Store one slab node (six fields and two zero pads) with 16-byte stores.
 __device__ __forceinline__ void st8(float* s, float a, float b, float c, float d, float e,
                                     float f) {
@@ -196,45 +186,53 @@ __device__ __forceinline__ void st8(double* s, double a, double b, double c, dou
   reinterpret_cast<double2*>(s)[3] = make_double2(0.0, 0.0);
 }
 
+// Bilinear gather from the interleaved field grid.  The xi push needs the first kGP
+// components of a node (psi, its gradient, B_x, B_y, B_z): one 16-byte and one 8-byte load
+// per node (FP32).
+constexpr int kGP = 6;
+__device__ __forceinline__ void ld6(const float* p, float v[6]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  const float2 r = *reinterpret_cast<const float2*>(p + 4);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w; v[4] = r.x; v[5] = r.y;
+}
+__device__ __forceinline__ void ld6(const double* p, double v[6]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  const double2 c = *reinterpret_cast<const double2*>(p + 4);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+}
+
 template <typename R>
-__device__ __forceinline__ void gather8(const R* __restrict__ fg, const Cic<R>& c, int nx,
-                                        R out[8]) {
-  R a[8], b[8], d[8], e[8];
+__device__ __forceinline__ void gather6(const R* __restrict__ fg, const Cic<R>& c, int nx,
+                                        R out[kGP]) {
+  R a[kGP], b[kGP], d[kGP], e[kGP];
   (void)QSA_IN(c.x0 >= 0 && c.x0 < nx && c.x1 >= 0 && c.x1 < nx && c.y0 >= 0 && c.y1 >= 0);
-  const R* pa = fg + ((size_t)c.y0 * nx + c.x0) * kFG;
-  const R* pb = fg + ((size_t)c.y0 * nx + c.x1) * kFG;
-  const R* pd = fg + ((size_t)c.y1 * nx + c.x0) * kFG;
-  const R* pe = fg + ((size_t)c.y1 * nx + c.x1) * kFG;
-  ld4(pa, a); ld4(pa + 4, a + 4);
-  ld4(pb, b); ld4(pb + 4, b + 4);
-  ld4(pd, d); ld4(pd + 4, d + 4);
-  ld4(pe, e); ld4(pe + 4, e + 4);
+  ld6(fg + ((size_t)c.y0 * nx + c.x0) * kFG, a);
+  ld6(fg + ((size_t)c.y0 * nx + c.x1) * kFG, b);
+  ld6(fg + ((size_t)c.y1 * nx + c.x0) * kFG, d);
+  ld6(fg + ((size_t)c.y1 * nx + c.x1) * kFG, e);
   const R gx = R(1) - c.fx, gy = R(1) - c.fy;
 #pragma unroll
-  for (int k = 0; k < 8; ++k)
+  for (int k = 0; k < kGP; ++k)
     out[k] = gy * (gx * a[k] + c.fx * b[k]) + c.fy * (gx * d[k] + c.fx * e[k]);
 }
 
 // The same gather for the two particles of a thread when both sit in their home cell
 // (column ix, row iy; x1, y1 the next ones): the four corner nodes are loaded once.
 template <typename R>
-__device__ __forceinline__ void gather8_pair(const R* __restrict__ fg, int ix, int x1, int iy,
+__device__ __forceinline__ void gather6_pair(const R* __restrict__ fg, int ix, int x1, int iy,
                                              int y1, int nx, const Cic<R> (&c)[2],
-                                             R (&out)[2][8]) {
-  R a[8], b[8], d[8], e[8];
-  const R* pa = fg + ((size_t)iy * nx + ix) * kFG;
-  const R* pb = fg + ((size_t)iy * nx + x1) * kFG;
-  const R* pd = fg + ((size_t)y1 * nx + ix) * kFG;
-  const R* pe = fg + ((size_t)y1 * nx + x1) * kFG;
-  ld4(pa, a); ld4(pa + 4, a + 4);
-  ld4(pb, b); ld4(pb + 4, b + 4);
-  ld4(pd, d); ld4(pd + 4, d + 4);
-  ld4(pe, e); ld4(pe + 4, e + 4);
+                                             R (&out)[2][kGP]) {
+  R a[kGP], b[kGP], d[kGP], e[kGP];
+  ld6(fg + ((size_t)iy * nx + ix) * kFG, a);
+  ld6(fg + ((size_t)iy * nx + x1) * kFG, b);
+  ld6(fg + ((size_t)y1 * nx + ix) * kFG, d);
+  ld6(fg + ((size_t)y1 * nx + x1) * kFG, e);
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
     const R gx = R(1) - c[u].fx, gy = R(1) - c[u].fy;
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < kGP; ++k)
       out[u][k] = gy * (gx * a[k] + c[u].fx * b[k]) + c[u].fy * (gx * d[k] + c[u].fx * e[k]);
   }
 }
@@ -501,7 +499,7 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
           int ii[2];
           R ox[2], oy[2], uxs[2], uys[2], pprev[2];
           Cic<R> c[2];
-          R F[2][8];
+          R F[2][kGP];
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             ii[u] = base + (ok[u] ? sub0 + u : sub0) * nx + ix;
@@ -524,12 +522,12 @@ __device__ void dep_phase(const SweepArgs<R>& a, R* tile, int mode, int j, doubl
 #pragma unroll
             for (int u = 0; u < 2; ++u)
               c[u] = Cic<R>{ix, gx1, crow, gy1, 1, hx[u] + ox[u], hy[u] + oy[u]};
-            gather8_pair(fgp, ix, gx1, crow, gy1, nx, c, F);
+            gather6_pair(fgp, ix, gx1, crow, gy1, nx, c, F);
           } else {
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
               c[u] = cic<R>(ix, crow, hx[u] + ox[u], hy[u] + oy[u], nx, ny, crow);
-              gather8(fgp, c[u], nx, F[u]);
+              gather6(fgp, c[u], nx, F[u]);
             }
           }
           // arithmetic of both particles; their deposit values are kept for the deposit step
