@@ -40,9 +40,11 @@ namespace qsa {
 
 constexpr int kMaxPipe = 16;
 constexpr int kMaxSpecies = 4;
-// resident blocks per SM the register budget is set for (a build setting for tuning)
+// resident blocks per SM the register budget is set for (a build setting for tuning): three
+// (85 registers a thread) run the late, filamented beam faster than four (64), at the same
+// linear-stage speed
 #ifndef QSA_PIPE_BLOCKS_PER_SM
-#define QSA_PIPE_BLOCKS_PER_SM 4
+#define QSA_PIPE_BLOCKS_PER_SM 3
 #endif
 constexpr int kPipeBlocksPerSM = QSA_PIPE_BLOCKS_PER_SM;
 
