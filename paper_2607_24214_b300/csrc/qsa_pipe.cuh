@@ -98,8 +98,9 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
   // active slots of the trial phases (t) and of the commit slot (c), with the offsets of
   // their first unit in each phase (deposit rows, FFT rows, FFT columns, beam groups)
   __shared__ int act_t[kMaxPipe], act_c[kMaxPipe];
-  __shared__ int ot_dep[kMaxPipe], ot_row[kMaxPipe], ot_col[kMaxPipe];
-  __shared__ int oc_dep[kMaxPipe], oc_row[kMaxPipe], oc_col[kMaxPipe], o_push[kMaxPipe];
+  __shared__ int ot_dep[kMaxPipe], ot_row[kMaxPipe], ot_col[kMaxPipe], ot_rowf[kMaxPipe];
+  __shared__ int oc_dep[kMaxPipe], oc_row[kMaxPipe], oc_col[kMaxPipe], oc_rowf[kMaxPipe];
+  __shared__ int o_push[kMaxPipe];
   __shared__ int ngrp[kMaxPipe];  // beam groups each slot pushes in this tick
   __shared__ int pcdone[kMaxPipe];  // tolerance mode: the slot's slice has converged
   __shared__ int n_t, n_c, stop;
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
     if (tid == 0) {
       // offsets of each slot's units in the phases of this tick (identical in every block)
       int nt = 0, nc = 0, all_done = 1;
-      int udep = 0, urow = 0, ucol = 0, cdep = 0, crow = 0, ccol = 0;
+      int udep = 0, urow = 0, ucol = 0, cdep = 0, crow = 0, ccol = 0, urowf = 0, crowf = 0;
       for (int s = 0; s < nslots; ++s) {
         const DevParams& p = sa[s].p;
         const int nk = p.nk, a = adv[s];
@@ -184,9 +185,11 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
           ot_dep[nt] = udep;
           ot_row[nt] = urow;
           ot_col[nt] = ucol;
+          ot_rowf[nt] = urowf;
           udep += p.ny;
           urow += ur;
           ucol += uc;
+          urowf += row_tasks<R>(p, nbr, DEP_TRIAL);
           act_t[nt++] = s;
         }
         pcdone[s] = 0;
@@ -194,9 +197,11 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
           oc_dep[nc] = cdep;
           oc_row[nc] = crow;
           oc_col[nc] = ccol;
+          oc_rowf[nc] = crowf;
           cdep += p.ny;
           crow += ur;
           ccol += uc;
+          crowf += row_tasks<R>(p, nbr, DEP_COMMIT);
           act_c[nc++] = s;
         }
         if (js[s] < nk || pf[s] < p.nxi) all_done = 0;
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
         for (int k = 0; k < nt; ++k) {
           const int s = act_t[k];
           if (pcdone[s]) continue;
-          row_phase(sa[s], buf, tw, DEP_TRIAL, js[s], unit0(ot_row[k], G), G, nbr);
+          row_phase(sa[s], buf, tw, DEP_TRIAL, js[s], unit0(ot_rowf[k], G), G, nbr);
         }
         if (!grid_sync(bar, epoch)) return;
         for (int k = 0; k < nt; ++k) {
@@ -316,7 +321,7 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
       for (int k = 0; k < nc; ++k) {
         const int s = act_c[k];
         row_phase(sa[s], buf, tw, js[s] < 0 ? DEP_INIT : DEP_COMMIT, js[s] + 1,
-                  unit0(oc_row[k], G), G, nbr);
+                  unit0(oc_rowf[k], G), G, nbr);
       }
       if (!grid_sync(bar, epoch)) return;
       for (int k = 0; k < nc; ++k) {

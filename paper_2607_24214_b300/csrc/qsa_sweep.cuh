@@ -768,6 +768,14 @@ template <typename R>
 __host__ __device__ inline int row_units(const DevParams& p, int nb) {
   return warp_rows<R>(p) ? (p.ny + kWarpRows - 1) / kWarpRows : (p.ny + nb - 1) / nb;
 }
+// Work items of the forward row phase: with rows by warps, one per unit and pair of fields
+// (three pairs of a trial phase's five fields, two of the commit's three), so that a block
+// takes the pairs of a unit apart and the phase's items spread over more blocks.
+template <typename R>
+__host__ __device__ inline int row_tasks(const DevParams& p, int nb, int mode) {
+  const int u = row_units<R>(p, nb);
+  return warp_rows<R>(p) ? u * (mode == DEP_TRIAL ? 3 : 2) : u;
+}
 
 // The same for the column phases of FP32 grids 256 points tall: a unit is one half-spectrum
 // column; the forward transforms along y of its fields run one per warp into the block's
@@ -820,7 +828,7 @@ __device__ __forceinline__ void col_inverse_w(const SweepArgs<R>& a, C<R>* buf, 
 // consecutive k_y per (field, k_x).  k0: the first beam-source node read.
 template <typename R>
 __device__ void row_unit_w(const SweepArgs<R>& a, C<R>* buf, const C<R>* tw, int mode, int k0,
-                           int qb, R& charge) {
+                           int qb, int pr, R& charge) {
   const DevParams& p = a.p;
   constexpr int nx = 256;
   const int ny = p.ny, nxh = p.nxh, nk = p.nk;
@@ -856,7 +864,7 @@ __device__ void row_unit_w(const SweepArgs<R>& a, C<R>* buf, const C<R>* tw, int
     p2 = part + (size_t)wrap(q - 1, ny) * tile_elems + 2 * nx;
     p3 = part + (size_t)wrap(q - 2, ny) * tile_elems + 3 * nx;
   }
-  for (int pr = 0; pr < npair; ++pr) {
+  {
     const int f0 = 2 * pr, f1 = 2 * pr + 1;
     if (act) {
       C<R> z[8];
@@ -976,7 +984,17 @@ __device__ void row_unit_w(const SweepArgs<R>& a, C<R>* buf, const C<R>* tw, int
     }
     __syncthreads();
   }
-  if (act && lane == 0) a.odirty[q] = 0;  // consumed (every lane read it before the barriers)
+  // the overflow row flags stay set: the unit's other pairs may still read them in other
+  // blocks; the column phase that follows clears them (clear_odirty)
+}
+
+// Clear the overflow-row flags that the forward row phase by warps has consumed (it cannot
+// clear them itself: the pairs of a row are read by different blocks).  Rows u0, u0 + G, ...
+template <typename R>
+__device__ __forceinline__ void clear_odirty(const SweepArgs<R>& a, int u0, int G) {
+  if (!warp_rows<R>(a.p)) return;
+  for (int q = u0 * (int)blockDim.x + (int)threadIdx.x; q < a.p.ny; q += G * (int)blockDim.x)
+    a.odirty[q] = 0;
 }
 
 // One unit of the inverse row phase by warps (see irow_phase): warp w transforms row qb + w
@@ -1109,7 +1127,8 @@ __device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, 
   const R* __restrict__ src = a.src;
   __shared__ double red[32];
   const bool wr = warp_rows<R>(p);
-  if (u0 * (wr ? kWarpRows : nb) >= ny) {  // no unit in this block
+  const int ntask = row_tasks<R>(p, nb, mode);
+  if (wr ? u0 >= ntask : u0 * nb >= ny) {  // no unit in this block
     if (threadIdx.x == 0 && mode != DEP_TRIAL) *pslot(a.dpart, jj, P_CHARGE) = 0.0;
     return;
   }
@@ -1118,8 +1137,8 @@ __device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, 
   const int k0 = (mode == DEP_TRIAL) ? jj : jj - 1;  // beam-source nodes k0, k0 + 1
   if (wr) {
     __syncthreads();
-    for (int u = u0; u * kWarpRows < ny; u += G)
-      row_unit_w(a, buf, tw, mode, k0, u * kWarpRows, charge);
+    for (int t = u0; t < ntask; t += G)
+      row_unit_w(a, buf, tw, mode, k0, (t / npair) * kWarpRows, t % npair, charge);
   }
   for (int u = u0; !wr && u * nb < ny; u += G) {
     const int qb = u * nb, nr = min(nb, ny - qb);
@@ -1265,6 +1284,7 @@ __device__ void col_phase_b(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int j, b
   C<R>* A = buf;
   C<R>* B = buf + kNF * ny * nb;
   __shared__ R s_kap;
+  clear_odirty(a, u0, G);
   if (u0 * (warp_cols<R>(p) ? 1 : nb) >= nxh) {  // no unit in this block
     if (threadIdx.x == 0 && last) {
       *pslot(a.dpart, j, P_PCNUM) = 0.0;
@@ -1425,6 +1445,7 @@ __device__ void col_phase_psi(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int u0
   C<R>* B = buf + kNF * ny * nb;
   const C<R>* __restrict__ rspec = a.rspec;
   const bool wc = warp_cols<R>(p);
+  clear_odirty(a, u0, G);
   if (u0 * (wc ? 1 : nb) >= nxh) return;  // no unit in this block
   load_tw(tw, a.twy, ny);
   if (wc) __syncthreads();  // the table
