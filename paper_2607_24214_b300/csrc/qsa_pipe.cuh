@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
   __shared__ int js[kMaxPipe], pf[kMaxPipe], npush[kMaxPipe], adv[kMaxPipe], margin[kMaxPipe];
   __shared__ double psi0[kMaxPipe], ez0h[kMaxPipe], ez0n[kMaxPipe], ez0j[kMaxPipe];
   // active slots of the trial phases (t) and of the commit slot (c), with the offsets of
-  // their first unit in each phase (deposit rows, FFT rows, FFT columns, beam groups)
+  // their first work item in each phase (deposit rows; inverse-row items (row); FFT columns;
+  // forward-row items (rowf); beam groups)
   __shared__ int act_t[kMaxPipe], act_c[kMaxPipe];
   __shared__ int ot_dep[kMaxPipe], ot_row[kMaxPipe], ot_col[kMaxPipe], ot_rowf[kMaxPipe];
   __shared__ int oc_dep[kMaxPipe], oc_row[kMaxPipe], oc_col[kMaxPipe], oc_rowf[kMaxPipe];
@@ -180,14 +181,14 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
       for (int s = 0; s < nslots; ++s) {
         const DevParams& p = sa[s].p;
         const int nk = p.nk, a = adv[s];
-        const int ur = row_units<R>(p, nbr), uc = col_units<R>(p, nbc);
+        const int uc = col_units<R>(p, nbc);
         if (a && js[s] >= 0) {
           ot_dep[nt] = udep;
           ot_row[nt] = urow;
           ot_col[nt] = ucol;
           ot_rowf[nt] = urowf;
           udep += p.ny;
-          urow += ur;
+          urow += irow_tasks<R>(p, nbr);
           ucol += uc;
           urowf += row_tasks<R>(p, nbr, DEP_TRIAL);
           act_t[nt++] = s;
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(256, kPipeBlocksPerSM)
           oc_col[nc] = ccol;
           oc_rowf[nc] = crowf;
           cdep += p.ny;
-          crow += ur;
+          crow += irow_tasks<R>(p, nbr);
           ccol += uc;
           crowf += row_tasks<R>(p, nbr, DEP_COMMIT);
           act_c[nc++] = s;

@@ -776,6 +776,13 @@ __host__ __device__ inline int row_tasks(const DevParams& p, int nb, int mode) {
   const int u = row_units<R>(p, nb);
   return warp_rows<R>(p) ? u * (mode == DEP_TRIAL ? 3 : 2) : u;
 }
+// Work items of the inverse row phase: with rows by warps, one per unit and pair of output
+// fields.
+template <typename R>
+__host__ __device__ inline int irow_tasks(const DevParams& p, int nb) {
+  const int u = row_units<R>(p, nb);
+  return warp_rows<R>(p) ? 2 * u : u;
+}
 
 // The same for the column phases of FP32 grids 256 points tall: a unit is one half-spectrum
 // column; the forward transforms along y of its fields run one per warp into the block's
@@ -997,12 +1004,14 @@ __device__ __forceinline__ void clear_odirty(const SweepArgs<R>& a, int u0, int 
     a.odirty[q] = 0;
 }
 
-// One unit of the inverse row phase by warps (see irow_phase): warp w transforms row qb + w
-// (two packed pairs of output fields, read row-contiguous from the column phase's spectra) and
-// writes the field grid, and on the last solve the slab, for the 8 columns x = lane + 32 d.
+// One item of the inverse row phase by warps (see irow_phase): warp w transforms row qb + w
+// of one packed pair of output fields (pr = 0: psi, d_x psi or B_x, B_y; pr = 1: d_y psi or
+// B_z, E_z), read row-contiguous from the column phase's spectra, and writes the field grid,
+// and on the last solve its components of the slab, for the 8 columns x = lane + 32 d.  The
+// two pairs of a row are independent, so they may run in different blocks.
 template <typename R>
 __device__ void irow_unit_w(const SweepArgs<R>& a, C<R>* buf, const C<R>* tw, bool psi_mode,
-                            int j, bool last, R ez0r, int qb, R (&en)[6], bool& bad) {
+                            int j, bool last, R ez0r, int qb, int pr, R (&en)[6], bool& bad) {
   const DevParams& p = a.p;
   constexpr int nx = 256;
   const int ny = p.ny, nxh = p.nxh;
@@ -1015,71 +1024,71 @@ __device__ void irow_unit_w(const SweepArgs<R>& a, C<R>* buf, const C<R>* tw, bo
   const C<R>* __restrict__ cspec = a.cspec;
   R* __restrict__ fg = a.fg;
   C<R>* F = buf + w * kWarpRowStride;
-  // the slab of the last solve adds W = -grad psi from the field grid, written one slice
-  // earlier and by now often out of L2: fetch the row while the transforms run
-  if (!psi_mode && last && lane == 0)
+  const bool slab = !psi_mode && last;
+  // the slab's W = -grad psi comes from the field grid, written one slice earlier and by
+  // now often out of L2: fetch the row while the transform runs
+  if (slab && pr == 0 && lane == 0)
     l2_prefetch(fg + (size_t)q * nx * kFG, (unsigned)((size_t)nx * kFG * sizeof(R)));
   const C<R>* r0 = cspec + (size_t)q * nxh;  // field f's row: r0 + f * ny * nxh
   const size_t fs = (size_t)ny * nxh;
-  for (int pr = 0; pr < 2; ++pr) {
-    const int f0 = 2 * pr, f1 = 2 * pr + 1;
-    C<R> z[8];
-    // full spectrum of z = a + i b from the half spectra of the real outputs a, b; four
-    // columns at a time with the loads issued first
+  const int f0 = 2 * pr, f1 = 2 * pr + 1;
+  C<R> z[8];
+  // full spectrum of z = a + i b from the half spectra of the real outputs a, b; four
+  // columns at a time with the loads issued first
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      C<R> fa[4], fb[4];
+  for (int h = 0; h < 2; ++h) {
+    C<R> fa[4], fb[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int k = lane + 32 * (4 * h + i);
-        const int kk = (k < nxh) ? k : nx - k;
-        fa[i] = r0[f0 * fs + kk];
-        fb[i] = (f1 < nout) ? r0[f1 * fs + kk] : C<R>{0, 0};
+    for (int i = 0; i < 4; ++i) {
+      const int k = lane + 32 * (4 * h + i);
+      const int kk = (k < nxh) ? k : nx - k;
+      fa[i] = r0[f0 * fs + kk];
+      fb[i] = (f1 < nout) ? r0[f1 * fs + kk] : C<R>{0, 0};
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = lane + 32 * (4 * h + i);
+      const int kk = (k < nxh) ? k : nx - k;
+      if (kk == 0 || 2 * kk == nx) {  // self-conjugate columns
+        fa[i].y = R(0);
+        fb[i].y = R(0);
       }
+      if (k >= nxh) {
+        fa[i] = cconj(fa[i]);
+        fb[i] = cconj(fb[i]);
+      }
+      z[4 * h + i] = cadd(fa[i], cmuli(fb[i]));
+    }
+  }
+  warp_fft256(z, F, tw, +1);
+  if (!slab) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int k = lane + 32 * (4 * h + i);
-        const int kk = (k < nxh) ? k : nx - k;
-        if (kk == 0 || 2 * kk == nx) {  // self-conjugate columns
-          fa[i].y = R(0);
-          fb[i].y = R(0);
-        }
-        if (k >= nxh) {
-          fa[i] = cconj(fa[i]);
-          fb[i] = cconj(fb[i]);
-        }
-        z[4 * h + i] = cadd(fa[i], cmuli(fb[i]));
+    for (int d = 0; d < 8; ++d) {
+      R* node = fg + ((size_t)q * nx + lane + 32 * d) * kFG;
+      const R va = z[d].x * scale, vb = z[d].y * scale;
+      if (pr == 0) {
+        node[psi_mode ? FG_PSI : FG_BX] = va;
+        node[psi_mode ? FG_GX : FG_BY] = vb;
+      } else if (psi_mode) {
+        node[FG_GY] = va;
+      } else {
+        node[FG_BZ] = va;
+        node[FG_EZ] = vb;
       }
     }
-    warp_fft256(z, F, tw, +1);
-    if (pr == 0 || psi_mode || !last) {
-#pragma unroll
-      for (int d = 0; d < 8; ++d) {
-        R* node = fg + ((size_t)q * nx + lane + 32 * d) * kFG;
-        const R va = z[d].x * scale, vb = z[d].y * scale;
-        if (pr == 0) {
-          node[psi_mode ? FG_PSI : FG_BX] = va;
-          node[psi_mode ? FG_GX : FG_BY] = vb;
-        } else if (psi_mode) {
-          node[FG_GY] = va;
-        } else {
-          node[FG_BZ] = va;
-          node[FG_EZ] = vb;
-        }
-      }
-      continue;
-    }
-    // the last solve: the slab node, its energies and the finiteness check; B_x, B_y are
-    // this thread's own stores of the first pair, W = -grad psi the field grid's; four
-    // columns at a time with the loads issued first
+    return;
+  }
+  // the last solve: the field grid, this pair's components of the slab node (W_x, W_y, B_x,
+  // B_y from the first; E_z and B_z, with the node's two pads, from the second), their
+  // energies and the finiteness check
+  if (pr == 0) {
+    // W = -grad psi from the field grid, four columns at a time with the loads issued first
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      R bx[4], by[4], gx[4], gy[4];
+      R gx[4], gy[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const R* node = fg + ((size_t)q * nx + lane + 32 * (4 * h + i)) * kFG;
-        bx[i] = node[FG_BX];
-        by[i] = node[FG_BY];
         gx[i] = node[FG_GX];
         gy[i] = node[FG_GY];
       }
@@ -1087,21 +1096,40 @@ __device__ void irow_unit_w(const SweepArgs<R>& a, C<R>* buf, const C<R>* tw, bo
       for (int i = 0; i < 4; ++i) {
         const int d = 4 * h + i, x = lane + 32 * d;
         R* node = fg + ((size_t)q * nx + x) * kFG;
-        const R va = z[d].x * scale, vb = z[d].y * scale;
-        node[FG_BZ] = va;
-        node[FG_EZ] = vb;
+        const R bx = z[d].x * scale, by = z[d].y * scale;
+        node[FG_BX] = bx;
+        node[FG_BY] = by;
         const R wx = -gx[i], wy = -gy[i];
-        const R ez = ez0r + vb;
-        st8(a.slab + (((size_t)j * ny + q) * nx + x) * 8, wx, wy, ez, bx[i], by[i], va);
-        const R Ex = wx + by[i], Ey = wy - bx[i];
+        R* sl = a.slab + (((size_t)j * ny + q) * nx + x) * 8;
+        sl[0] = wx;
+        sl[1] = wy;
+        sl[3] = bx;
+        sl[4] = by;
+        const R Ex = wx + by, Ey = wy - bx;
         en[0] += Ex * Ex;
         en[1] += Ey * Ey;
-        en[2] += ez * ez;
-        en[3] += bx[i] * bx[i];
-        en[4] += by[i] * by[i];
-        en[5] += va * va;
-        if (!(isfinite(Ex) && isfinite(Ey) && isfinite(ez) && isfinite(va))) bad = true;
+        en[3] += bx * bx;
+        en[4] += by * by;
+        if (!(isfinite(Ex) && isfinite(Ey))) bad = true;
       }
+    }
+  } else {
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const int x = lane + 32 * d;
+      R* node = fg + ((size_t)q * nx + x) * kFG;
+      const R va = z[d].x * scale, vb = z[d].y * scale;
+      node[FG_BZ] = va;
+      node[FG_EZ] = vb;
+      const R ez = ez0r + vb;
+      R* sl = a.slab + (((size_t)j * ny + q) * nx + x) * 8;
+      sl[2] = ez;
+      sl[5] = va;
+      sl[6] = R(0);
+      sl[7] = R(0);
+      en[2] += ez * ez;
+      en[5] += va * va;
+      if (!(isfinite(ez) && isfinite(va))) bad = true;
     }
   }
 }
@@ -1533,7 +1561,9 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
   const C<R>* __restrict__ cspec = a.cspec;
   R* __restrict__ fg = a.fg;
   __shared__ double red[64];
-  if (u0 * (warp_rows<R>(p) ? kWarpRows : nb) >= ny) {  // no unit in this block
+  const bool wr = warp_rows<R>(p);
+  const int ntask = irow_tasks<R>(p, nb);
+  if (wr ? u0 >= ntask : u0 * nb >= ny) {  // no unit in this block
     if (threadIdx.x == 0 && !psi_mode && last)
       for (int f = 0; f < 6; ++f) *pslot(a.dpart, j, P_E0 + f) = 0.0;
     return;
@@ -1541,11 +1571,10 @@ __device__ void irow_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, bool psi_
   R en[6] = {0, 0, 0, 0, 0, 0};
   bool bad = false;
   load_tw(tw, a.twx, nx);
-  const bool wr = warp_rows<R>(p);
   if (wr) {
     __syncthreads();
-    for (int u = u0; u * kWarpRows < ny; u += G)
-      irow_unit_w(a, buf, tw, psi_mode, j, last, ez0r, u * kWarpRows, en, bad);
+    for (int t = u0; t < ntask; t += G)
+      irow_unit_w(a, buf, tw, psi_mode, j, last, ez0r, (t >> 1) * kWarpRows, t & 1, en, bad);
     __syncthreads();  // the buffers and the table are reused by the block's next phase
   }
   for (int u = u0; !wr && u * nb < ny; u += G) {
