@@ -829,10 +829,11 @@ __device__ __forceinline__ void col_inverse_w(const SweepArgs<R>& a, C<R>* buf, 
   for (int d = 0; d < 8; ++d) a.cspec[((size_t)w * ny + lane + 32 * d) * nxh + kx] = z[d];
 }
 
-// One unit of the forward row phase by warps: rows qb .. qb + 7 (those below ny).  Warp w forms
-// the packed pairs of row qb + w (the same sums as row_phase), transforms them, and leaves each
-// spectrum in its buffer; the block then writes the half spectra of its rows, eight
-// consecutive k_y per (field, k_x).  k0: the first beam-source node read.
+// One item of the forward row phase by warps: pair pr of fields (2 pr, 2 pr + 1) of rows
+// qb .. qb + 7 (those below ny).  Warp w forms the packed pair of row qb + w (the same sums as
+// row_phase), transforms it, and leaves the spectrum in its buffer; the block then writes the
+// half spectra of its rows, eight consecutive k_y per (field, k_x).  k0: the first
+// beam-source node read.  The pairs of a unit are separate items (row_tasks).
 template <typename R>
 __device__ void row_unit_w(const SweepArgs<R>& a, C<R>* buf, const C<R>* tw, int mode, int k0,
                            int qb, int pr, R& charge) {
@@ -1140,6 +1141,8 @@ __device__ void irow_unit_w(const SweepArgs<R>& a, C<R>* buf, const C<R>* tw, bo
 // A unit of the FFT phases is nb consecutive rows (or half-spectrum columns): their
 // transforms run in one block_fft call (more butterflies per thread between the stage
 // barriers) and the transposed writes of neighbouring rows (columns) land next to each other.
+// With rows by warps (FP32, 256 wide) a unit is kWarpRows rows and its pairs of fields are
+// dealt as separate items (row_tasks, irow_tasks).
 template <typename R>
 __device__ void row_phase(const SweepArgs<R>& a, C<R>* buf, C<R>* tw, int mode, int jj, int u0,
                           int G, int nb) {
