@@ -80,6 +80,21 @@ def test_batch_of_uneven_instances(qsa_mod, prec):
     check_batch(qsa_mod, instances(5, prec), 3, TOL[prec])
 
 
+def test_batch_mixing_row_paths(qsa_mod):
+    """Mixed precision, grids 256 wide (rows by warps: each row unit's pairs of fields are
+    separate work items) in one launch with narrower grids (rows by block transforms): the
+    slots' work items of every phase are laid end to end with different counts per unit."""
+    ps = []
+    for i, (nx, ny) in enumerate([(256, 16), (32, 32), (256, 8), (24, 24)]):
+        p = config.c1_fp64_electron_beam().with_(
+            nx=nx, ny=ny, Lx=nx * 0.05, Ly=ny * 0.25, nxi=24, Lxi=3.0, precision="mixed",
+            seed=40 + i, dt=3.0 + i, diag_modes=[(1, 1)])
+        p.species[0].alpha = 0.02 * (1 + i)
+        p.species[0].gamma_b = 60.0 + 30.0 * i
+        ps.append(p)
+    check_batch(qsa_mod, ps, 3, TOL["mixed"])
+
+
 def test_batch_larger_than_one_launch(qsa_mod):
     """18 instances: two launches per step (16 + 2)."""
     check_batch(qsa_mod, instances(18, "fp64"), 2, TOL["fp64"])
