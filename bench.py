@@ -39,6 +39,7 @@ METRIC = "plasma particle-slice updates/s (push+deposit+field solve), mixed vs F
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pipe_kernel_c2_linear_launch_dram.md")
 WORKLOAD = "c2_mixed_electron_beam_256x256_1024slices"
 CPU_SAMPLE_SLICES = 12
+REF_BUDGET_S = 150.0  # the reference arm's timed and warm-up steps together
 
 
 def bytes_per_update(p):
@@ -203,13 +204,20 @@ def time_steps(q, p, steps, warmup, torch, stream, extra=None):
     return t0.elapsed_time(t1), sw, pu, launches
 
 
-def cpu_baseline(p, slices=CPU_SAMPLE_SLICES):
-    """The FP64 oracle, as it stands, on the first `slices` slices of one sweep of the same
-    workload (the particles of the first xi cells only: the slice loop is sequential in xi)."""
-    from oracle import qspic
+def oracle_sample_beam(p, slices):
+    """The synthetic beam particles of the first slices + 2 xi cells (the oracle's sample)."""
     from paper_2607_24214_b300 import inputs
     per_layer = p.nx * p.ny * p.species[0].ppc_x * p.species[0].ppc_y * p.species[0].ppc_xi
-    sub = inputs.beam_arrays(p, 0, 0, (slices + 2) * per_layer)
+    return inputs.beam_arrays(p, 0, 0, (slices + 2) * per_layer)
+
+
+def cpu_baseline(p, slices=CPU_SAMPLE_SLICES, sub=None):
+    """The FP64 oracle, as it stands, on the first `slices` slices of one sweep of the same
+    workload (the particles of the first xi cells only: the slice loop is sequential in xi).
+    sub: those particles, when already generated (oracle_sample_beam)."""
+    from oracle import qspic
+    if sub is None:
+        sub = oracle_sample_beam(p, slices)
     t = time.perf_counter()
     src = qspic.beam_sources(p, [sub], n_nodes=slices + 2)
     qspic.plasma_sweep(p, src, n_slices=slices)
@@ -260,26 +268,36 @@ def cpu_c1_full():
 
 
 def run_reference(args, p):
+    """The reference arm: the FP64 oracle, as it stands, on this host's cores, for the same
+    metric and workload.  Each of the --warmup untimed and --steps timed steps is one oracle
+    sample (the first slices of one sweep); unless --ref-slices fixes it, the sample is sized
+    from a one-slice probe so that all the steps take about REF_BUDGET_S seconds."""
     rank, world, _ = dist_info()
     if rank != 0:
         return
+    steps, warmup = max(args.steps, 1), max(args.warmup, 0)
+    slices = args.ref_slices
+    if slices <= 0:
+        _, t1 = cpu_baseline(p, 1)  # untimed probe
+        slices = int(max(1, min(CPU_SAMPLE_SLICES, REF_BUDGET_S / ((steps + warmup) * t1))))
+    sub = oracle_sample_beam(p, slices)  # the inputs, generated once
+    for _ in range(warmup):
+        cpu_baseline(p, slices, sub)
     vals = []
-    for _ in range(args.warmup_ref):
-        cpu_baseline(p, 2)
     t0 = time.perf_counter()
-    for _ in range(args.steps_ref):
-        v, _ = cpu_baseline(p, args.ref_slices)
+    for _ in range(steps):
+        v, _ = cpu_baseline(p, slices, sub)
         vals.append(v)
     wall = time.perf_counter() - t0
     val = float(np.median(vals))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "updates/s",
-            "n_gpus": args.gpus, "steps": args.steps_ref, "warmup": args.warmup_ref,
-            "ms_per_step": 1e3 * wall / max(args.steps_ref, 1), "higher_is_better": True,
+            "n_gpus": args.gpus, "steps": steps, "warmup": warmup,
+            "ms_per_step": 1e3 * wall / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"first {args.ref_slices} slices"},
+            "config": {"workload": WORKLOAD, "sample": f"first {slices} slices"},
             "cpu_baseline": {"value": val, "unit": "updates/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {args.ref_slices} of {p.nxi + 1} slices of "
-                                       f"one sweep, {p.nx}x{p.ny}, numpy FP64"},
+                             "sample": f"first {slices} of {p.nxi + 1} slices of one sweep "
+                                       f"per step, {p.nx}x{p.ny}, numpy FP64"},
             "e2e": {"value": val, "unit": "updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -342,10 +360,9 @@ def main():
                     help="timed steps of the batched C4 scan after its 8 untimed autotuning "
                          "steps (42: the scan's 50 steps in all)")
     ap.add_argument("--no-adjoint", action="store_true")
-    ap.add_argument("--steps-ref", type=int, default=2)
-    ap.add_argument("--ref-slices", type=int, default=CPU_SAMPLE_SLICES,
-                    help="slices of the oracle sample per reference step")
-    ap.add_argument("--warmup-ref", type=int, default=0)
+    ap.add_argument("--ref-slices", type=int, default=0,
+                    help="slices of the oracle sample per reference step (0: sized so that "
+                         "the reference arm's steps take about REF_BUDGET_S seconds)")
     ap.add_argument("--nxi", type=int, default=0,
                     help="override the number of slices (small profiling cases only)")
     args = ap.parse_args()
